@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""GFMC throughput benchmark on GB300: spin updates/s at L = 32, M = 1024.
+
+Workload (one chain, synthetic): double-exchange model at infinite Hund
+coupling on a 32^3 periodic cubic lattice, t = 1, spins uniform on the sphere
+(seed 0), beta = 20/t, mu = -2t, Jackson kernel, M = 1024 moments, sequential
+sweep with Philox proposals (seed 1).  A "step" is one block of
+``--updates-per-step`` consecutive single-spin updates of the sweep (each
+update = 511 fused 7-vector stencil steps + moments + FFT + quadrature +
+Metropolis + patch), i.e. one pass of the whole hot path over that block.
+
+The headline ``value`` is the FP64 path (all arithmetic in FP64); the same run
+also times the FP32-mixed path and reports it under ``fp32_mixed``.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gfmc|reference]
+
+Under torchrun each rank runs an independent replica chain (chain_id = rank):
+the path shards by chains, with no data-path collective ("replicas only").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "spin updates/s at L=32,M=1024 (FP64 vs FP32-mixed); stencil GB/s; p99 sweep latency"
+UNIT = "spin updates/s"
+
+# Algorithmic work of one site in one fused stencil step (7 vectors):
+#   stencil  7 x (6 complex MACs + 2r - r_prev)      = 7 x (6 x 8 + 4)   = 364 flop
+#   Gram     28 <r_m|r_m> (7 real diagonal) + 28 <r_m|r_m+1>
+#            = 7 x 3 + 21 x 6 + 28 x 6                                     = 315 flop
+#   sums     112 real partial products added once                           = 112 flop
+FLOP_PER_SITE_STEP = 364 + 315 + 112
+# Bytes of one site in one step: read r_m and r_{m-1}, write r_{m+1} for 7
+# vectors (21 complex values) plus the site's bond row (3 complex values).
+def bytes_per_site_step(real_bytes: int) -> int:
+    return 21 * 2 * real_bytes + 3 * 2 * real_bytes
+
+
+def update_work(L: int, M: int, real_bytes: int):
+    N = L ** 3
+    steps = M // 2 - 1
+    return steps * N * FLOP_PER_SITE_STEP, steps * N * bytes_per_site_step(real_bytes)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# FP64 / FP32 vector (non-tensor) ALU peaks of GB300, derived from the unit
+# counts and the maximum SM clock: 152 SMs x 2070 MHz x 2 flop per FMA x
+# FMA lanes per SM per clock (FP32: 128; FP64: 2, from the 1.25 TFLOP/s figure).
+def alu_peak_tflops(precision: str, sm_mhz: float = 2070.0) -> float:
+    lanes = 2.0 if precision == "fp64" else 128.0
+    return 152 * sm_mhz * 1e6 * 2 * lanes / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = list(self.rows)
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(n_gpus: int):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return rank, world, local, dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, value: float) -> float:
+    if dist is None:
+        return value
+    import torch
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_device(ch, stream, U, steps, warmup, flush, dist, sampler=None):
+    """Device-timed steps: CUDA events on the chain's stream around each step,
+    a 256 MiB L2 flush between steps outside the events."""
+    import torch
+    for _ in range(warmup):
+        ch.updates_into(U)
+    barrier(dist)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    if sampler:
+        sampler.start()
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k)
+        starts[k].record(stream)
+        ch.updates_into(U)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    barrier(dist)
+    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    return per, clocks
+
+
+def time_e2e(ch, stream, U, steps, spins0):
+    """End to end through the public API with pinned host buffers: upload the
+    chain state, run the block of updates with host traces, read the spins."""
+    import numpy as np
+    import torch
+    N = ch.N
+    h_spins = torch.empty((N, 2), dtype=torch.float64, pin_memory=True).numpy()
+    h_out = torch.empty((N, 2), dtype=torch.float64, pin_memory=True).numpy()
+    h_dec = torch.empty(U, dtype=torch.uint8, pin_memory=True).numpy()
+    h_dom = torch.empty(U, dtype=torch.float64, pin_memory=True).numpy()
+    h_spins[:] = spins0
+    counter = ch.counter
+    torch.cuda.synchronize()
+    per = []
+    for _ in range(steps):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        ch.set_state(h_spins, counter)
+        ch.updates_into(U, decisions=h_dec, d_omega=h_dom)
+        ch.get_spins(h_out)
+        e.record(stream)
+        e.synchronize()
+        per.append(s.elapsed_time(e))
+        h_spins[:] = h_out
+        counter += U
+    h2d = N * 16
+    d2h = U * (1 + 8) + N * 16 + 8 + 8
+    assert np.isfinite(h_dom).all()
+    return per, h2d, d2h
+
+
+def cpu_baseline(L, M, spins, n_updates):
+    from oracle import oracle as O
+    O.build()
+    t0 = time.perf_counter()
+    O.updates(L, spins, n_updates, M, beta=20.0, chem=-2.0, seed=1)
+    dt = time.perf_counter() - t0
+    return n_updates / dt, dt
+
+
+def run_reference(args, rank, world, dist):
+    """The oracle (plain single-threaded C, FP64) on the same workload."""
+    if rank != 0:
+        return 0
+    from paper_1303_6016_gb300 import inputs
+    L, M = args.L, args.M
+    spins = inputs.uniform_sphere(L, 0)
+    from oracle import oracle as O
+    O.build()
+    U = 1
+    per = []
+    s = spins.copy()
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        res = O.updates(L, s, U, M, beta=20.0, chem=-2.0, seed=1, upd0=k * U)
+        dt = time.perf_counter() - t0
+        s = res["spins"]
+        if k >= args.warmup:
+            per.append(dt * 1000.0)
+    ms = statistics.mean(per)
+    value = U / (ms / 1000.0)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(L, M, U, "fp64"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{U} update per step from the start of sweep 0 at L={L}, M={M}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(L, M, U, precision):
+    return {"workload": f"GFMC single chain, L={L} (N={L ** 3}) periodic cubic, M={M} Jackson moments, "
+                        "t=1, beta=20/t, mu=-2t, spins uniform on the sphere (seed 0), sequential sweep, "
+                        "Philox proposals (seed 1)",
+            "L": L, "M": M, "updates_per_step": U, "precision": precision,
+            "l2": "flushed between timed steps (256 MiB write); the chain's working set is L2-resident "
+                  "within a step"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gfmc", choices=["gfmc", "reference"])
+    ap.add_argument("--L", type=int, default=32)
+    ap.add_argument("--M", type=int, default=1024)
+    ap.add_argument("--updates-per-step", type=int, default=0)
+    ap.add_argument("--mixed-updates-per-step", type=int, default=0)
+    ap.add_argument("--cpu-updates", type=int, default=2)
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank, world, local, dist = dist_setup(args.gpus)
+    if args.impl == "reference":
+        return run_reference(args, rank, world, dist)
+
+    import torch
+    from paper_1303_6016_gb300 import build, gfmc, inputs
+    if rank == 0 or world == 1:
+        build.build()
+    barrier(dist)
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    L, M, N = args.L, args.M, args.L ** 3
+    spins = inputs.uniform_sphere(L, 0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    U = args.updates_per_step or 16
+    Um = args.mixed_updates_per_step or 64
+    peaks = load_peaks()
+
+    # ---- FP64 headline ----
+    ch = gfmc.Chain(L, spins, M=M, beta=20.0, mu=-2.0, seed=1, chain_id=rank, stream=stream.cuda_stream)
+    sampler = ClockSampler(local)
+    per, clocks = time_device(ch, stream, U, args.steps, args.warmup, flush, dist, sampler)
+    total_ms = max_over_ranks(dist, sum(per))
+    value = world * args.steps * U / (total_ms / 1000.0)
+    ms_step = total_ms / args.steps
+    flop_u, bytes_u = update_work(L, M, 8)
+    launch_s = statistics.mean(per) / 1000.0
+    achieved_tf = U * flop_u / launch_s / 1e12
+    peak_tf = alu_peak_tflops("fp64", clocks.get("sm_max_mhz") or 2070.0) if clocks else alu_peak_tflops("fp64")
+    e2e_per, h2d, d2h = time_e2e(ch, stream, U, max(3, args.steps // 2), ch.get_spins())
+    e2e_value = U / (statistics.mean(e2e_per) / 1000.0) * world
+    ch.close()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(workload_config(L, M, U, "fp64"), parallelism=f"replicas{world}"),
+        "stencil_gbs": U * bytes_u / launch_s / 1e9,
+        "latency_ms_per_update": {"p50": statistics.median(per) / U, "p99": sorted(per)[-1] / U},
+        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
+                     "frac": achieved_tf / peak_tf, "traffic": None,
+                     "peak_source": "FP64 vector peak derived from 152 SMs x max SM clock x 2 FMA lanes "
+                                    "(1.25 TFLOP/s class); not in MEASURED_PEAKS.json"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+
+    # ---- FP32-mixed ----
+    if not args.no_mixed:
+        chm = gfmc.Chain(L, spins, M=M, beta=20.0, mu=-2.0, seed=1, chain_id=rank, precision="fp32_mixed",
+                         stream=stream.cuda_stream)
+        perm, clocks_m = time_device(chm, stream, Um, args.steps, args.warmup, flush, dist, ClockSampler(local))
+        tot_m = max_over_ranks(dist, sum(perm))
+        flop_m, bytes_m = update_work(L, M, 4)
+        launch_m = statistics.mean(perm) / 1000.0
+        gbs = Um * bytes_m / launch_m / 1e9
+        hbm = peaks.get("hbm_gbs")
+        line["fp32_mixed"] = {
+            "value": world * args.steps * Um / (tot_m / 1000.0), "unit": UNIT, "updates_per_step": Um,
+            "ms_per_step": tot_m / args.steps, "stencil_gbs": gbs,
+            "latency_ms_per_update": {"p50": statistics.median(perm) / Um, "p99": sorted(perm)[-1] / Um},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                         "frac": gbs / hbm if hbm else None, "traffic": None,
+                         "note": "algorithmic bytes; the working set is L2-resident, HBM copy peak of "
+                                 "MEASURED_PEAKS.json as the reference bandwidth"},
+            "alu_tflops": Um * flop_m / launch_m / 1e12, "clocks": clocks_m,
+            "gpu_launches": args.steps,
+        }
+        chm.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, dt = cpu_baseline(L, M, spins, args.cpu_updates)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"first {args.cpu_updates} updates of sweep 0 at L={L}, M={M} "
+                                          f"({dt:.1f} s, single-threaded C, FP64)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,165 @@
+/*
+ * gfmc.h -- C ABI of the GB300 GFMC engine (libgfmc.so).
+ *
+ * The engine runs the single-spin update of the O(N) Green-function-based
+ * Monte Carlo method (GFMC) for the double-exchange model at infinite Hund
+ * coupling on an L x L x L periodic simple cubic lattice (arXiv:1303.6016,
+ * Sec. 2.1 and 2.2, Algorithm 1).  One handle owns one Markov chain; all of
+ * its state (spins, hoppings, recursion vectors, random-number position)
+ * lives in device memory, and every step of an update runs in CUDA kernels
+ * for sm_103a.
+ *
+ * Conventions used by every call
+ *   N = L^3 sites, site index i = x + L*(y + L*z) (x fastest), periodic.
+ *   A spin is given by its polar and azimuthal angles (theta, phi) in radians,
+ *   theta in [0, pi], phi finite; arrays of spins are double[N][2].
+ *   Local order of the 7 sites around a site o: 0 = o, 1 = o+x, 2 = o-x,
+ *   3 = o+y, 4 = o-y, 5 = o+z, 6 = o-z (the paper's n,e,s,o,w,t,b relabelled).
+ *   Hopping t_ij = t <chi_i|chi_j> with chi = (cos(theta/2), e^{i phi} sin(theta/2));
+ *   H_ij = -t_ij (Sec. 2.1, Eq. ht up to a diagonal gauge).  Htilde = H / a.
+ *   Energies, t, mu and Delta Omega are in the same units; beta = 1/T.
+ *
+ * Ownership: the caller owns every pointer passed in or out; the library
+ * copies inputs before returning and never keeps a caller pointer.  Host
+ * pointers are plain host memory (pageable or pinned).
+ *
+ * Synchronisation: every call is synchronous -- it enqueues its work on the
+ * handle's stream and returns after that work has finished.
+ *
+ * Errors: every call returns a gfmc_status; the library never aborts or
+ * exits.  gfmc_last_error() returns a message for the last failed call.
+ * A device-side wait that exceeds its budget ends the kernel and returns
+ * GFMC_ETIMEOUT; the handle stays usable.
+ */
+#ifndef GFMC_H
+#define GFMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gfmc_ctx* gfmc_t;
+
+typedef enum {
+    GFMC_OK = 0,
+    GFMC_EINVAL = 1,   /* an argument is out of range (message says which) */
+    GFMC_ENOMEM = 2,   /* device or host allocation failed */
+    GFMC_ECUDA = 3,    /* a CUDA runtime call failed (message has the CUDA error) */
+    GFMC_ETIMEOUT = 4, /* a bounded device wait ran out; the launch was abandoned */
+    GFMC_ENUMERIC = 5  /* a non-finite value appeared in d(z) or Delta Omega */
+} gfmc_status;
+
+enum { GFMC_PREC_FP64 = 0, GFMC_PREC_FP32_MIXED = 1 };
+enum { GFMC_KERNEL_JACKSON = 0, GFMC_KERNEL_LORENTZ = 1 };
+
+typedef struct {
+    /* GFMC_PREC_FP64: recursion vectors, stencil, moments and quadrature in FP64.
+     * GFMC_PREC_FP32_MIXED: recursion vectors and stencil in FP32 complex, dot
+     * products summed in FP32 within a warp and in FP64 above it; moments,
+     * Green's function, determinant and quadrature in FP64. */
+    int precision;
+    /* Kernel g_n damping the moments (Sec. 2.2, mu~_m = mu_m g_m):
+     * GFMC_KERNEL_JACKSON (default) or GFMC_KERNEL_LORENTZ
+     * g_n = sinh(lambda (1 - n/M)) / sinh(lambda). */
+    int kernel;
+    double lorentz_lambda; /* <= 0 selects 4.0 */
+    double spectral_scale; /* a in Htilde = H / a; <= 0 selects 6.05 |t|; must exceed 6 |t| */
+    uint64_t seed;         /* Philox4x32-10 key of the proposals and Metropolis draws */
+    uint32_t chain_id;     /* second key word (XORed with the seed's high word) */
+    void* stream;          /* cudaStream_t to run on; NULL = the legacy default stream */
+    int num_ctas;          /* <= 0: chosen by the library */
+} gfmc_options;
+
+/* Fill *opt with the defaults (FP64, Jackson, a = 6.05|t|, seed 1, chain 0,
+ * default stream, automatic CTA count). */
+void gfmc_default_options(gfmc_options* opt);
+
+/* Create a chain (Sec. 2.1: the spin configuration and H({S}); Sec. 3.3.2:
+ * H and the spins are kept resident in device memory).
+ *   L      lattice edge, 3 <= L <= 42 (N = L^3 <= 74088).
+ *   spins  host double[N][2] (theta, phi), copied.
+ *   t      hopping amplitude, nonzero and finite.
+ *   mu     chemical potential (finite).
+ *   beta   inverse temperature, > 0 and finite.
+ *   M      number of Chebyshev moments: a power of two, 16 <= M <= 4096.
+ *   opt    NULL for defaults.
+ *   out    receives the handle.
+ * The update counter starts at 0: update number u visits site u mod N. */
+gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double beta, int M,
+                        const gfmc_options* opt, gfmc_t* out);
+
+/* The raw (undamped) local moments of the current configuration
+ * (Sec. 2.2: mu_m = <i|T_m(Htilde)|i> and Eq. recursive, extended to the 7x7
+ * block of o and its neighbours; obtained with the doubling of Eq. mu2).
+ *   site    o in [0, N).
+ *   mu_out  host complex128 [7][7][M] as interleaved doubles (re, im):
+ *           mu_out[2*((j*7 + k)*M + n) + {0,1}] = <l_j| T_n(Htilde) |l_k>. */
+gfmc_status gfmc_moments(gfmc_t h, int64_t site, double* mu_out);
+
+/* Delta Omega = Delta S_eff / beta for moving the spin at `site` to
+ * (theta_new, phi_new), from the moments of the current configuration
+ * (Sec. 2.2: Eq. green_delta, Eq. d_z_green, the mixed elements G_{o+v,o+v}
+ * and G_{o+iv,o+iv}, Eq. green_short/green_fft, Eq. d_seff2).  The chain is
+ * not changed.  d_omega receives one double (units of t). */
+gfmc_status gfmc_delta_omega(gfmc_t h, int64_t site, double theta_new, double phi_new,
+                             double* d_omega);
+
+/* Run n_updates sequential single-spin Metropolis updates (Algorithm 1, the
+ * inner loop over sites): update number u (the handle's counter) visits site
+ * u mod N, proposes a new direction uniform on the sphere from Philox draws,
+ * accepts iff exp(-beta Delta Omega) > u01, and on acceptance sets the spin
+ * (H <- H + Delta).  Each completed sweep appends |sum_i S_i| / N.
+ *   n_updates      >= 0.
+ *   n_accepted     host uint64, receives the number accepted (may be NULL).
+ *   decisions      host uint8[n_updates], 1 = accepted (may be NULL).
+ *   d_omega_trace  host double[n_updates] (may be NULL).
+ *   magnetization  host double[n_updates / N + 1] (may be NULL).
+ *   n_mag          host int64, receives how many magnetisations were written
+ *                  (may be NULL). */
+gfmc_status gfmc_updates(gfmc_t h, int64_t n_updates, uint64_t* n_accepted,
+                         uint8_t* decisions, double* d_omega_trace, double* magnetization,
+                         int64_t* n_mag);
+
+/* n_sweeps full sweeps (n_sweeps * N updates) from the current counter;
+ * magnetization receives one value per completed sweep (Algorithm 1).
+ * decisions and d_omega_trace have n_sweeps*N entries.  Any pointer may be NULL. */
+gfmc_status gfmc_sweep(gfmc_t h, int n_sweeps, uint64_t* n_accepted, double* magnetization,
+                       uint8_t* decisions, double* d_omega_trace);
+
+/* Copy the current spins to host double[N][2]. */
+gfmc_status gfmc_get_spins(gfmc_t h, double* spins_out);
+
+/* Replace the spins (host double[N][2], copied) and the update counter
+ * (resume a saved chain, or follow another implementation through a tie). */
+gfmc_status gfmc_set_state(gfmc_t h, const double* spins, uint64_t update_counter);
+
+/* Read the update counter. */
+gfmc_status gfmc_get_counter(gfmc_t h, uint64_t* update_counter);
+
+/* Budget, in SM clock cycles, of every bounded device wait of h's launches
+ * (default 4e9, about two seconds); cycles > 0.  A wait that exceeds it ends
+ * the launch with GFMC_ETIMEOUT. */
+gfmc_status gfmc_set_wait_budget(gfmc_t h, int64_t cycles);
+
+/* Failure-injection hook for tests: when enable != 0, the next engine launch
+ * of h has CTA 0 withhold its completion flags, so that the CTAs reading its
+ * sites wait for a flag that nothing sets, exhaust their budget and end the
+ * launch with GFMC_ETIMEOUT (no device fault; h stays usable).  The hook
+ * clears itself after that launch.  It has an effect only when the chain runs
+ * on more than one CTA. */
+gfmc_status gfmc_inject_stall(gfmc_t h, int enable);
+
+/* Message of the last failed call on h (NULL: of the last failed create or of
+ * a call on an invalid handle in this thread).  Never NULL. */
+const char* gfmc_last_error(gfmc_t h);
+
+/* Free the handle and its device memory.  NULL is ignored. */
+void gfmc_destroy(gfmc_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GFMC_H */

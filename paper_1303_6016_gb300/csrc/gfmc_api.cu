@@ -1,0 +1,500 @@
+// gfmc_api.cu -- the C ABI of include/gfmc.h: argument checks, the per-chain
+// device state, the tile plan of the persistent engine, launches and errors.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/gfmc.h"
+#include "gfmc_internal.h"
+
+using gfmc::Params;
+
+struct gfmc_ctx {
+    int L = 0, N = 0, M = 0, precision = 0, kernel = 0, device = 0;
+    double t = 0, chem = 0, beta = 0, a = 0, lambda = 4.0;
+    uint64_t seed = 1;
+    uint32_t chain_id = 0;
+    cudaStream_t stream = nullptr;
+    uint64_t counter = 0;
+    long long budget = 4000000000LL;
+    int stall_next = 0;
+    Params P{};
+    std::vector<void*> allocs;
+    // growable output buffers of the sweep mode
+    long long trace_cap = 0;
+    unsigned char* d_dec = nullptr;
+    double* d_dom = nullptr;
+    double* d_maxinc = nullptr;
+    double* d_mag = nullptr;
+    unsigned long long* d_nacc = nullptr;
+    long long* d_nmag = nullptr;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+gfmc_status fail(gfmc_ctx* h, gfmc_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else g_err = buf;
+    return st;
+}
+
+gfmc_status cuda_fail(gfmc_ctx* h, cudaError_t e, const char* what)
+{
+    return fail(h, e == cudaErrorMemoryAllocation ? GFMC_ENOMEM : GFMC_ECUDA, "%s: %s (%s)", what,
+                cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+template <class T> cudaError_t dalloc(gfmc_ctx* h, T** p, size_t n)
+{
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
+    if (e != cudaSuccess) return e;
+    h->allocs.push_back(q);
+    *p = (T*)q;
+    return cudaSuccess;
+}
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+gfmc_status check_spins(gfmc_ctx* h, const double* spins, int N)
+{
+    if (!spins) return fail(h, GFMC_EINVAL, "spins is NULL");
+    for (int i = 0; i < N; ++i) {
+        const double th = spins[2 * i], ph = spins[2 * i + 1];
+        if (!std::isfinite(th) || !std::isfinite(ph) || th < 0.0 || th > M_PI)
+            return fail(h, GFMC_EINVAL, "spin %d has (theta, phi) = (%g, %g); theta must lie in [0, pi] "
+                        "and both must be finite", i, th, ph);
+    }
+    return GFMC_OK;
+}
+
+// Site tiles of the CTAs and, for each CTA, the other CTAs owning a neighbour
+// of one of its sites (the only CTAs its stencil reads and that read it).
+gfmc_status plan_tiles(gfmc_ctx* h, int ncta, std::vector<int>& start, std::vector<int>& ptr,
+                       std::vector<int>& idx)
+{
+    const int N = h->N, L = h->L;
+    start.resize(ncta + 1);
+    for (int c = 0; c <= ncta; ++c) start[c] = (int)(((long long)c * N) / ncta);
+    std::vector<int> owner(N);
+    for (int c = 0; c < ncta; ++c)
+        for (int i = start[c]; i < start[c + 1]; ++i) owner[i] = c;
+    ptr.assign(1, 0);
+    idx.clear();
+    std::vector<int> mark(ncta, -1);
+    for (int c = 0; c < ncta; ++c) {
+        for (int i = start[c]; i < start[c + 1]; ++i) {
+            const int x = i % L, y = (i / L) % L, z = i / (L * L);
+            const int nbs[6] = {(x + 1) % L + L * (y + L * z), (x + L - 1) % L + L * (y + L * z),
+                                x + L * ((y + 1) % L + L * z), x + L * ((y + L - 1) % L + L * z),
+                                x + L * (y + L * ((z + 1) % L)), x + L * (y + L * ((z + L - 1) % L))};
+            for (int d = 0; d < 6; ++d) {
+                const int oc = owner[nbs[d]];
+                if (oc != c && mark[oc] != c) {
+                    mark[oc] = c;
+                    idx.push_back(oc);
+                }
+            }
+        }
+        ptr.push_back((int)idx.size());
+        if (ptr[c + 1] - ptr[c] > gfmc::kMaxNbrCta)
+            return fail(h, GFMC_EINVAL, "tile %d depends on %d CTAs (limit %d); choose fewer CTAs", c,
+                        ptr[c + 1] - ptr[c], gfmc::kMaxNbrCta);
+    }
+    return GFMC_OK;
+}
+
+gfmc_status ensure_trace(gfmc_ctx* h, long long n)
+{
+    if (n <= h->trace_cap) return GFMC_OK;
+    long long cap = n < 1024 ? 1024 : n;
+    void* bufs[4] = {h->d_dec, h->d_dom, h->d_maxinc, h->d_mag};
+    for (void* b : bufs)
+        if (b) {
+            cudaFree(b);
+            for (auto& a : h->allocs)
+                if (a == b) a = nullptr;
+        }
+    h->d_dec = nullptr;
+    h->d_dom = h->d_maxinc = h->d_mag = nullptr;
+    cudaError_t e;
+    if ((e = dalloc(h, &h->d_dec, (size_t)cap)) != cudaSuccess ||
+        (e = dalloc(h, &h->d_dom, (size_t)cap)) != cudaSuccess ||
+        (e = dalloc(h, &h->d_maxinc, (size_t)cap)) != cudaSuccess ||
+        (e = dalloc(h, &h->d_mag, (size_t)(cap / h->N + 2))) != cudaSuccess) {
+        h->trace_cap = 0;
+        return cuda_fail(h, e, "allocating trace buffers");
+    }
+    h->trace_cap = cap;
+    return GFMC_OK;
+}
+
+// Run one engine launch and wait for it; translate the device error word.
+gfmc_status run_engine(gfmc_ctx* h, Params& P)
+{
+    cudaError_t e;
+    if ((e = cudaSetDevice(h->device)) != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    if ((e = cudaMemsetAsync(P.flags, 0, sizeof(unsigned) * P.ncta, h->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(P.bar, 0, sizeof(unsigned) * 2, h->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(P.err, 0, sizeof(int) * 4, h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "clearing engine control words");
+    P.budget = h->budget;
+    P.stall = h->stall_next;
+    h->stall_next = 0;
+    e = h->precision == GFMC_PREC_FP64 ? gfmc::launch_engine_f64(P, h->stream)
+                                        : gfmc::launch_engine_f32(P, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "launching the GFMC engine");
+    int err[4] = {0, 0, 0, 0};
+    if ((e = cudaMemcpyAsync(err, P.err, sizeof(err), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+        return cuda_fail(h, e, "reading the engine status");
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(h, e, "engine execution");
+    if (err[0] == gfmc::ERR_TIMEOUT)
+        return fail(h, GFMC_ETIMEOUT, "a device wait ran out of its budget (stage %d, CTA %d, aux %d)", err[1],
+                    err[2], err[3]);
+    if (err[0] == gfmc::ERR_NUMERIC)
+        return fail(h, GFMC_ENUMERIC, "non-finite d(z) at node %d (CTA %d)", err[3], err[2]);
+    if (err[0] != 0) return fail(h, GFMC_ECUDA, "engine error word %d", err[0]);
+    return GFMC_OK;
+}
+
+gfmc_status refresh_hoppings(gfmc_ctx* h)
+{
+    cudaError_t e = gfmc::launch_build_hoppings(h->P, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "building the bond table");
+    if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(h, e, "building the bond table");
+    return GFMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gfmc_default_options(gfmc_options* opt)
+{
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = GFMC_PREC_FP64;
+    opt->kernel = GFMC_KERNEL_JACKSON;
+    opt->lorentz_lambda = 4.0;
+    opt->spectral_scale = 0.0;
+    opt->seed = 1;
+    opt->chain_id = 0;
+    opt->stream = nullptr;
+    opt->num_ctas = 0;
+}
+
+gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double beta, int M,
+                        const gfmc_options* opt_in, gfmc_t* out)
+{
+    if (!out) return fail(nullptr, GFMC_EINVAL, "out is NULL");
+    *out = nullptr;
+    gfmc_options opt;
+    gfmc_default_options(&opt);
+    if (opt_in) opt = *opt_in;
+    if (L < 3 || L > gfmc::kMaxL) return fail(nullptr, GFMC_EINVAL, "L = %d outside [3, %d]", L, gfmc::kMaxL);
+    if (!std::isfinite(t) || t == 0.0) return fail(nullptr, GFMC_EINVAL, "t = %g must be finite and nonzero", t);
+    if (!std::isfinite(mu)) return fail(nullptr, GFMC_EINVAL, "mu must be finite");
+    if (!std::isfinite(beta) || !(beta > 0)) return fail(nullptr, GFMC_EINVAL, "beta = %g must be > 0", beta);
+    if (!is_pow2(M) || M < 16 || M > 4096)
+        return fail(nullptr, GFMC_EINVAL, "M = %d must be a power of two in [16, 4096]", M);
+    if (opt.precision != GFMC_PREC_FP64 && opt.precision != GFMC_PREC_FP32_MIXED)
+        return fail(nullptr, GFMC_EINVAL, "unknown precision %d", opt.precision);
+    if (opt.kernel != GFMC_KERNEL_JACKSON && opt.kernel != GFMC_KERNEL_LORENTZ)
+        return fail(nullptr, GFMC_EINVAL, "unknown kernel %d", opt.kernel);
+    const double a = opt.spectral_scale > 0 ? opt.spectral_scale : 6.05 * std::fabs(t);
+    if (!std::isfinite(a) || !(a > 6.0 * std::fabs(t)))
+        return fail(nullptr, GFMC_EINVAL, "spectral scale a = %g must exceed 6|t| = %g", a, 6.0 * std::fabs(t));
+    const double lam = opt.lorentz_lambda > 0 ? opt.lorentz_lambda : 4.0;
+    if (!std::isfinite(lam)) return fail(nullptr, GFMC_EINVAL, "lorentz_lambda must be finite");
+
+    gfmc_ctx* h = new (std::nothrow) gfmc_ctx;
+    if (!h) return fail(nullptr, GFMC_ENOMEM, "host allocation failed");
+    h->L = L;
+    h->N = L * L * L;
+    h->M = M;
+    h->t = t;
+    h->chem = mu;
+    h->beta = beta;
+    h->a = a;
+    h->lambda = lam;
+    h->precision = opt.precision;
+    h->kernel = opt.kernel;
+    h->seed = opt.seed;
+    h->chain_id = opt.chain_id;
+    h->stream = (cudaStream_t)opt.stream;
+
+    gfmc_status st = check_spins(h, spins, h->N);
+    if (st != GFMC_OK) {
+        g_err = h->err;
+        delete h;
+        return st;
+    }
+    auto bail = [&](gfmc_status s) {
+        g_err = h->err;
+        gfmc_destroy(h);
+        return s;
+    };
+    cudaError_t e;
+    if ((e = cudaGetDevice(&h->device)) != cudaSuccess) return bail(cuda_fail(h, e, "cudaGetDevice"));
+
+    int maxc = 0;
+    if ((e = gfmc::engine_max_ctas(h->precision, M, &maxc)) != cudaSuccess)
+        return bail(cuda_fail(h, e, "querying engine occupancy"));
+    const int N = h->N;
+    const int need = (N + gfmc::kThreads - 1) / gfmc::kThreads;
+    int ncta = opt.num_ctas;
+    if (ncta <= 0) {
+        ncta = N / 64;
+        if (ncta < need) ncta = need;
+        if (ncta > maxc) ncta = maxc;
+        if (ncta < 1) ncta = 1;
+    }
+    if (ncta < need || ncta > maxc || ncta > N)
+        return bail(fail(h, GFMC_EINVAL, "num_ctas = %d: need %d <= num_ctas <= min(%d resident, N = %d)", ncta, need,
+                         maxc, N));
+    std::vector<int> tstart, nptr, nidx;
+    if ((st = plan_tiles(h, ncta, tstart, nptr, nidx)) != GFMC_OK) return bail(st);
+
+    Params& P = h->P;
+    P.L = L;
+    P.N = N;
+    P.M = M;
+    P.nsteps = M / 2 - 1;
+    P.ncta = ncta;
+    P.t = t;
+    P.chem = mu;
+    P.beta = beta;
+    P.a = a;
+    P.seed = h->seed;
+    P.chain_id = h->chain_id;
+    const size_t vbytes = h->precision == GFMC_PREC_FP64 ? sizeof(double2) : sizeof(float2);
+    int *d_ts = nullptr, *d_np = nullptr, *d_ni = nullptr;
+    void* rb = nullptr;
+    if ((e = dalloc(h, &P.spins, 2 * (size_t)N)) != cudaSuccess ||
+        (e = dalloc(h, &P.hop64, 3 * (size_t)N)) != cudaSuccess ||
+        (e = dalloc(h, &P.hop32, 3 * (size_t)N)) != cudaSuccess ||
+        (e = dalloc(h, (char**)&rb, 2 * (size_t)gfmc::kVec * N * vbytes)) != cudaSuccess ||
+        (e = dalloc(h, &P.gker, (size_t)M)) != cudaSuccess || (e = dalloc(h, &P.twc, (size_t)M)) != cudaSuccess ||
+        (e = dalloc(h, &P.fftw, (size_t)M / 2)) != cudaSuccess ||
+        (e = dalloc(h, &P.sinth, (size_t)M)) != cudaSuccess || (e = dalloc(h, &P.cumw, (size_t)M)) != cudaSuccess ||
+        (e = dalloc(h, &P.partial, (size_t)P.nsteps * ncta * gfmc::kEntries)) != cudaSuccess ||
+        (e = dalloc(h, &P.fftin, 4 * (size_t)M)) != cudaSuccess ||
+        (e = dalloc(h, &P.gnode, 4 * (size_t)M)) != cudaSuccess ||
+        (e = dalloc(h, &P.qpart, 2 * (size_t)ncta)) != cudaSuccess ||
+        (e = dalloc(h, &P.magpart, 3 * (size_t)ncta)) != cudaSuccess ||
+        (e = dalloc(h, &P.mom_out, 49 * (size_t)M)) != cudaSuccess ||
+        (e = dalloc(h, &d_ts, tstart.size())) != cudaSuccess || (e = dalloc(h, &d_np, nptr.size())) != cudaSuccess ||
+        (e = dalloc(h, &d_ni, nidx.size() + 1)) != cudaSuccess ||
+        (e = dalloc(h, &P.flags, (size_t)ncta)) != cudaSuccess || (e = dalloc(h, &P.bar, 2)) != cudaSuccess ||
+        (e = dalloc(h, &P.err, 4)) != cudaSuccess || (e = dalloc(h, &h->d_nacc, 1)) != cudaSuccess ||
+        (e = dalloc(h, &h->d_nmag, 1)) != cudaSuccess)
+        return bail(cuda_fail(h, e, "allocating chain state"));
+    P.rbuf = rb;
+    P.tile_start = d_ts;
+    P.nbr_ptr = d_np;
+    P.nbr_idx = d_ni;
+    if ((e = cudaMemcpyAsync(P.spins, spins, sizeof(double) * 2 * N, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d_ts, tstart.data(), sizeof(int) * tstart.size(), cudaMemcpyHostToDevice, h->stream)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(d_np, nptr.data(), sizeof(int) * nptr.size(), cudaMemcpyHostToDevice, h->stream)) !=
+            cudaSuccess ||
+        (!nidx.empty() && (e = cudaMemcpyAsync(d_ni, nidx.data(), sizeof(int) * nidx.size(), cudaMemcpyHostToDevice,
+                                                h->stream)) != cudaSuccess))
+        return bail(cuda_fail(h, e, "uploading chain state"));
+    if ((e = gfmc::launch_setup_tables(P, h->kernel, h->lambda, h->stream)) != cudaSuccess)
+        return bail(cuda_fail(h, e, "building quadrature tables"));
+    if ((st = refresh_hoppings(h)) != GFMC_OK) return bail(st);
+    if ((st = ensure_trace(h, 1024)) != GFMC_OK) return bail(st);
+    *out = h;
+    return GFMC_OK;
+}
+
+gfmc_status gfmc_moments(gfmc_t h, int64_t site, double* mu_out)
+{
+    if (!h) return fail(nullptr, GFMC_EINVAL, "invalid handle");
+    if (site < 0 || site >= h->N) return fail(h, GFMC_EINVAL, "site %lld outside [0, %d)", (long long)site, h->N);
+    if (!mu_out) return fail(h, GFMC_EINVAL, "mu_out is NULL");
+    Params P = h->P;
+    P.mode = gfmc::MODE_MOMENTS;
+    P.site = site;
+    P.n_updates = 1;
+    P.domega_out = h->d_dom;
+    P.maxinc_out = h->d_maxinc;
+    P.dec_out = h->d_dec;
+    P.mag_out = h->d_mag;
+    P.n_acc = h->d_nacc;
+    P.n_mag = h->d_nmag;
+    gfmc_status st = run_engine(h, P);
+    if (st != GFMC_OK) return st;
+    cudaError_t e = cudaMemcpy(mu_out, P.mom_out, sizeof(double2) * 49 * (size_t)h->M, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "copying moments");
+    return GFMC_OK;
+}
+
+gfmc_status gfmc_delta_omega(gfmc_t h, int64_t site, double theta_new, double phi_new, double* d_omega)
+{
+    if (!h) return fail(nullptr, GFMC_EINVAL, "invalid handle");
+    if (site < 0 || site >= h->N) return fail(h, GFMC_EINVAL, "site %lld outside [0, %d)", (long long)site, h->N);
+    if (!d_omega) return fail(h, GFMC_EINVAL, "d_omega is NULL");
+    if (!std::isfinite(theta_new) || !std::isfinite(phi_new) || theta_new < 0.0 || theta_new > M_PI)
+        return fail(h, GFMC_EINVAL, "proposal (%g, %g): theta must lie in [0, pi], both finite", theta_new, phi_new);
+    Params P = h->P;
+    P.mode = gfmc::MODE_DELTA;
+    P.site = site;
+    P.theta_new = theta_new;
+    P.phi_new = phi_new;
+    P.n_updates = 1;
+    P.domega_out = h->d_dom;
+    P.maxinc_out = h->d_maxinc;
+    P.dec_out = h->d_dec;
+    P.mag_out = h->d_mag;
+    P.n_acc = h->d_nacc;
+    P.n_mag = h->d_nmag;
+    gfmc_status st = run_engine(h, P);
+    if (st != GFMC_OK) return st;
+    cudaError_t e = cudaMemcpy(d_omega, h->d_dom, sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "copying Delta Omega");
+    return GFMC_OK;
+}
+
+gfmc_status gfmc_updates(gfmc_t h, int64_t n_updates, uint64_t* n_accepted, uint8_t* decisions,
+                         double* d_omega_trace, double* magnetization, int64_t* n_mag)
+{
+    if (!h) return fail(nullptr, GFMC_EINVAL, "invalid handle");
+    if (n_updates < 0) return fail(h, GFMC_EINVAL, "n_updates = %lld < 0", (long long)n_updates);
+    uint64_t total_acc = 0;
+    int64_t total_mag = 0;
+    // Launch in chunks of at most one sweep so a single launch stays short.
+    int64_t done = 0;
+    while (done < n_updates) {
+        const int64_t left = n_updates - done;
+        const int64_t chunk = left < h->N ? left : h->N;
+        gfmc_status st = ensure_trace(h, chunk);
+        if (st != GFMC_OK) return st;
+        Params P = h->P;
+        P.mode = gfmc::MODE_SWEEP;
+        P.upd0 = h->counter;
+        P.n_updates = chunk;
+        P.dec_out = h->d_dec;
+        P.domega_out = h->d_dom;
+        P.maxinc_out = h->d_maxinc;
+        P.mag_out = h->d_mag;
+        P.n_acc = h->d_nacc;
+        P.n_mag = h->d_nmag;
+        st = run_engine(h, P);
+        if (st != GFMC_OK) return st;
+        unsigned long long nacc = 0;
+        long long nm = 0;
+        cudaError_t e;
+        if ((e = cudaMemcpy(&nacc, h->d_nacc, sizeof(nacc), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+            (e = cudaMemcpy(&nm, h->d_nmag, sizeof(nm), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(h, e, "reading sweep counters");
+        if (decisions &&
+            (e = cudaMemcpy(decisions + done, h->d_dec, (size_t)chunk, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(h, e, "copying decisions");
+        if (d_omega_trace && (e = cudaMemcpy(d_omega_trace + done, h->d_dom, sizeof(double) * chunk,
+                                             cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(h, e, "copying the Delta Omega trace");
+        if (magnetization && nm > 0 &&
+            (e = cudaMemcpy(magnetization + total_mag, h->d_mag, sizeof(double) * nm, cudaMemcpyDeviceToHost)) !=
+                cudaSuccess)
+            return cuda_fail(h, e, "copying magnetisations");
+        total_acc += nacc;
+        total_mag += nm;
+        h->counter += (uint64_t)chunk;
+        done += chunk;
+    }
+    if (n_accepted) *n_accepted = total_acc;
+    if (n_mag) *n_mag = total_mag;
+    return GFMC_OK;
+}
+
+gfmc_status gfmc_sweep(gfmc_t h, int n_sweeps, uint64_t* n_accepted, double* magnetization, uint8_t* decisions,
+                       double* d_omega_trace)
+{
+    if (!h) return fail(nullptr, GFMC_EINVAL, "invalid handle");
+    if (n_sweeps < 0) return fail(h, GFMC_EINVAL, "n_sweeps = %d < 0", n_sweeps);
+    if (h->counter % (uint64_t)h->N != 0)
+        return fail(h, GFMC_EINVAL, "the chain is inside a sweep (counter %llu); use gfmc_updates",
+                    (unsigned long long)h->counter);
+    return gfmc_updates(h, (int64_t)n_sweeps * h->N, n_accepted, decisions, d_omega_trace, magnetization, nullptr);
+}
+
+gfmc_status gfmc_get_spins(gfmc_t h, double* spins_out)
+{
+    if (!h) return fail(nullptr, GFMC_EINVAL, "invalid handle");
+    if (!spins_out) return fail(h, GFMC_EINVAL, "spins_out is NULL");
+    cudaError_t e = cudaMemcpyAsync(spins_out, h->P.spins, sizeof(double) * 2 * h->N, cudaMemcpyDeviceToHost,
+                                    h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "copying spins");
+    return GFMC_OK;
+}
+
+gfmc_status gfmc_set_state(gfmc_t h, const double* spins, uint64_t update_counter)
+{
+    if (!h) return fail(nullptr, GFMC_EINVAL, "invalid handle");
+    gfmc_status st = check_spins(h, spins, h->N);
+    if (st != GFMC_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(h->P.spins, spins, sizeof(double) * 2 * h->N, cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "uploading spins");
+    if ((st = refresh_hoppings(h)) != GFMC_OK) return st;
+    h->counter = update_counter;
+    return GFMC_OK;
+}
+
+gfmc_status gfmc_get_counter(gfmc_t h, uint64_t* update_counter)
+{
+    if (!h) return fail(nullptr, GFMC_EINVAL, "invalid handle");
+    if (!update_counter) return fail(h, GFMC_EINVAL, "update_counter is NULL");
+    *update_counter = h->counter;
+    return GFMC_OK;
+}
+
+gfmc_status gfmc_set_wait_budget(gfmc_t h, int64_t cycles)
+{
+    if (!h) return fail(nullptr, GFMC_EINVAL, "invalid handle");
+    if (cycles <= 0) return fail(h, GFMC_EINVAL, "wait budget %lld must be > 0", (long long)cycles);
+    h->budget = cycles;
+    return GFMC_OK;
+}
+
+gfmc_status gfmc_inject_stall(gfmc_t h, int enable)
+{
+    if (!h) return fail(nullptr, GFMC_EINVAL, "invalid handle");
+    h->stall_next = enable != 0;
+    return GFMC_OK;
+}
+
+const char* gfmc_last_error(gfmc_t h)
+{
+    if (h) return h->err.c_str();
+    return g_err.c_str();
+}
+
+void gfmc_destroy(gfmc_t h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    for (void* p : h->allocs)
+        if (p) cudaFree(p);
+    delete h;
+}
+
+}  // extern "C"

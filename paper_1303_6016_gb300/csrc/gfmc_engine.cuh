@@ -1,0 +1,764 @@
+// gfmc_engine.cuh -- the persistent GFMC update engine for sm_103a.
+//
+// One cooperative launch runs a sequence of single-spin updates of one chain
+// (arXiv:1303.6016, Algorithm 1 and Sec. 2.2) with every CTA resident:
+//
+//   per update (site o):
+//     set-up      local sites, Philox draw, Delta~ coefficients (every CTA)
+//     phase 0     r_0 = e_{l_v}, r_1 = Htilde e_{l_v} on the CTA's own sites
+//     steps m     r_{m+1} = 2 Htilde r_m - r_{m-1} for the 7 vectors, matrix
+//                 free on the periodic 6-neighbour stencil (Eq. recursive),
+//                 fused with the 2 x 28 Gram dot products <r_m^j|r_m^k>,
+//                 <r_m^j|r_{m+1}^k> (Eq. mu2); a CTA only waits for the CTAs
+//                 whose sites its stencil reads (release/acquire flags)
+//     reduce      per-CTA Gram partials -> 7x7 moments mu_n (doubling) ->
+//                 the four real sequences <V|T_n|V>, V = o, v, o+v, o+iv,
+//                 damped by g_n and twisted by e^{-i n pi/2M} (Eq. mu_to_mu_tilde)
+//     FFT         M-point FFT of each sequence (Eq. green_fft), node mapping
+//                 chi_{2j} = gamma_j, chi_{2j+1} = conj(gamma_{M-j-1}), and
+//                 G_V(w_k) = (2i / sin theta_k) chi_k (Eq. green_short)
+//     quadrature  mixed elements -> G_ov, G_vo; d_k (Eq. d_z_green);
+//                 continuous Im log d_k; Delta Omega by the Chebyshev-Gauss
+//                 rule on the same nodes (Eq. d_seff2)
+//     decision    exp(-beta Delta Omega) > u (Algorithm 1), spin and the six
+//                 bonds of o patched on acceptance (H <- H + Delta)
+//
+// R is the arithmetic type of the recursion vectors and the stencil (double
+// for the FP64 path, float for the mixed path).  Products for the dot
+// products are formed in R and summed in R across a warp; everything above
+// the warp (CTA sums, cross-CTA sums, moments, FFT, determinant, quadrature)
+// is FP64 for both paths.
+//
+// Every spin-wait is bounded by p.budget clock cycles; on expiry the kernel
+// records GFMC_ETIMEOUT in p.err and all CTAs leave at their next wait.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "gfmc_internal.h"
+
+namespace gfmc {
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+
+template <class R> struct Cx;
+template <> struct Cx<double> { using T = double2; };
+template <> struct Cx<float> { using T = float2; };
+
+template <class T> __device__ __forceinline__ T c_make(decltype(T{}.x) x, decltype(T{}.x) y)
+{
+    T r;
+    r.x = x;
+    r.y = y;
+    return r;
+}
+
+// acc += h * r (complex), four fused multiply-adds
+template <class T> __device__ __forceinline__ void c_fma(T& acc, T h, T r)
+{
+    acc.x = fma(h.x, r.x, acc.x);
+    acc.x = fma(-h.y, r.y, acc.x);
+    acc.y = fma(h.x, r.y, acc.y);
+    acc.y = fma(h.y, r.x, acc.y);
+}
+
+__device__ __forceinline__ double2 dmul(double2 a, double2 b)
+{
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 dadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 dsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 dconj(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 dscale(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+
+__device__ __forceinline__ double2 ldcg2(const double2* p) { return __ldcg(p); }
+__device__ __forceinline__ float2 ldcg2(const float2* p) { return __ldcg(p); }
+__device__ __forceinline__ void stcg2(double2* p, double2 v) { __stcg(p, v); }
+__device__ __forceinline__ void stcg2(float2* p, float2 v) { __stcg(p, v); }
+
+// upper-triangle pair p (row-major, j <= k) of the 7x7 block
+__host__ __device__ constexpr int pair_j(int p)
+{
+    int j = 0;
+    while (p >= 7 - j) {
+        p -= 7 - j;
+        ++j;
+    }
+    return j;
+}
+__host__ __device__ constexpr int pair_k(int p)
+{
+    int j = 0;
+    while (p >= 7 - j) {
+        p -= 7 - j;
+        ++j;
+    }
+    return j + p;
+}
+__host__ __device__ constexpr int pair_of(int j, int k)
+{
+    return j * 7 - j * (j - 1) / 2 + (k - j);
+}
+
+// ---------------------------------------------------------------------------
+// memory ordering and bounded waits
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* a)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* a, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_relaxed_s32(const int* a)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void set_error(const Params& p, int code, int where, int aux)
+{
+    if (atomicCAS(p.err, 0, code) == 0) {
+        p.err[1] = where;
+        p.err[2] = (int)blockIdx.x;
+        p.err[3] = aux;
+        __threadfence();
+    }
+}
+
+// All CTAs of the launch meet here.  Returns false (in every thread) when an
+// error has been recorded by any CTA or this CTA's wait ran out.
+__device__ inline bool grid_barrier(const Params& p, int where)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        if (p.ncta > 1) {
+            unsigned gen = ld_acquire_u32(&p.bar[1]);
+            __threadfence();
+            unsigned prev = atomicAdd(&p.bar[0], 1u);
+            if (prev == (unsigned)p.ncta - 1u) {
+                atomicExch(&p.bar[0], 0u);
+                __threadfence();
+                st_release_u32(&p.bar[1], gen + 1u);
+            } else {
+                long long t0 = clock64();
+                while (ld_acquire_u32(&p.bar[1]) == gen) {
+                    if (ld_relaxed_s32(p.err) != 0) break;
+                    if (clock64() - t0 > p.budget) {
+                        set_error(p, ERR_TIMEOUT, where, 0);
+                        break;
+                    }
+                }
+            }
+            __threadfence();
+        }
+        if (ld_relaxed_s32(p.err) != 0) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Wait until every CTA whose sites this CTA's stencil reads (and which reads
+// this CTA's sites) has completed `target` stencil phases.
+__device__ inline bool wait_neighbours(const Params& p, int cta, unsigned target, int where)
+{
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) s_ok = 1;
+    __syncthreads();
+    if (p.ncta > 1) {
+        const int b = p.nbr_ptr[cta], e = p.nbr_ptr[cta + 1];
+        for (int q = b + (int)threadIdx.x; q < e; q += blockDim.x) {
+            const unsigned* f = &p.flags[p.nbr_idx[q]];
+            long long t0 = clock64();
+            while ((int)(ld_acquire_u32(f) - target) < 0) {
+                if (ld_relaxed_s32(p.err) != 0) {
+                    s_ok = 0;
+                    break;
+                }
+                if (clock64() - t0 > p.budget) {
+                    set_error(p, ERR_TIMEOUT, where, (int)target);
+                    s_ok = 0;
+                    break;
+                }
+            }
+            __threadfence();
+        }
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ void publish(const Params& p, int cta, unsigned value)
+{
+    __syncthreads();
+    if (p.ncta > 1 && threadIdx.x == 0 && !(p.stall && cta == 0)) {
+        __threadfence();
+        st_release_u32(&p.flags[cta], value);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// reductions
+// ---------------------------------------------------------------------------
+
+// Butterfly reduce-scatter of 32 values over the 32 lanes of a warp: on
+// return, lane l holds the warp-wide sum of value index l.
+template <class R> __device__ __forceinline__ R warp_reduce_scatter32(R (&v)[32], int lane)
+{
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const bool up = lane & 16;
+        R send = up ? v[i] : v[i + 16];
+        R keep = up ? v[i + 16] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const bool up = lane & 8;
+        R send = up ? v[i] : v[i + 8];
+        R keep = up ? v[i + 8] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool up = lane & 4;
+        R send = up ? v[i] : v[i + 4];
+        R keep = up ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool up = lane & 2;
+        R send = up ? v[i] : v[i + 2];
+        R keep = up ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+    }
+    {
+        const bool up = lane & 1;
+        R send = up ? v[0] : v[1];
+        R keep = up ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 1);
+    }
+    return v[0];
+}
+
+// Deterministic CTA-wide sum (and max) of one double per thread.
+__device__ __forceinline__ void block_sum_max(double s, double mx, double* out_s, double* out_m)
+{
+    __shared__ double sh_s[kWarps], sh_m[kWarps];
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        sh_s[warp] = s;
+        sh_m[warp] = mx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < kWarps; ++w) {
+            a += sh_s[w];
+            b = fmax(b, sh_m[w]);
+        }
+        *out_s = a;
+        *out_m = b;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// lattice, spins, random numbers
+// ---------------------------------------------------------------------------
+
+// neighbour of site i in direction d: 0 = +x, 1 = -x, 2 = +y, 3 = -y, 4 = +z, 5 = -z
+__device__ __forceinline__ int nbr_site(int i, int d, int L)
+{
+    const int LL = L * L;
+    const int x = i % L, y = (i / L) % L, z = i / LL;
+    switch (d) {
+        case 0: return (x == L - 1) ? i - (L - 1) : i + 1;
+        case 1: return (x == 0) ? i + (L - 1) : i - 1;
+        case 2: return (y == L - 1) ? i - (L - 1) * L : i + L;
+        case 3: return (y == 0) ? i + (L - 1) * L : i - L;
+        case 4: return (z == L - 1) ? i - (L - 1) * LL : i + LL;
+        default: return (z == 0) ? i + (L - 1) * LL : i - LL;
+    }
+}
+
+// spinor chi = (cos(th/2), e^{i ph} sin(th/2)) as (c, sx, sy)
+__device__ __forceinline__ void spinor3(double th, double ph, double& c, double& sx, double& sy)
+{
+    double sh, ch, sp, cp;
+    sincos(0.5 * th, &sh, &ch);
+    sincos(ph, &sp, &cp);
+    c = ch;
+    sx = cp * sh;
+    sy = sp * sh;
+}
+
+// <chi_a|chi_b>
+__device__ __forceinline__ double2 overlap3(double ca, double xa, double ya, double cb, double xb,
+                                            double yb)
+{
+    return make_double2(ca * cb + (xa * xb + ya * yb), xa * yb - ya * xb);
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k.x += 0x9E3779B9u;
+            k.y += 0xBB67AE85u;
+        }
+        const unsigned hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const unsigned hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// Proposal (uniform on the sphere) and Metropolis uniform of update `upd`.
+__device__ __forceinline__ void draw_update(unsigned long long seed, unsigned chain, unsigned long long upd,
+                                            double& th, double& ph, double& u)
+{
+    const uint2 key = make_uint2((unsigned)seed, (unsigned)(seed >> 32) ^ chain);
+    const uint4 x = philox4x32_10(make_uint4((unsigned)upd, (unsigned)(upd >> 32), 0u, 0u), key);
+    const double u1 = (double)x.x * 0x1p-32;
+    const double u2 = (double)x.y * 0x1p-32;
+    th = acos(1.0 - 2.0 * u1);
+    ph = 2.0 * CUDART_PI * u2;
+    u = ((double)(x.z >> 5) * 67108864.0 + (double)(x.w >> 6)) * 0x1p-53;
+}
+
+// Htilde_{i, nbr(i, d)} from the bond table (hop[alpha][i] = Htilde_{i, i+e_alpha}).
+template <class T> __device__ __forceinline__ T hop_of(const T* hop, int N, int i, int d, int nb)
+{
+    const int alpha = d >> 1;
+    if ((d & 1) == 0) return ldcg2(hop + (size_t)alpha * N + i);
+    T h = ldcg2(hop + (size_t)alpha * N + nb);
+    h.y = -h.y;
+    return h;
+}
+
+// ---------------------------------------------------------------------------
+// combined moments <V|T_n|V> for V = o, v, o+v, o+iv from the 28 upper pairs
+// of mu_n and |v> = sum_k c_k |l_k> (c_0 = 0)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double combined_moment(int V, const double2* mu, const double2* c)
+{
+    const double moo = mu[0].x;
+    double2 X = make_double2(0.0, 0.0);  // <o|T|v> = sum_k c_k mu^{0k}
+#pragma unroll
+    for (int k = 1; k < 7; ++k) X = dadd(X, dmul(c[k], mu[k]));
+    double vv = 0.0;  // <v|T|v>
+#pragma unroll
+    for (int j = 1; j < 7; ++j) {
+        vv += (c[j].x * c[j].x + c[j].y * c[j].y) * mu[pair_of(j, j)].x;
+#pragma unroll
+        for (int k = j + 1; k < 7; ++k) vv += 2.0 * dmul(dmul(dconj(c[j]), c[k]), mu[pair_of(j, k)]).x;
+    }
+    switch (V) {
+        case 0: return moo;
+        case 1: return vv;
+        case 2: return moo + vv + 2.0 * X.x;
+        default: return moo + vv - 2.0 * X.y;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gram products of one site, 14 complex entries per chunk, compile-time indexed
+// ---------------------------------------------------------------------------
+template <class R, class R2, int C, int Q>
+__device__ __forceinline__ void gram_fill(const R2 (&rc)[kVec], const R2 (&rn)[kVec], R (&vals)[32])
+{
+    constexpr int e = 14 * C + Q;
+    constexpr int g = e / kPairs, pp = e % kPairs;
+    constexpr int j = pair_j(pp), k = pair_k(pp);
+    const R2 x = rc[j];
+    const R2 y = (g == 0) ? rc[k] : rn[k];
+    vals[2 * Q] = fma(x.x, y.x, x.y * y.y);
+    vals[2 * Q + 1] = (g == 0 && j == k) ? (R)0 : fma(x.x, y.y, -(x.y * y.x));
+    if constexpr (Q + 1 < 14) gram_fill<R, R2, C, Q + 1>(rc, rn, vals);
+}
+
+// conj(x_j) y_k for the 14 entries of chunk C, summed over the warp; lane l < 28
+// stores real component l of the chunk into dst[28 C + l].
+template <class R, class R2, int C>
+__device__ __forceinline__ void gram_chunk_reduce(const R2 (&rc)[kVec], const R2 (&rn)[kVec], int lane, double* dst)
+{
+    R vals[32];
+    gram_fill<R, R2, C, 0>(rc, rn, vals);
+#pragma unroll
+    for (int qq = 28; qq < 32; ++qq) vals[qq] = (R)0;
+    const R s = warp_reduce_scatter32(vals, lane);
+    if (lane < 28) dst[28 * C + lane] = (double)s;
+}
+
+// ---------------------------------------------------------------------------
+// the engine
+// ---------------------------------------------------------------------------
+
+template <class R>
+__global__ void __launch_bounds__(kThreads, 1) gfmc_engine(const Params p)
+{
+    using R2 = typename Cx<R>::T;
+    extern __shared__ double2 dyn[];  // FFT buffer / phases (M double2)
+    __shared__ double red[kWarps][kEntries];
+    __shared__ double2 s_mu2[kWarps][2][kPairs];
+    __shared__ double2 s_mu1[kPairs];
+    __shared__ double2 s_c[kVec];
+    __shared__ int s_loc[kVec];
+    __shared__ double s_draw[3];
+    __shared__ double s_dom;
+    __shared__ int s_acc;
+
+    const int cta = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int N = p.N, L = p.L, M = p.M;
+    const int s0 = p.tile_start[cta], s1 = p.tile_start[cta + 1];
+    const int i = s0 + tid;
+    const bool active = i < s1;
+    const R2* hop = nullptr;
+    if constexpr (sizeof(R) == 8) hop = (const R2*)p.hop64; else hop = (const R2*)p.hop32;
+
+    int nb[6];
+#pragma unroll
+    for (int d = 0; d < 6; ++d) nb[d] = active ? nbr_site(i, d, L) : 0;
+
+    R2* buf0 = (R2*)p.rbuf;
+    R2* buf1 = buf0 + (size_t)kVec * N;
+    const long long nupd = (p.mode == MODE_SWEEP) ? p.n_updates : 1;
+    unsigned phase = 0;
+    long long nmag = 0;
+    unsigned long long nacc = 0;
+
+    for (long long q = 0; q < nupd; ++q) {
+        const unsigned long long upd = p.upd0 + (unsigned long long)q;
+        const int o = (p.mode == MODE_SWEEP) ? (int)(upd % (unsigned long long)N) : (int)p.site;
+
+        // ---- set-up: local sites, proposal, Delta~ coefficients ----
+        if (tid == 0) {
+            s_loc[0] = o;
+            for (int d = 0; d < 6; ++d) s_loc[d + 1] = nbr_site(o, d, L);
+            double th = 0.0, ph = 0.0, u = 0.0;
+            if (p.mode == MODE_SWEEP) draw_update(p.seed, p.chain_id, upd, th, ph, u);
+            else if (p.mode == MODE_DELTA) { th = p.theta_new; ph = p.phi_new; }
+            s_draw[0] = th;
+            s_draw[1] = ph;
+            s_draw[2] = u;
+        }
+        __syncthreads();
+        if (tid < kVec) {
+            double2 cv = make_double2(0.0, 0.0);
+            if (tid > 0 && p.mode != MODE_MOMENTS) {
+                // Delta~_{l_j,o} = (H'_{j,o} - H_{j,o}) / a = -t (<chi_j|chi'_o> - <chi_j|chi_o>) / a
+                const int j = s_loc[tid];
+                double cj, xj, yj, co, xo, yo, cn, xn, yn;
+                spinor3(__ldcg(p.spins + 2 * j), __ldcg(p.spins + 2 * j + 1), cj, xj, yj);
+                spinor3(__ldcg(p.spins + 2 * o), __ldcg(p.spins + 2 * o + 1), co, xo, yo);
+                spinor3(s_draw[0], s_draw[1], cn, xn, yn);
+                const double2 on = overlap3(cj, xj, yj, cn, xn, yn);
+                const double2 oo = overlap3(cj, xj, yj, co, xo, yo);
+                cv = make_double2((-p.t * on.x + p.t * oo.x) / p.a, (-p.t * on.y + p.t * oo.y) / p.a);
+            }
+            s_c[tid] = cv;
+        }
+        R2 h[6];
+#pragma unroll
+        for (int d = 0; d < 6; ++d) h[d] = active ? hop_of(hop, N, i, d, nb[d]) : c_make<R2>(0, 0);
+        __syncthreads();
+
+        // ---- phase 0: r_0 = e_{l_v}, r_1 = Htilde e_{l_v} ----
+        if (active) {
+#pragma unroll
+            for (int v = 0; v < kVec; ++v) {
+                const int lv = s_loc[v];
+                R2 r0 = c_make<R2>(i == lv ? (R)1 : (R)0, (R)0);
+                R2 r1 = c_make<R2>(0, 0);
+#pragma unroll
+                for (int d = 0; d < 6; ++d)
+                    if (nb[d] == lv) {
+                        r1.x += h[d].x;
+                        r1.y += h[d].y;
+                    }
+                stcg2(buf0 + (size_t)v * N + i, r0);
+                stcg2(buf1 + (size_t)v * N + i, r1);
+            }
+        }
+        publish(p, cta, phase + 1);
+
+        // ---- steps m = 1 .. M/2-1: r_{m+1} = 2 Htilde r_m - r_{m-1} and the Gram sums ----
+        for (int m = 1; m <= p.nsteps; ++m) {
+            if (!wait_neighbours(p, cta, phase + (unsigned)m, 100 + m)) return;
+            R2* cur = (m & 1) ? buf1 : buf0;
+            R2* prv = (m & 1) ? buf0 : buf1;
+            R2 rc[kVec], rn[kVec];
+            if (active) {
+#pragma unroll
+                for (int v = 0; v < kVec; ++v) {
+                    const R2* cv = cur + (size_t)v * N;
+                    R2 acc = c_make<R2>(0, 0);
+#pragma unroll
+                    for (int d = 0; d < 6; ++d) c_fma(acc, h[d], ldcg2(cv + nb[d]));
+                    const R2 rp = ldcg2(prv + (size_t)v * N + i);
+                    rc[v] = ldcg2(cv + i);
+                    rn[v] = c_make<R2>(fma((R)2, acc.x, -rp.x), fma((R)2, acc.y, -rp.y));
+                    if (m < p.nsteps) stcg2(prv + (size_t)v * N + i, rn[v]);
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < kVec; ++v) {
+                    rc[v] = c_make<R2>(0, 0);
+                    rn[v] = c_make<R2>(0, 0);
+                }
+            }
+            // Gram entries e = 0..55: e < 28 -> conj(r_m^j) r_m^k, else conj(r_m^j) r_{m+1}^k,
+            // (j, k) the upper pair e mod 28; processed in 4 chunks of 14 complex values.
+            gram_chunk_reduce<R, R2, 0>(rc, rn, lane, red[warp]);
+            gram_chunk_reduce<R, R2, 1>(rc, rn, lane, red[warp]);
+            gram_chunk_reduce<R, R2, 2>(rc, rn, lane, red[warp]);
+            gram_chunk_reduce<R, R2, 3>(rc, rn, lane, red[warp]);
+            __syncthreads();
+            if (tid < kEntries) {
+                double s = 0.0;
+#pragma unroll
+                for (int w = 0; w < kWarps; ++w) s += red[w][tid];
+                p.partial[((size_t)(m - 1) * p.ncta + cta) * kEntries + tid] = s;
+            }
+            publish(p, cta, phase + (unsigned)m + 1u);
+        }
+        phase += (unsigned)p.nsteps + 1u;
+        if (!grid_barrier(p, 1)) return;
+
+        // ---- reduce: partial Gram sums -> mu_n -> damped, twisted combined sequences ----
+        if (tid < kPairs) {
+            // mu_1^{jk} = Htilde_{l_j, l_k}
+            const int j = pair_j(tid), k = pair_k(tid);
+            const int lj = s_loc[j], lk = s_loc[k];
+            double2 s = make_double2(0.0, 0.0);
+            for (int d = 0; d < 6; ++d) {
+                const int nbj = nbr_site(lj, d, L);
+                if (nbj == lk) s = dadd(s, hop_of(p.hop64, N, lj, d, nbj));
+            }
+            s_mu1[tid] = s;
+        }
+        __syncthreads();
+        {
+            const int gw = cta * kWarps + warp, TW = p.ncta * kWarps;
+            for (int item = gw; item <= p.nsteps; item += TW) {
+                if (item == 0) {
+                    if (lane < kPairs) {
+                        const bool diag = pair_j(lane) == pair_k(lane);
+                        s_mu2[warp][0][lane] = make_double2(diag ? 1.0 : 0.0, 0.0);
+                        s_mu2[warp][1][lane] = s_mu1[lane];
+                    }
+                } else {
+                    const double* src = p.partial + (size_t)(item - 1) * p.ncta * kEntries;
+                    for (int e = lane; e < kEntries; e += 32) {
+                        double s = 0.0;
+                        for (int c = 0; c < p.ncta; ++c) s += __ldcg(src + (size_t)c * kEntries + e);
+                        red[warp][e] = s;
+                    }
+                    __syncwarp();
+                    if (lane < kPairs) {
+                        const bool diag = pair_j(lane) == pair_k(lane);
+                        const double2 e1 = make_double2(red[warp][2 * lane], red[warp][2 * lane + 1]);
+                        const double2 e2 = make_double2(red[warp][56 + 2 * lane], red[warp][57 + 2 * lane]);
+                        s_mu2[warp][0][lane] = make_double2(2.0 * e1.x - (diag ? 1.0 : 0.0), 2.0 * e1.y);
+                        s_mu2[warp][1][lane] = dsub(dscale(2.0, e2), s_mu1[lane]);
+                    }
+                }
+                __syncwarp();
+                const int n0 = 2 * item;
+                if (p.mode == MODE_MOMENTS) {
+                    for (int idx = lane; idx < 98; idx += 32) {
+                        const int sgn = idx / 49, jk = idx % 49, j = jk / 7, k = jk % 7;
+                        double2 v = (j <= k) ? s_mu2[warp][sgn][pair_of(j, k)] : dconj(s_mu2[warp][sgn][pair_of(k, j)]);
+                        p.mom_out[(size_t)jk * M + n0 + sgn] = v;
+                    }
+                } else if (lane < 8) {
+                    const int sgn = lane >> 2, V = lane & 3, n = n0 + sgn;
+                    const double val = combined_moment(V, s_mu2[warp][sgn], s_c);
+                    const double gn = __ldcg(p.gker + n) * (n == 0 ? 0.5 : 1.0);
+                    p.fftin[(size_t)V * M + n] = dscale(gn * val, __ldcg(p.twc + n));
+                }
+                __syncwarp();
+            }
+        }
+        if (!grid_barrier(p, 2)) return;
+        if (p.mode == MODE_MOMENTS) return;
+
+        // ---- FFT of the four sequences and G_V at the nodes ----
+        {
+            int lg = 0;
+            while ((1 << lg) < M) ++lg;
+            for (int V = cta; V < 4; V += p.ncta) {
+                double2* x = dyn;
+                for (int n = tid; n < M; n += kThreads)
+                    x[__brev((unsigned)n) >> (32 - lg)] = __ldcg(p.fftin + (size_t)V * M + n);
+                __syncthreads();
+                for (int half = 1, lh = 0; half < M; half <<= 1, ++lh) {
+                    const int tstride = M >> (lh + 1);
+                    for (int b = tid; b < (M >> 1); b += kThreads) {
+                        const int grp = b >> lh, pos = b & (half - 1);
+                        const int i0 = (grp << (lh + 1)) + pos, i1 = i0 + half;
+                        const double2 w = __ldcg(p.fftw + (size_t)pos * tstride);
+                        const double2 u = x[i0], t = dmul(w, x[i1]);
+                        x[i0] = dadd(u, t);
+                        x[i1] = dsub(u, t);
+                    }
+                    __syncthreads();
+                }
+                for (int k = tid; k < M; k += kThreads) {
+                    const double2 chi = (k & 1) ? dconj(x[M - 1 - (k >> 1)]) : x[k >> 1];
+                    const double sc = 2.0 / __ldcg(p.sinth + k);
+                    p.gnode[(size_t)V * M + k] = make_double2(-sc * chi.y, sc * chi.x);
+                }
+                __syncthreads();
+            }
+        }
+        if (!grid_barrier(p, 3)) return;
+
+        // ---- d_k, continuous phase, Chebyshev-Gauss partial sums ----
+        {
+            const int k0 = (int)(((long long)cta * M) / p.ncta);
+            const int k1 = (int)(((long long)(cta + 1) * M) / p.ncta);
+            const int kend = min(k1 + 1, M);
+            double* sarg = (double*)dyn;
+            for (int k = k0 + tid; k < kend; k += kThreads) {
+                const double2 Goo = __ldcg(p.gnode + k), Gvv = __ldcg(p.gnode + (size_t)M + k);
+                const double2 Gp = __ldcg(p.gnode + 2 * (size_t)M + k), Gq = __ldcg(p.gnode + 3 * (size_t)M + k);
+                const double2 Am = dsub(dsub(Gp, Goo), Gvv);  // G_ov + G_vo
+                const double2 Bm = dsub(dsub(Gq, Goo), Gvv);  // i (G_ov - G_vo)
+                // G_ov = (A - iB)/2, G_vo = (A + iB)/2
+                const double2 Gov = make_double2(0.5 * (Am.x + Bm.y), 0.5 * (Am.y - Bm.x));
+                const double2 Gvo = make_double2(0.5 * (Am.x - Bm.y), 0.5 * (Am.y + Bm.x));
+                const double2 d = dsub(dmul(make_double2(1.0 + Gov.x, Gov.y), make_double2(1.0 + Gvo.x, Gvo.y)),
+                                       dmul(Goo, Gvv));
+                if (!isfinite(d.x) || !isfinite(d.y)) set_error(p, ERR_NUMERIC, 40, k);
+                sarg[k - k0] = atan2(d.y, d.x);
+            }
+            __syncthreads();
+            double part = 0.0, mx = 0.0;
+            for (int k = k0 + tid; k < k1; k += kThreads) {
+                double inc;
+                if (k == M - 1) {
+                    inc = sarg[k - k0];
+                } else {
+                    inc = sarg[k - k0] - sarg[k + 1 - k0];
+                    if (inc > CUDART_PI) inc -= 2.0 * CUDART_PI;
+                    else if (inc <= -CUDART_PI) inc += 2.0 * CUDART_PI;
+                }
+                part += inc * __ldcg(p.cumw + k);
+                mx = fmax(mx, fabs(inc));
+            }
+            double ps, pm;
+            block_sum_max(part, mx, &ps, &pm);
+            if (tid == 0) {
+                p.qpart[2 * cta] = ps;
+                p.qpart[2 * cta + 1] = pm;
+            }
+        }
+        if (!grid_barrier(p, 4)) return;
+
+        // ---- Delta Omega, Metropolis decision, patch ----
+        if (tid == 0) {
+            double s = 0.0, mx = 0.0;
+            for (int c = 0; c < p.ncta; ++c) {
+                s += __ldcg(p.qpart + 2 * c);
+                mx = fmax(mx, __ldcg(p.qpart + 2 * c + 1));
+            }
+            const double dom = p.a / M * s;
+            s_dom = dom;
+            int acc = 0;
+            if (p.mode == MODE_SWEEP) {
+                const double ratio = exp(-p.beta * dom);
+                acc = ratio > s_draw[2];
+            }
+            s_acc = acc;
+            if (cta == 0) {
+                const long long slot = (p.mode == MODE_SWEEP) ? q : 0;
+                p.domega_out[slot] = dom;
+                if (p.maxinc_out) p.maxinc_out[slot] = mx;
+                if (p.mode == MODE_SWEEP && p.dec_out) p.dec_out[q] = (unsigned char)acc;
+            }
+        }
+        __syncthreads();
+        if (p.mode == MODE_DELTA) return;
+        nacc += (unsigned long long)s_acc;
+        if (cta == 0 && s_acc && tid < 7) {
+            const double thn = s_draw[0], phn = s_draw[1];
+            if (tid == 6) {
+                p.spins[2 * o] = thn;
+                p.spins[2 * o + 1] = phn;
+            } else {
+                const int alpha = tid >> 1;
+                const bool fwd = (tid & 1) == 0;
+                const int j = s_loc[tid + 1];  // o+e_alpha (fwd) or o-e_alpha
+                double cn, xn, yn, cj, xj, yj;
+                spinor3(thn, phn, cn, xn, yn);
+                spinor3(__ldcg(p.spins + 2 * j), __ldcg(p.spins + 2 * j + 1), cj, xj, yj);
+                // fwd: Htilde_{o, o+e} = -t <chi'_o|chi_j>/a stored at o;
+                // bwd: Htilde_{o-e, o} = -t <chi_j|chi'_o>/a stored at o-e
+                const double2 ov = fwd ? overlap3(cn, xn, yn, cj, xj, yj) : overlap3(cj, xj, yj, cn, xn, yn);
+                const double2 hv = make_double2(-p.t * ov.x / p.a, -p.t * ov.y / p.a);
+                const size_t at = (size_t)alpha * N + (fwd ? o : j);
+                p.hop64[at] = hv;
+                p.hop32[at] = make_float2((float)hv.x, (float)hv.y);
+            }
+        }
+        if (!grid_barrier(p, 5)) return;
+
+        // ---- magnetisation after each completed sweep ----
+        if ((upd + 1ull) % (unsigned long long)N == 0ull) {
+            double sx = 0.0, sy = 0.0, sz = 0.0;
+            if (active) {
+                const double th = __ldcg(p.spins + 2 * i), ph = __ldcg(p.spins + 2 * i + 1);
+                double st, ct, sp, cp;
+                sincos(th, &st, &ct);
+                sincos(ph, &sp, &cp);
+                sx = st * cp;
+                sy = st * sp;
+                sz = ct;
+            }
+            double a0, b0;
+            block_sum_max(sx, 0.0, &a0, &b0);
+            if (tid == 0) p.magpart[3 * cta] = a0;
+            block_sum_max(sy, 0.0, &a0, &b0);
+            if (tid == 0) p.magpart[3 * cta + 1] = a0;
+            block_sum_max(sz, 0.0, &a0, &b0);
+            if (tid == 0) p.magpart[3 * cta + 2] = a0;
+            if (!grid_barrier(p, 6)) return;
+            if (cta == 0 && tid == 0) {
+                double X = 0.0, Y = 0.0, Z = 0.0;
+                for (int c = 0; c < p.ncta; ++c) {
+                    X += __ldcg(p.magpart + 3 * c);
+                    Y += __ldcg(p.magpart + 3 * c + 1);
+                    Z += __ldcg(p.magpart + 3 * c + 2);
+                }
+                p.mag_out[nmag] = sqrt(X * X + Y * Y + Z * Z) / N;
+            }
+            ++nmag;
+        }
+    }
+    if (cta == 0 && tid == 0 && p.mode == MODE_SWEEP) {
+        *p.n_acc = nacc;
+        *p.n_mag = nmag;
+    }
+}
+
+}  // namespace gfmc

@@ -1,0 +1,88 @@
+// gfmc_internal.h -- structures shared by the host API and the CUDA kernels.
+//
+// One chain = one Params block.  All arrays are device memory owned by the
+// handle (gfmc_api.cu); the kernels only read these pointers.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gfmc {
+
+constexpr int kThreads = 256;            // threads per CTA of the persistent engine
+constexpr int kWarps = kThreads / 32;
+constexpr int kVec = 7;                  // local vectors: o and its 6 neighbours
+constexpr int kPairs = 28;               // upper-triangle pairs (j <= k) of the 7x7 block
+constexpr int kEntries = 112;            // 2 Gram blocks x 28 pairs x (re, im)
+constexpr int kMaxNbrCta = 64;           // neighbour CTAs a tile may depend on
+constexpr int kMaxL = 42;                // N = L^3 <= kThreads * SMs
+
+enum Mode : int { MODE_MOMENTS = 0, MODE_DELTA = 1, MODE_SWEEP = 2 };
+
+enum ErrCode : int { ERR_NONE = 0, ERR_TIMEOUT = 4, ERR_NUMERIC = 5 };
+
+struct Params {
+    // lattice and model
+    int L, N, M, nsteps, ncta;
+    double t, chem, beta, a;
+
+    // chain state
+    double* spins;    // [N][2] (theta, phi)
+    double2* hop64;   // [3][N]   Htilde_{i, i+e_alpha}, alpha = x, y, z
+    float2* hop32;    // [3][N]   the same rounded to FP32 (mixed path)
+    void* rbuf;       // [2][7][N] recursion vectors (double2 or float2)
+
+    // constant tables, filled by the set-up kernel
+    double* gker;     // [M]     kernel g_n
+    double2* twc;     // [M]     e^{-i n pi / (2M)}
+    double2* fftw;    // [M/2]   e^{-2 pi i j / M}
+    double* sinth;    // [M]     sin theta_k, theta_k = pi (k + 1/2) / M
+    double* cumw;     // [M]     C_k = sum_{j<=k} sin theta_j f(a cos theta_j)
+
+    // per-update scratch
+    double* partial;  // [nsteps][ncta][kEntries]  per-CTA Gram partial sums
+    double2* fftin;   // [4][M]  damped, twisted combined moments
+    double2* gnode;   // [4][M]  G_V(w_k) for V = o, v, o+v, o+iv
+    double* qpart;    // [ncta][2]  (phase-sum partial, max |increment|)
+    double* magpart;  // [ncta][3]
+    double2* mom_out; // [7][7][M] full moment matrix (moments mode)
+
+    // tile partition of the sites over CTAs and the CTAs each tile reads from
+    const int* tile_start;  // [ncta + 1]
+    const int* nbr_ptr;     // [ncta + 1]
+    const int* nbr_idx;     // [nbr_ptr[ncta]]
+
+    // synchronisation
+    unsigned* flags;  // [ncta]  completed stencil phases of each CTA
+    unsigned* bar;    // [2]     grid barrier: arrival count, generation
+    int* err;         // [4]     code, where, cta, aux
+    long long budget; // clock64 cycles a single wait may spin before giving up
+    int stall;        // test hook: CTA 0 withholds its completion flags
+
+    // work description
+    int mode;
+    long long site;            // moments / delta modes
+    double theta_new, phi_new; // delta mode
+    unsigned long long upd0;   // sweep mode: first update number
+    long long n_updates;       // sweep mode
+    unsigned long long seed;
+    unsigned chain_id;
+
+    // outputs
+    unsigned char* dec_out;    // [n_updates]
+    double* domega_out;        // [n_updates] (sweep) or [1] (delta)
+    double* maxinc_out;        // [n_updates] or [1]
+    double* mag_out;           // [n_updates / N + 1]
+    unsigned long long* n_acc; // [1]
+    long long* n_mag;          // [1]
+};
+
+// Launchers (defined in the kernel translation units).
+cudaError_t launch_engine_f64(const Params& p, cudaStream_t s);
+cudaError_t launch_engine_f32(const Params& p, cudaStream_t s);
+int engine_smem_bytes(int M);
+cudaError_t engine_max_ctas(int precision, int M, int* out);
+cudaError_t launch_build_hoppings(const Params& p, cudaStream_t s);
+cudaError_t launch_setup_tables(const Params& p, int kernel_kind, double lambda, cudaStream_t s);
+
+}  // namespace gfmc

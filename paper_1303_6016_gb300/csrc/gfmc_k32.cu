@@ -1,0 +1,32 @@
+// FP32-mixed instantiation of the persistent GFMC engine: FP32 recursion
+// vectors and stencil, FP32 warp sums of the Gram products, FP64 above.
+#include "gfmc_engine.cuh"
+
+namespace gfmc {
+
+cudaError_t launch_engine_f32(const Params& p, cudaStream_t s)
+{
+    const int smem = engine_smem_bytes(p.M);
+    cudaError_t e = cudaFuncSetAttribute(gfmc_engine<float>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    Params q = p;
+    void* args[] = {(void*)&q};
+    return cudaLaunchCooperativeKernel((void*)gfmc_engine<float>, dim3(p.ncta), dim3(kThreads), args,
+                                       (size_t)smem, s);
+}
+
+cudaError_t engine_max_ctas_f32(int M, int* out)
+{
+    const int smem = engine_smem_bytes(M);
+    cudaError_t e = cudaFuncSetAttribute(gfmc_engine<float>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gfmc_engine<float>, kThreads, smem);
+    if (e != cudaSuccess) return e;
+    *out = per_sm;
+    return cudaSuccess;
+}
+
+}  // namespace gfmc

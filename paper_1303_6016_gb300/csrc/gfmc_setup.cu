@@ -1,0 +1,135 @@
+// gfmc_setup.cu -- device-side set-up of a chain: the bond table of Htilde and
+// the constant tables of the quadrature (kernel g_n, FFT twiddles, node
+// sines, cumulative Fermi weights).  Runs once per create / set_state.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "gfmc_internal.h"
+
+namespace gfmc {
+
+cudaError_t engine_max_ctas_f64(int M, int* out);
+cudaError_t engine_max_ctas_f32(int M, int* out);
+
+int engine_smem_bytes(int M) { return M * (int)sizeof(double2); }
+
+cudaError_t engine_max_ctas(int precision, int M, int* out)
+{
+    int per_sm = 0;
+    cudaError_t e = precision == 0 ? engine_max_ctas_f64(M, &per_sm) : engine_max_ctas_f32(M, &per_sm);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    *out = per_sm * sms;
+    return cudaSuccess;
+}
+
+namespace {
+
+__device__ __forceinline__ int forward_nbr(int i, int alpha, int L)
+{
+    const int LL = L * L;
+    const int x = i % L, y = (i / L) % L, z = i / LL;
+    if (alpha == 0) return (x == L - 1) ? i - (L - 1) : i + 1;
+    if (alpha == 1) return (y == L - 1) ? i - (L - 1) * L : i + L;
+    return (z == L - 1) ? i - (L - 1) * LL : i + LL;
+}
+
+// Htilde_{i, i+e_alpha} = -t <chi_i|chi_{i+e_alpha}> / a  (Sec. 2.1, Eq. ht in
+// the gauge chi = (cos(th/2), e^{i ph} sin(th/2)); Sec. 2.2 rescaling).
+__global__ void build_hoppings_kernel(Params p)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= p.N) return;
+    double shi, chi, spi, cpi;
+    sincos(0.5 * p.spins[2 * i], &shi, &chi);
+    sincos(p.spins[2 * i + 1], &spi, &cpi);
+    const double ci = chi, xi = cpi * shi, yi = spi * shi;
+    for (int alpha = 0; alpha < 3; ++alpha) {
+        const int j = forward_nbr(i, alpha, p.L);
+        double shj, chj, spj, cpj;
+        sincos(0.5 * p.spins[2 * j], &shj, &chj);
+        sincos(p.spins[2 * j + 1], &spj, &cpj);
+        const double cj = chj, xj = cpj * shj, yj = spj * shj;
+        const double re = ci * cj + (xi * xj + yi * yj);
+        const double im = xi * yj - yi * xj;
+        const double2 h = make_double2(-p.t * re / p.a, -p.t * im / p.a);
+        p.hop64[(size_t)alpha * p.N + i] = h;
+        p.hop32[(size_t)alpha * p.N + i] = make_float2((float)h.x, (float)h.y);
+    }
+}
+
+// g_n: kind 0 Jackson [(M-n+1) cos(pi n/(M+1)) + sin(pi n/(M+1)) cot(pi/(M+1))]/(M+1)
+// (Weisse et al., Rev. Mod. Phys. 78, 275, the KPM review the paper cites);
+// kind 1 Lorentz sinh(lambda (1 - n/M)) / sinh(lambda) (Sec. 2.2).
+// twc_n = e^{-i n pi/(2M)} (Eq. mu_to_mu_tilde); fftw_j = e^{-2 pi i j/M}
+// (Eq. green_fft); sin theta_k with theta_k = pi (k + 1/2)/M (the FFT nodes).
+__global__ void setup_tables_kernel(Params p, int kind, double lambda)
+{
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    const int M = p.M;
+    if (n >= M) return;
+    double g;
+    if (kind == 0) {
+        const double q = CUDART_PI / (M + 1);
+        g = ((M - n + 1) * cos(q * n) + sin(q * n) * cos(q) / sin(q)) / (M + 1);
+    } else {
+        g = sinh(lambda * (1.0 - (double)n / M)) / sinh(lambda);
+    }
+    p.gker[n] = g;
+    double s, c;
+    sincospi((double)n / (2.0 * M), &s, &c);
+    p.twc[n] = make_double2(c, -s);
+    p.sinth[n] = sinpi((n + 0.5) / M);
+    if (n < M / 2) {
+        sincospi(2.0 * n / M, &s, &c);
+        p.fftw[n] = make_double2(c, -s);
+    }
+}
+
+__device__ __forceinline__ double fermi(double E, double beta, double chem)
+{
+    const double x = beta * (E - chem);
+    if (x > 0) {
+        const double e = exp(-x);
+        return e / (1.0 + e);
+    }
+    return 1.0 / (1.0 + exp(x));
+}
+
+// C_k = sum_{j <= k} sin(theta_j) f(a cos theta_j): the Chebyshev-Gauss weights
+// of Eq. d_seff2 summed from k = 0, so that the quadrature of the continuous
+// phase phi_k = phi_{M-1} + sum_{j >= k} inc_j becomes
+// phi_{M-1} C_{M-1} + sum_j inc_j C_j.  One thread: a plain running sum.
+__global__ void cumw_kernel(Params p)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    double s = 0.0;
+    for (int k = 0; k < p.M; ++k) {
+        const double x = (k + 0.5) / p.M;
+        s += sinpi(x) * fermi(p.a * cospi(x), p.beta, p.chem);
+        p.cumw[k] = s;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_build_hoppings(const Params& p, cudaStream_t s)
+{
+    build_hoppings_kernel<<<(p.N + 255) / 256, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_setup_tables(const Params& p, int kernel_kind, double lambda, cudaStream_t s)
+{
+    setup_tables_kernel<<<(p.M + 255) / 256, 256, 0, s>>>(p, kernel_kind, lambda);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    cumw_kernel<<<1, 32, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace gfmc

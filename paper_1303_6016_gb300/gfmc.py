@@ -1,0 +1,217 @@
+"""Python binding of libgfmc.so (the C ABI in include/gfmc.h).
+
+Argument marshalling only: every step of a GFMC update runs in the CUDA
+kernels behind the C ABI.  The library must have been built
+(``python -m paper_1303_6016_gb300.build`` or ``__graft_entry__.build()``);
+without it every call raises -- there is no CPU fallback.
+
+    from paper_1303_6016_gb300 import gfmc, inputs
+    ch = gfmc.Chain(L=16, spins=inputs.uniform_sphere(16, 0), M=1024, beta=20.0, mu=-2.0)
+    mu = ch.moments(site=0)                       # complex128 [7, 7, M]
+    dO = ch.delta_omega(0, theta_new, phi_new)    # float, units of t
+    out = ch.updates(4096)                         # decisions, Delta Omega trace, ...
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgfmc.so")
+
+GFMC_OK, GFMC_EINVAL, GFMC_ENOMEM, GFMC_ECUDA, GFMC_ETIMEOUT, GFMC_ENUMERIC = range(6)
+PRECISIONS = {"fp64": 0, "fp32_mixed": 1}
+KERNELS = {"jackson": 0, "lorentz": 1}
+
+# Names exported by libgfmc.so; include/gfmc.h declares exactly these.
+EXPORTS = ("gfmc_default_options", "gfmc_create", "gfmc_moments", "gfmc_delta_omega",
+           "gfmc_updates", "gfmc_sweep", "gfmc_get_spins", "gfmc_set_state", "gfmc_get_counter",
+           "gfmc_set_wait_budget", "gfmc_inject_stall", "gfmc_last_error", "gfmc_destroy")
+
+
+class GfmcError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"gfmc status {status}: {message}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("kernel", ctypes.c_int),
+                ("lorentz_lambda", ctypes.c_double), ("spectral_scale", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("chain_id", ctypes.c_uint32),
+                ("stream", ctypes.c_void_p), ("num_ctas", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libgfmc.so and declare its signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA engine first "
+                           "(python -m paper_1303_6016_gb300.build); there is no fallback")
+    L = ctypes.CDLL(path)
+    vp, d, i64, u64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_uint64
+    L.gfmc_default_options.argtypes = [ctypes.POINTER(Options)]
+    L.gfmc_default_options.restype = None
+    L.gfmc_create.argtypes = [ctypes.c_int, d, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                              ctypes.c_int, ctypes.POINTER(Options), ctypes.POINTER(vp)]
+    L.gfmc_moments.argtypes = [vp, i64, d]
+    L.gfmc_delta_omega.argtypes = [vp, i64, ctypes.c_double, ctypes.c_double, d]
+    L.gfmc_updates.argtypes = [vp, i64, ctypes.POINTER(u64), ctypes.POINTER(ctypes.c_uint8), d, d,
+                               ctypes.POINTER(i64)]
+    L.gfmc_sweep.argtypes = [vp, ctypes.c_int, ctypes.POINTER(u64), d, ctypes.POINTER(ctypes.c_uint8), d]
+    L.gfmc_get_spins.argtypes = [vp, d]
+    L.gfmc_set_state.argtypes = [vp, d, u64]
+    L.gfmc_get_counter.argtypes = [vp, ctypes.POINTER(u64)]
+    L.gfmc_set_wait_budget.argtypes = [vp, i64]
+    L.gfmc_inject_stall.argtypes = [vp, ctypes.c_int]
+    L.gfmc_last_error.argtypes = [vp]
+    L.gfmc_last_error.restype = ctypes.c_char_p
+    L.gfmc_destroy.argtypes = [vp]
+    L.gfmc_destroy.restype = None
+    for name in ("gfmc_create", "gfmc_moments", "gfmc_delta_omega", "gfmc_updates", "gfmc_sweep",
+                 "gfmc_get_spins", "gfmc_set_state", "gfmc_get_counter", "gfmc_set_wait_budget",
+                 "gfmc_inject_stall"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def current_stream_handle():
+    """The raw cudaStream_t of torch's current stream, or None (default stream)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream) or None
+    except Exception:  # torch absent or without CUDA
+        pass
+    return None
+
+
+class Chain:
+    """One GFMC Markov chain resident on the GPU (a gfmc_t handle)."""
+
+    def __init__(self, L: int, spins, t: float = 1.0, mu: float = -2.0, beta: float = 20.0,
+                 M: int = 256, precision: str = "fp64", kernel: str = "jackson",
+                 lorentz_lambda: float = 4.0, spectral_scale: float = 0.0, seed: int = 1,
+                 chain_id: int = 0, stream=None, num_ctas: int = 0):
+        lib = load()
+        self.L, self.N, self.M = int(L), int(L) ** 3, int(M)
+        self.t, self.mu, self.beta = float(t), float(mu), float(beta)
+        self.precision = precision
+        opt = Options()
+        lib.gfmc_default_options(ctypes.byref(opt))
+        opt.precision = PRECISIONS[precision]
+        opt.kernel = KERNELS[kernel]
+        opt.lorentz_lambda = float(lorentz_lambda)
+        opt.spectral_scale = float(spectral_scale)
+        opt.seed = int(seed)
+        opt.chain_id = int(chain_id)
+        s = current_stream_handle() if stream is None else stream
+        opt.stream = s if s else None
+        opt.num_ctas = int(num_ctas)
+        sp = np.ascontiguousarray(spins, dtype=np.float64).reshape(-1, 2)
+        if sp.shape[0] != self.N:
+            raise ValueError(f"spins has {sp.shape[0]} rows, expected N = {self.N}")
+        h = ctypes.c_void_p()
+        st = lib.gfmc_create(self.L, _dp(sp), self.t, self.mu, self.beta, self.M, ctypes.byref(opt),
+                             ctypes.byref(h))
+        if st != GFMC_OK:
+            raise GfmcError(st, lib.gfmc_last_error(None).decode())
+        self._h = h
+        self._lib = lib
+
+    # -- helpers --
+    def _check(self, st):
+        if st != GFMC_OK:
+            raise GfmcError(st, self._lib.gfmc_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gfmc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- API --
+    def moments(self, site: int) -> np.ndarray:
+        mu = np.zeros((7, 7, self.M), dtype=np.complex128)
+        self._check(self._lib.gfmc_moments(self._h, int(site), _dp(mu.view(np.float64))))
+        return mu
+
+    def delta_omega(self, site: int, theta_new: float, phi_new: float) -> float:
+        out = np.zeros(1)
+        self._check(self._lib.gfmc_delta_omega(self._h, int(site), float(theta_new), float(phi_new),
+                                               _dp(out)))
+        return float(out[0])
+
+    def updates(self, n: int, trace: bool = True) -> dict:
+        n = int(n)
+        acc = ctypes.c_uint64(0)
+        nmag = ctypes.c_int64(0)
+        dec = np.zeros(n if trace else 0, dtype=np.uint8)
+        dom = np.zeros(n if trace else 0, dtype=np.float64)
+        mag = np.zeros(n // self.N + 2, dtype=np.float64)
+        self._check(self._lib.gfmc_updates(
+            self._h, n, ctypes.byref(acc),
+            dec.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)) if trace else None,
+            _dp(dom) if trace else None, _dp(mag), ctypes.byref(nmag)))
+        return {"n_accepted": int(acc.value), "decisions": dec, "d_omega": dom,
+                "magnetization": mag[: nmag.value]}
+
+    def updates_into(self, n: int, decisions=None, d_omega=None, magnetization=None) -> tuple:
+        """gfmc_updates writing into caller-owned (e.g. pinned) numpy buffers;
+        returns (n_accepted, n_magnetisations)."""
+        acc = ctypes.c_uint64(0)
+        nmag = ctypes.c_int64(0)
+        self._check(self._lib.gfmc_updates(
+            self._h, int(n), ctypes.byref(acc),
+            decisions.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)) if decisions is not None else None,
+            _dp(d_omega) if d_omega is not None else None,
+            _dp(magnetization) if magnetization is not None else None, ctypes.byref(nmag)))
+        return int(acc.value), int(nmag.value)
+
+    def sweep(self, n_sweeps: int = 1, trace: bool = True) -> dict:
+        return self.updates(int(n_sweeps) * self.N, trace=trace)
+
+    def get_spins(self, out=None) -> np.ndarray:
+        if out is None:
+            out = np.zeros((self.N, 2), dtype=np.float64)
+        self._check(self._lib.gfmc_get_spins(self._h, _dp(out)))
+        return out
+
+    def set_state(self, spins, counter: int):
+        sp = np.ascontiguousarray(spins, dtype=np.float64).reshape(-1, 2)
+        self._check(self._lib.gfmc_set_state(self._h, _dp(sp), int(counter)))
+
+    def set_wait_budget(self, cycles: int):
+        self._check(self._lib.gfmc_set_wait_budget(self._h, int(cycles)))
+
+    def inject_stall(self, enable: bool = True):
+        self._check(self._lib.gfmc_inject_stall(self._h, 1 if enable else 0))
+
+    @property
+    def counter(self) -> int:
+        c = ctypes.c_uint64(0)
+        self._check(self._lib.gfmc_get_counter(self._h, ctypes.byref(c)))
+        return int(c.value)
