@@ -192,7 +192,6 @@ __device__ inline bool wait_neighbours(const Params& p, int cta, unsigned target
                     break;
                 }
             }
-            __threadfence();
         }
     }
     __syncthreads();
@@ -203,7 +202,6 @@ __device__ __forceinline__ void publish(const Params& p, int cta, unsigned value
 {
     __syncthreads();
     if (p.ncta > 1 && threadIdx.x == 0 && !(p.stall && cta == 0)) {
-        __threadfence();
         st_release_u32(&p.flags[cta], value);
     }
 }
@@ -409,6 +407,35 @@ __device__ __forceinline__ void gram_chunk_reduce(const R2 (&rc)[kVec], const R2
     if (lane < 28) dst[28 * C + lane] = (double)s;
 }
 
+// FP64 Gram sums of one CTA from shared memory: thread (entry e, group g)
+// accumulates conj(x_j) y_k over the sites s = g, g+4, ... of the tile with
+// fused multiply-adds only; the four groups are added in order.  sr holds
+// r_m of vector v at sr[v*kStage + s] and r_{m+1} at sr[(7+v)*kStage + s].
+__device__ __forceinline__ void gram_smem_f64(const double2* sr, int T, double* gsum, double* out)
+{
+    const int tid = threadIdx.x;
+    if (tid < 4 * 56) {
+        const int e = tid % 56, g = tid / 56;
+        const int pp = e % kPairs;
+        const int j = pair_j(pp), k = pair_k(pp);
+        const double2* xs = sr + j * kStage;
+        const double2* ys = sr + (e < kPairs ? k : kVec + k) * kStage;
+        double re = 0.0, im = 0.0;
+        for (int s = g; s < T; s += 4) {
+            const double2 x = xs[s], y = ys[s];
+            re = fma(x.x, y.x, re);
+            re = fma(x.y, y.y, re);
+            im = fma(x.x, y.y, im);
+            im = fma(-x.y, y.x, im);
+        }
+        if (e < kPairs && j == k) im = 0.0;
+        gsum[g * kEntries + 2 * e] = re;
+        gsum[g * kEntries + 2 * e + 1] = im;
+    }
+    __syncthreads();
+    if (tid < kEntries) out[tid] = ((gsum[tid] + gsum[kEntries + tid]) + gsum[2 * kEntries + tid]) + gsum[3 * kEntries + tid];
+}
+
 // ---------------------------------------------------------------------------
 // the engine
 // ---------------------------------------------------------------------------
@@ -482,64 +509,78 @@ __global__ void __launch_bounds__(kThreads, 1) gfmc_engine(const Params p)
         for (int d = 0; d < 6; ++d) h[d] = active ? hop_of(hop, N, i, d, nb[d]) : c_make<R2>(0, 0);
         __syncthreads();
 
-        // ---- phase 0: r_0 = e_{l_v}, r_1 = Htilde e_{l_v} ----
-        if (active) {
+        // ---- phase 0: r_0 = e_{l_v} and r_1 = Htilde e_{l_v} of the own site, kept in registers;
+        //      only r_1 is published (no CTA ever reads another CTA's r_0) ----
+        R2 prv[kVec], cur[kVec];
 #pragma unroll
-            for (int v = 0; v < kVec; ++v) {
-                const int lv = s_loc[v];
-                R2 r0 = c_make<R2>(i == lv ? (R)1 : (R)0, (R)0);
-                R2 r1 = c_make<R2>(0, 0);
+        for (int v = 0; v < kVec; ++v) {
+            const int lv = s_loc[v];
+            prv[v] = c_make<R2>((active && i == lv) ? (R)1 : (R)0, (R)0);
+            R2 r1 = c_make<R2>(0, 0);
 #pragma unroll
-                for (int d = 0; d < 6; ++d)
-                    if (nb[d] == lv) {
-                        r1.x += h[d].x;
-                        r1.y += h[d].y;
-                    }
-                stcg2(buf0 + (size_t)v * N + i, r0);
-                stcg2(buf1 + (size_t)v * N + i, r1);
-            }
+            for (int d = 0; d < 6; ++d)
+                if (active && nb[d] == lv) {
+                    r1.x += h[d].x;
+                    r1.y += h[d].y;
+                }
+            cur[v] = r1;
+            if (active) stcg2(buf1 + (size_t)v * N + i, r1);
         }
         publish(p, cta, phase + 1);
 
         // ---- steps m = 1 .. M/2-1: r_{m+1} = 2 Htilde r_m - r_{m-1} and the Gram sums ----
         for (int m = 1; m <= p.nsteps; ++m) {
             if (!wait_neighbours(p, cta, phase + (unsigned)m, 100 + m)) return;
-            R2* cur = (m & 1) ? buf1 : buf0;
-            R2* prv = (m & 1) ? buf0 : buf1;
-            R2 rc[kVec], rn[kVec];
+            const R2* rd = (m & 1) ? buf1 : buf0;  // r_m of every site
+            R2* wr = (m & 1) ? buf0 : buf1;        // receives r_{m+1}; held r_{m-1}
+            R2 nxt[kVec];
             if (active) {
 #pragma unroll
                 for (int v = 0; v < kVec; ++v) {
-                    const R2* cv = cur + (size_t)v * N;
+                    const R2* cv = rd + (size_t)v * N;
                     R2 acc = c_make<R2>(0, 0);
 #pragma unroll
                     for (int d = 0; d < 6; ++d) c_fma(acc, h[d], ldcg2(cv + nb[d]));
-                    const R2 rp = ldcg2(prv + (size_t)v * N + i);
-                    rc[v] = ldcg2(cv + i);
-                    rn[v] = c_make<R2>(fma((R)2, acc.x, -rp.x), fma((R)2, acc.y, -rp.y));
-                    if (m < p.nsteps) stcg2(prv + (size_t)v * N + i, rn[v]);
+                    nxt[v] = c_make<R2>(fma((R)2, acc.x, -prv[v].x), fma((R)2, acc.y, -prv[v].y));
+                    if (m < p.nsteps) stcg2(wr + (size_t)v * N + i, nxt[v]);
                 }
             } else {
 #pragma unroll
+                for (int v = 0; v < kVec; ++v) nxt[v] = c_make<R2>(0, 0);
+            }
+            double* prow = p.partial + ((size_t)(m - 1) * p.ncta + cta) * kEntries;
+            if constexpr (sizeof(R) == 8) {
+                // stage r_m, r_{m+1} of the own site for the shared-memory Gram sums
+#pragma unroll
                 for (int v = 0; v < kVec; ++v) {
-                    rc[v] = c_make<R2>(0, 0);
-                    rn[v] = c_make<R2>(0, 0);
+                    dyn[v * kStage + tid] = cur[v];
+                    dyn[(kVec + v) * kStage + tid] = nxt[v];
                 }
             }
-            // Gram entries e = 0..55: e < 28 -> conj(r_m^j) r_m^k, else conj(r_m^j) r_{m+1}^k,
-            // (j, k) the upper pair e mod 28; processed in 4 chunks of 14 complex values.
-            gram_chunk_reduce<R, R2, 0>(rc, rn, lane, red[warp]);
-            gram_chunk_reduce<R, R2, 1>(rc, rn, lane, red[warp]);
-            gram_chunk_reduce<R, R2, 2>(rc, rn, lane, red[warp]);
-            gram_chunk_reduce<R, R2, 3>(rc, rn, lane, red[warp]);
-            __syncthreads();
-            if (tid < kEntries) {
-                double s = 0.0;
-#pragma unroll
-                for (int w = 0; w < kWarps; ++w) s += red[w][tid];
-                p.partial[((size_t)(m - 1) * p.ncta + cta) * kEntries + tid] = s;
-            }
+            // r_{m+1} is stored: neighbours may start step m+1 while this CTA forms its dots
             publish(p, cta, phase + (unsigned)m + 1u);
+            if constexpr (sizeof(R) == 8) {
+                gram_smem_f64(dyn, s1 - s0, &red[0][0], prow);
+            } else {
+                // Gram entries e = 0..55: e < 28 -> conj(r_m^j) r_m^k, else conj(r_m^j) r_{m+1}^k,
+                // (j, k) the upper pair e mod 28; 4 chunks of 14 complex values, warp butterfly.
+                gram_chunk_reduce<R, R2, 0>(cur, nxt, lane, red[warp]);
+                gram_chunk_reduce<R, R2, 1>(cur, nxt, lane, red[warp]);
+                gram_chunk_reduce<R, R2, 2>(cur, nxt, lane, red[warp]);
+                gram_chunk_reduce<R, R2, 3>(cur, nxt, lane, red[warp]);
+                __syncthreads();
+                if (tid < kEntries) {
+                    double sum = 0.0;
+#pragma unroll
+                    for (int w = 0; w < kWarps; ++w) sum += red[w][tid];
+                    prow[tid] = sum;
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < kVec; ++v) {
+                prv[v] = cur[v];
+                cur[v] = nxt[v];
+            }
         }
         phase += (unsigned)p.nsteps + 1u;
         if (!grid_barrier(p, 1)) return;

@@ -16,6 +16,7 @@ constexpr int kPairs = 28;               // upper-triangle pairs (j <= k) of the
 constexpr int kEntries = 112;            // 2 Gram blocks x 28 pairs x (re, im)
 constexpr int kMaxNbrCta = 64;           // neighbour CTAs a tile may depend on
 constexpr int kMaxL = 42;                // N = L^3 <= kThreads * SMs
+constexpr int kStage = kThreads + 1;     // row stride of the staged vectors (bank spread)
 
 enum Mode : int { MODE_MOMENTS = 0, MODE_DELTA = 1, MODE_SWEEP = 2 };
 

@@ -11,7 +11,14 @@ namespace gfmc {
 cudaError_t engine_max_ctas_f64(int M, int* out);
 cudaError_t engine_max_ctas_f32(int M, int* out);
 
-int engine_smem_bytes(int M) { return M * (int)sizeof(double2); }
+// Dynamic shared memory of the engine: the FFT buffer (M double2) or the
+// staged own-site vectors of the FP64 Gram sums (14 x kStage double2).
+int engine_smem_bytes(int M)
+{
+    const int fft = M * (int)sizeof(double2);
+    const int stage = 2 * kVec * kStage * (int)sizeof(double2);
+    return fft > stage ? fft : stage;
+}
 
 cudaError_t engine_max_ctas(int precision, int M, int* out)
 {
