@@ -34,6 +34,7 @@
 #ifndef GFMC_H
 #define GFMC_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -150,6 +151,38 @@ gfmc_status gfmc_set_wait_budget(gfmc_t h, int64_t cycles);
  * clears itself after that launch.  It has an effect only when the chain runs
  * on more than one CTA. */
 gfmc_status gfmc_inject_stall(gfmc_t h, int enable);
+
+/* Delta Omega of one proposal with no allocation of any kind.  The paper has
+ * no counterpart: this entry point exists for callers that cannot allocate
+ * device memory while they run -- for instance a plugin's enqueue step inside
+ * a framework that owns the device memory pool, code held to a fixed memory
+ * budget, or code that must not let cudaMalloc synchronise the device.  It
+ * computes what gfmc_delta_omega computes (FP64 path) for the configuration
+ * d_spins, without a handle, and calls no cudaMalloc, cudaFree or other
+ * allocating routine: its scratch is one file-scope device array of 8 MiB
+ * that every GPU which loads the library holds until the process exits.
+ *   L, t, mu, beta, M      as for gfmc_create; the scratch limits them to
+ *                          (L, M) whose buffers fit in 8 MiB with at most 32
+ *                          CTAs (for example L <= 16 with M <= 512, or L <= 12
+ *                          with M <= 1024); larger sizes return GFMC_EINVAL
+ *                          with the bytes they would need.
+ *   kernel, lorentz_lambda, spectral_scale   as in gfmc_options (<= 0: defaults).
+ *   d_spins   DEVICE pointer, double[N][2] (theta, phi), owned by the caller, read only.
+ *   site, theta_new, phi_new   as for gfmc_delta_omega.
+ *   d_omega   DEVICE pointer to one double that receives Delta Omega.
+ *   stream    cudaStream_t to run on (NULL: the legacy default stream); the
+ *             call waits for its own work on that stream before returning.
+ *   err_msg   optional host buffer of err_len bytes for a message on failure.
+ * The first call on a device looks up the device address of the scratch
+ * array (with that device current); make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents
+ * (the call clears what must start at zero), so calls that overlap on the GPU
+ * -- from two threads, or on two streams -- race and must be serialised by
+ * the caller. */
+gfmc_status gfmc_delta_omega_noalloc(int L, const double* d_spins, double t, double mu, double beta, int M,
+                                     int kernel, double lorentz_lambda, double spectral_scale, int64_t site,
+                                     double theta_new, double phi_new, double* d_omega, void* stream,
+                                     char* err_msg, size_t err_len);
 
 /* Message of the last failed call on h (NULL: of the last failed create or of
  * a call on an invalid handle in this thread).  Never NULL. */

@@ -28,7 +28,8 @@ KERNELS = {"jackson": 0, "lorentz": 1}
 # Names exported by libgfmc.so; include/gfmc.h declares exactly these.
 EXPORTS = ("gfmc_default_options", "gfmc_create", "gfmc_moments", "gfmc_delta_omega",
            "gfmc_updates", "gfmc_sweep", "gfmc_get_spins", "gfmc_set_state", "gfmc_get_counter",
-           "gfmc_set_wait_budget", "gfmc_inject_stall", "gfmc_last_error", "gfmc_destroy")
+           "gfmc_set_wait_budget", "gfmc_inject_stall", "gfmc_last_error", "gfmc_destroy",
+           "gfmc_delta_omega_noalloc")
 
 
 class GfmcError(RuntimeError):
@@ -75,6 +76,11 @@ def load(path: str = LIB_PATH):
     L.gfmc_last_error.restype = ctypes.c_char_p
     L.gfmc_destroy.argtypes = [vp]
     L.gfmc_destroy.restype = None
+    L.gfmc_delta_omega_noalloc.argtypes = [ctypes.c_int, vp, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_double, i64, ctypes.c_double, ctypes.c_double, vp, vp,
+                                           ctypes.c_char_p, ctypes.c_size_t]
+    L.gfmc_delta_omega_noalloc.restype = ctypes.c_int
     for name in ("gfmc_create", "gfmc_moments", "gfmc_delta_omega", "gfmc_updates", "gfmc_sweep",
                  "gfmc_get_spins", "gfmc_set_state", "gfmc_get_counter", "gfmc_set_wait_budget",
                  "gfmc_inject_stall"):
