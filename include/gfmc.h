@@ -139,6 +139,26 @@ gfmc_status gfmc_set_state(gfmc_t h, const double* spins, uint64_t update_counte
 /* Read the update counter. */
 gfmc_status gfmc_get_counter(gfmc_t h, uint64_t* update_counter);
 
+/* Run a batch of independent chains in one launch, each on its own team of
+ * CTAs (the multi-chain form of Algorithm 1's Monte Carlo sampling, Sec. 3.2:
+ * independent chains share nothing).  Chain c runs n_updates[c] sequential
+ * updates from its own counter, exactly as gfmc_updates would (same draws,
+ * same decisions up to the rounding order of the team's sums).
+ *   chains       n_chains distinct handles of the same precision and device.
+ *   team_ctas    CTAs for each chain, 1 <= team_ctas[c] <= min(N, 1024)
+ *                (NULL: 1 each); the chain's per-CTA buffers grow as needed.  A one-CTA team keeps its recursion
+ *                vectors in shared memory when they fit (L <= 12 FP32, L <= 10 FP64).
+ *   n_accepted   host uint64[n_chains] or NULL.
+ *   decisions    host array of n_chains pointers to uint8[n_updates[c]] (the array
+ *                or any entry may be NULL); d_omega_trace likewise with double.
+ *   stream       cudaStream_t (NULL: the legacy default stream).
+ * The sum of team_ctas must fit on the device at once (GFMC_EINVAL otherwise,
+ * with the capacity); a chain whose device wait runs out reports GFMC_ETIMEOUT
+ * and the other chains still complete.  Magnetisations of completed sweeps are
+ * not returned by this call. */
+gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_updates, const int* team_ctas,
+                           uint64_t* n_accepted, uint8_t** decisions, double** d_omega_trace, void* stream);
+
 /* Budget, in SM clock cycles, of every bounded device wait of h's launches
  * (default 4e9, about two seconds); cycles > 0.  A wait that exceeds it ends
  * the launch with GFMC_ETIMEOUT. */

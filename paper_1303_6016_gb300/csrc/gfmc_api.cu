@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -35,6 +36,13 @@ struct gfmc_ctx {
     double* d_mag = nullptr;
     unsigned long long* d_nacc = nullptr;
     long long* d_nmag = nullptr;
+    // CTAs the per-CTA buffers (partials, flags, phase sums) are sized for
+    int cap_ncta = 0;
+    // tile plan of this chain for a team of team_tc CTAs (batch launches)
+    int team_tc = 0;
+    int* d_team_tiles = nullptr;
+    int* d_team_nptr = nullptr;
+    int* d_team_nidx = nullptr;
     std::string err;
 };
 
@@ -173,6 +181,43 @@ gfmc_status run_engine(gfmc_ctx* h, Params& P)
     return GFMC_OK;
 }
 
+void release(gfmc_ctx* h, void* q)
+{
+    if (!q) return;
+    cudaFree(q);
+    for (auto& a : h->allocs)
+        if (a == q) a = nullptr;
+}
+
+// Grow the per-CTA buffers of h to hold a team of tc CTAs.
+gfmc_status ensure_team_capacity(gfmc_ctx* h, int tc)
+{
+    if (tc <= h->cap_ncta) return GFMC_OK;
+    Params& P = h->P;
+    double *part = nullptr, *qp = nullptr, *mp = nullptr;
+    unsigned* fl = nullptr;
+    cudaError_t e;
+    if ((e = dalloc(h, &part, (size_t)P.nsteps * tc * gfmc::kEntries)) != cudaSuccess ||
+        (e = dalloc(h, &qp, 2 * (size_t)tc)) != cudaSuccess || (e = dalloc(h, &mp, 3 * (size_t)tc)) != cudaSuccess ||
+        (e = dalloc(h, &fl, (size_t)tc)) != cudaSuccess) {
+        release(h, part);
+        release(h, qp);
+        release(h, mp);
+        release(h, fl);
+        return cuda_fail(h, e, "growing per-CTA buffers");
+    }
+    release(h, P.partial);
+    release(h, P.qpart);
+    release(h, P.magpart);
+    release(h, P.flags);
+    P.partial = part;
+    P.qpart = qp;
+    P.magpart = mp;
+    P.flags = fl;
+    h->cap_ncta = tc;
+    return GFMC_OK;
+}
+
 gfmc_status refresh_hoppings(gfmc_ctx* h)
 {
     cudaError_t e = gfmc::launch_build_hoppings(h->P, h->stream);
@@ -277,6 +322,8 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
     P.M = M;
     P.nsteps = M / 2 - 1;
     P.ncta = ncta;
+    P.divL = (unsigned)(((1ull << 32) + (unsigned long long)L - 1) / (unsigned long long)L);
+    P.divLL = (unsigned)(((1ull << 32) + (unsigned long long)L * L - 1) / ((unsigned long long)L * L));
     P.t = t;
     P.chem = mu;
     P.beta = beta;
@@ -306,6 +353,7 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
         (e = dalloc(h, &h->d_nmag, 1)) != cudaSuccess)
         return bail(cuda_fail(h, e, "allocating chain state"));
     P.rbuf = rb;
+    h->cap_ncta = ncta;
     P.tile_start = d_ts;
     P.nbr_ptr = d_np;
     P.nbr_idx = d_ni;
@@ -480,6 +528,151 @@ gfmc_status gfmc_inject_stall(gfmc_t h, int enable)
     if (!h) return fail(nullptr, GFMC_EINVAL, "invalid handle");
     h->stall_next = enable != 0;
     return GFMC_OK;
+}
+
+gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_updates, const int* team_ctas,
+                           uint64_t* n_accepted, uint8_t** decisions, double** d_omega_trace, void* stream)
+{
+    if (!chains || n_chains < 1 || !n_updates) return fail(nullptr, GFMC_EINVAL, "need chains, n_chains >= 1, n_updates");
+    const int prec = chains[0] ? chains[0]->precision : -1;
+    const int dev = chains[0] ? chains[0]->device : -1;
+    for (int c = 0; c < n_chains; ++c) {
+        gfmc_ctx* h = chains[c];
+        if (!h) return fail(nullptr, GFMC_EINVAL, "chain %d is NULL", c);
+        for (int d = 0; d < c; ++d)
+            if (chains[d] == h) return fail(nullptr, GFMC_EINVAL, "chain %d appears twice", c);
+        if (h->precision != prec) return fail(nullptr, GFMC_EINVAL, "chain %d has another precision", c);
+        if (h->device != dev) return fail(nullptr, GFMC_EINVAL, "chain %d lives on another device", c);
+        if (n_updates[c] < 0) return fail(nullptr, GFMC_EINVAL, "n_updates[%d] < 0", c);
+        const int tc = team_ctas ? team_ctas[c] : 1;
+        const int tmax = std::min(h->N, 1024);
+        if (tc < 1 || tc > tmax) return fail(nullptr, GFMC_EINVAL, "team_ctas[%d] = %d outside [1, %d]", c, tc, tmax);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if ((e = cudaSetDevice(dev)) != cudaSuccess) return cuda_fail(nullptr, e, "cudaSetDevice");
+    const size_t vsz = prec == GFMC_PREC_FP64 ? sizeof(double2) : sizeof(float2);
+    // Shared memory: the largest resident lattice plus the work area of the largest M.
+    int work = 0;
+    for (int c = 0; c < n_chains; ++c) work = std::max(work, gfmc::engine_smem_bytes(chains[c]->M));
+    int dev_smem = 0;
+    if ((e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+        return cuda_fail(nullptr, e, "querying shared memory");
+    const int reserve = 20 * 1024;  // static shared memory of the kernel and the parameter copy
+    size_t vec_bytes = 0;
+    std::vector<int> resident(n_chains, 0);
+    for (int c = 0; c < n_chains; ++c) {
+        const int tc = team_ctas ? team_ctas[c] : 1;
+        const size_t vb = 2 * (size_t)gfmc::kVec * chains[c]->N * vsz;
+        if (tc == 1 && vb + work + reserve <= (size_t)dev_smem) {
+            resident[c] = 1;
+            vec_bytes = std::max(vec_bytes, (vb + 255) & ~(size_t)255);
+        }
+    }
+    const int smem = (int)vec_bytes + work;
+    int grid = 0;
+    for (int c = 0; c < n_chains; ++c) grid += team_ctas ? team_ctas[c] : 1;
+    int maxc = 0;
+    if ((e = gfmc::team_max_ctas(prec, smem, &maxc)) != cudaSuccess) return cuda_fail(nullptr, e, "team occupancy");
+    if (grid > maxc)
+        return fail(nullptr, GFMC_EINVAL, "the batch needs %d co-resident CTAs, the device holds %d at %d B of "
+                    "shared memory; run it in smaller parts", grid, maxc, smem);
+
+    std::vector<gfmc::TeamJob> jobs(n_chains);
+    int cta0 = 0;
+    for (int c = 0; c < n_chains; ++c) {
+        gfmc_ctx* h = chains[c];
+        const int tc = team_ctas ? team_ctas[c] : 1;
+        gfmc_status st = ensure_trace(h, std::max<int64_t>(n_updates[c], 1));
+        if (st == GFMC_OK) st = ensure_team_capacity(h, tc);
+        if (st != GFMC_OK) return fail(nullptr, st, "chain %d: %s", c, h->err.c_str());
+        if (h->team_tc != tc) {
+            std::vector<int> ts, np, ni;
+            if ((st = plan_tiles(h, tc, ts, np, ni)) != GFMC_OK) return fail(nullptr, st, "chain %d: %s", c, h->err.c_str());
+            for (int* q : {h->d_team_tiles, h->d_team_nptr, h->d_team_nidx})
+                if (q) {
+                    cudaFree(q);
+                    for (auto& a : h->allocs)
+                        if (a == q) a = nullptr;
+                }
+            h->d_team_tiles = h->d_team_nptr = h->d_team_nidx = nullptr;
+            h->team_tc = 0;
+            if ((e = dalloc(h, &h->d_team_tiles, ts.size())) != cudaSuccess ||
+                (e = dalloc(h, &h->d_team_nptr, np.size())) != cudaSuccess ||
+                (e = dalloc(h, &h->d_team_nidx, ni.size() + 1)) != cudaSuccess ||
+                (e = cudaMemcpy(h->d_team_tiles, ts.data(), sizeof(int) * ts.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+                (e = cudaMemcpy(h->d_team_nptr, np.data(), sizeof(int) * np.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+                (!ni.empty() && (e = cudaMemcpy(h->d_team_nidx, ni.data(), sizeof(int) * ni.size(),
+                                                 cudaMemcpyHostToDevice)) != cudaSuccess))
+                return cuda_fail(nullptr, e, "uploading a team plan");
+            h->team_tc = tc;
+        }
+        Params P = h->P;
+        P.ncta = tc;
+        P.tile_start = h->d_team_tiles;
+        P.nbr_ptr = h->d_team_nptr;
+        P.nbr_idx = h->d_team_nidx;
+        P.mode = gfmc::MODE_SWEEP;
+        P.upd0 = h->counter;
+        P.n_updates = n_updates[c];
+        P.dec_out = h->d_dec;
+        P.domega_out = h->d_dom;
+        P.maxinc_out = h->d_maxinc;
+        P.mag_out = h->d_mag;
+        P.n_acc = h->d_nacc;
+        P.n_mag = h->d_nmag;
+        P.budget = h->budget;
+        P.stall = 0;
+        jobs[c].p = P;
+        jobs[c].cta0 = cta0;
+        jobs[c].vec_smem = resident[c];
+        cta0 += tc;
+        if ((e = cudaMemsetAsync(P.flags, 0, sizeof(unsigned) * tc, s)) != cudaSuccess ||
+            (e = cudaMemsetAsync(P.bar, 0, sizeof(unsigned) * 2, s)) != cudaSuccess ||
+            (e = cudaMemsetAsync(P.err, 0, sizeof(int) * 4, s)) != cudaSuccess ||
+            (e = cudaMemsetAsync(P.n_acc, 0, sizeof(unsigned long long), s)) != cudaSuccess)
+            return cuda_fail(nullptr, e, "clearing control words");
+    }
+    gfmc::TeamJob* d_jobs = nullptr;
+    if ((e = cudaMalloc(&d_jobs, sizeof(gfmc::TeamJob) * n_chains)) != cudaSuccess)
+        return cuda_fail(nullptr, e, "allocating the job table");
+    struct Free {
+        void* p;
+        ~Free() { cudaFree(p); }
+    } guard{d_jobs};
+    if ((e = cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(gfmc::TeamJob) * n_chains, cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+        return cuda_fail(nullptr, e, "uploading the job table");
+    e = prec == GFMC_PREC_FP64 ? gfmc::launch_team_f64(d_jobs, n_chains, grid, (int)vec_bytes, smem, s)
+                               : gfmc::launch_team_f32(d_jobs, n_chains, grid, (int)vec_bytes, smem, s);
+    if (e != cudaSuccess) return cuda_fail(nullptr, e, "launching the batch");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(nullptr, e, "batch execution");
+    gfmc_status result = GFMC_OK;
+    for (int c = 0; c < n_chains; ++c) {
+        gfmc_ctx* h = chains[c];
+        int err[4];
+        unsigned long long nacc = 0;
+        if ((e = cudaMemcpy(err, h->P.err, sizeof(err), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+            (e = cudaMemcpy(&nacc, h->d_nacc, sizeof(nacc), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(nullptr, e, "reading batch status");
+        if (err[0] != 0 && result == GFMC_OK) {
+            result = err[0] == gfmc::ERR_TIMEOUT ? GFMC_ETIMEOUT : err[0] == gfmc::ERR_NUMERIC ? GFMC_ENUMERIC : GFMC_ECUDA;
+            fail(nullptr, result, "chain %d: device error %d at stage %d", c, err[0], err[1]);
+            h->err = g_err;
+            continue;
+        }
+        if (err[0] != 0) continue;
+        if (n_accepted) n_accepted[c] = nacc;
+        if (decisions && decisions[c] && n_updates[c] > 0 &&
+            (e = cudaMemcpy(decisions[c], h->d_dec, (size_t)n_updates[c], cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(nullptr, e, "copying decisions");
+        if (d_omega_trace && d_omega_trace[c] && n_updates[c] > 0 &&
+            (e = cudaMemcpy(d_omega_trace[c], h->d_dom, sizeof(double) * n_updates[c], cudaMemcpyDeviceToHost)) !=
+                cudaSuccess)
+            return cuda_fail(nullptr, e, "copying Delta Omega traces");
+        h->counter += (uint64_t)n_updates[c];
+    }
+    return result;
 }
 
 const char* gfmc_last_error(gfmc_t h)

@@ -436,15 +436,233 @@ __device__ __forceinline__ void gram_smem_f64(const double2* sr, int T, double* 
     if (tid < kEntries) out[tid] = ((gsum[tid] + gsum[kEntries + tid]) + gsum[2 * kEntries + tid]) + gsum[3 * kEntries + tid];
 }
 
+// FP64 Gram sums accumulated over one staged chunk of up to kThreads sites
+// (thread (entry e, group g) as in gram_smem_f64), into the thread's re, im.
+__device__ __forceinline__ void gram_smem_acc(const double2* sr, int T, double& re, double& im)
+{
+    const int tid = threadIdx.x;
+    if (tid < 4 * 56) {
+        const int e = tid % 56, g = tid / 56;
+        const int pp = e % kPairs;
+        const int j = pair_j(pp), k = pair_k(pp);
+        const double2* xs = sr + j * kStage;
+        const double2* ys = sr + (e < kPairs ? k : kVec + k) * kStage;
+        for (int s = g; s < T; s += 4) {
+            const double2 x = xs[s], y = ys[s];
+            re = fma(x.x, y.x, re);
+            re = fma(x.y, y.y, re);
+            im = fma(x.x, y.y, im);
+            im = fma(-x.y, y.x, im);
+        }
+    }
+}
+
+// The four groups of gram_smem_acc added in order into out[kEntries].
+__device__ __forceinline__ void gram_smem_finish(double re, double im, double* gsum, double* out)
+{
+    const int tid = threadIdx.x;
+    if (tid < 4 * 56) {
+        const int e = tid % 56, g = tid / 56;
+        const int pp = e % kPairs;
+        if (e < kPairs && pair_j(pp) == pair_k(pp)) im = 0.0;
+        gsum[g * kEntries + 2 * e] = re;
+        gsum[g * kEntries + 2 * e + 1] = im;
+    }
+    __syncthreads();
+    if (tid < kEntries) out[tid] = ((gsum[tid] + gsum[kEntries + tid]) + gsum[2 * kEntries + tid]) + gsum[3 * kEntries + tid];
+}
+
+// Per-thread FP32 Gram accumulation of one site's 56 entries, compile-time indexed.
+template <class R, class R2, int E>
+__device__ __forceinline__ void gram_acc(const R2 (&rc)[kVec], const R2 (&rn)[kVec], R (&acc)[kEntries])
+{
+    constexpr int g = E / kPairs, pp = E % kPairs;
+    constexpr int j = pair_j(pp), k = pair_k(pp);
+    const R2 x = rc[j];
+    const R2 y = (g == 0) ? rc[k] : rn[k];
+    acc[2 * E] = fma(x.x, y.x, fma(x.y, y.y, acc[2 * E]));
+    if constexpr (!(g == 0 && j == k)) acc[2 * E + 1] = fma(x.x, y.y, fma(-x.y, y.x, acc[2 * E + 1]));
+    if constexpr (E + 1 < 2 * kPairs) gram_acc<R, R2, E + 1>(rc, rn, acc);
+}
+
+template <class R, int C>
+__device__ __forceinline__ void acc_chunk_reduce(const R (&acc)[kEntries], int lane, double* dst)
+{
+    R vals[32];
+#pragma unroll
+    for (int q = 0; q < 28; ++q) vals[q] = acc[28 * C + q];
+#pragma unroll
+    for (int q = 28; q < 32; ++q) vals[q] = (R)0;
+    const R s = warp_reduce_scatter32(vals, lane);
+    if (lane < 28) dst[28 * C + lane] = (double)s;
+}
+
+// Vector storage of a team: L2-resident global memory or the CTA's shared memory.
+struct GlobalVec {
+    template <class T> __device__ __forceinline__ T ld(const T* a) const { return ldcg2(a); }
+    template <class T> __device__ __forceinline__ void st(T* a, T v) const { stcg2(a, v); }
+};
+struct SmemVec {
+    template <class T> __device__ __forceinline__ T ld(const T* a) const { return *a; }
+    template <class T> __device__ __forceinline__ void st(T* a, T v) const { *a = v; }
+};
+
+// Neighbours of site i in the order +x, -x, +y, -y, +z, -z (exact magic-number division).
+__device__ __forceinline__ void site_nbrs(int i, int L, unsigned mL, unsigned mLL, int (&nb)[6])
+{
+    const int LL = L * L;
+    const int z = (int)__umulhi((unsigned)i, mLL);
+    const int r = i - z * LL;
+    const int y = (int)__umulhi((unsigned)r, mL);
+    const int x = r - y * L;
+    nb[0] = (x == L - 1) ? i - (L - 1) : i + 1;
+    nb[1] = (x == 0) ? i + (L - 1) : i - 1;
+    nb[2] = (y == L - 1) ? i - (L - 1) * L : i + L;
+    nb[3] = (y == 0) ? i + (L - 1) * L : i - L;
+    nb[4] = (z == L - 1) ? i - (L - 1) * LL : i + LL;
+    nb[5] = (z == 0) ? i + (L - 1) * LL : i - LL;
+}
+
+// Phase 0 and the stencil steps of one update for a team CTA whose tile may
+// hold any number of sites: every vector value lives in memory (vm), the
+// thread walks its sites s0 + tid, s0 + tid + kThreads, ...
+template <class R, class V>
+__device__ bool team_steps(const Params& p, int cta, unsigned phase, typename Cx<R>::T* buf0,
+                           typename Cx<R>::T* buf1, const int* s_loc, double (*red)[kEntries], double2* dyn,
+                           V vm)
+{
+    using R2 = typename Cx<R>::T;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int N = p.N, L = p.L;
+    const int s0 = p.tile_start[cta], s1 = p.tile_start[cta + 1];
+    const R2* hop;
+    if constexpr (sizeof(R) == 8) hop = (const R2*)p.hop64; else hop = (const R2*)p.hop32;
+
+    for (int i = s0 + tid; i < s1; i += kThreads) {
+        int nb[6];
+        site_nbrs(i, L, p.divL, p.divLL, nb);
+#pragma unroll
+        for (int v = 0; v < kVec; ++v) {
+            const int lv = s_loc[v];
+            R2 r0 = c_make<R2>(i == lv ? (R)1 : (R)0, (R)0);
+            R2 r1 = c_make<R2>(0, 0);
+#pragma unroll
+            for (int d = 0; d < 6; ++d)
+                if (nb[d] == lv) {
+                    const R2 h = hop_of(hop, N, i, d, nb[d]);
+                    r1.x += h.x;
+                    r1.y += h.y;
+                }
+            vm.st(buf0 + (size_t)v * N + i, r0);
+            vm.st(buf1 + (size_t)v * N + i, r1);
+        }
+    }
+    publish(p, cta, phase + 1);
+
+    for (int m = 1; m <= p.nsteps; ++m) {
+        if (!wait_neighbours(p, cta, phase + (unsigned)m, 100 + m)) return false;
+        const R2* rd = (m & 1) ? buf1 : buf0;  // r_m of every site
+        R2* wr = (m & 1) ? buf0 : buf1;        // r_{m-1}, overwritten by r_{m+1}
+        double* prow = p.partial + ((size_t)(m - 1) * p.ncta + cta) * kEntries;
+        if constexpr (sizeof(R) == 4) {
+            R acc[kEntries];
+#pragma unroll
+            for (int e = 0; e < kEntries; ++e) acc[e] = (R)0;
+            for (int i = s0 + tid; i < s1; i += kThreads) {
+                int nb[6];
+                site_nbrs(i, L, p.divL, p.divLL, nb);
+                R2 h[6];
+#pragma unroll
+                for (int d = 0; d < 6; ++d) h[d] = hop_of(hop, N, i, d, nb[d]);
+                R2 cur[kVec], nxt[kVec];
+#pragma unroll
+                for (int v = 0; v < kVec; ++v) {
+                    const R2* cv = rd + (size_t)v * N;
+                    R2 a = c_make<R2>(0, 0);
+#pragma unroll
+                    for (int d = 0; d < 6; ++d) c_fma(a, h[d], vm.ld(cv + nb[d]));
+                    cur[v] = vm.ld(cv + i);
+                    const R2 pv = vm.ld(wr + (size_t)v * N + i);
+                    nxt[v] = c_make<R2>(fma((R)2, a.x, -pv.x), fma((R)2, a.y, -pv.y));
+                    if (m < p.nsteps) vm.st(wr + (size_t)v * N + i, nxt[v]);
+                }
+                gram_acc<R, R2, 0>(cur, nxt, acc);
+            }
+            publish(p, cta, phase + (unsigned)m + 1u);
+            acc_chunk_reduce<R, 0>(acc, lane, red[warp]);
+            acc_chunk_reduce<R, 1>(acc, lane, red[warp]);
+            acc_chunk_reduce<R, 2>(acc, lane, red[warp]);
+            acc_chunk_reduce<R, 3>(acc, lane, red[warp]);
+            __syncthreads();
+            if (tid < kEntries) {
+                double sum = 0.0;
+#pragma unroll
+                for (int w = 0; w < kWarps; ++w) sum += red[w][tid];
+                prow[tid] = sum;
+            }
+        } else {
+            double re = 0.0, im = 0.0;
+            const int T = s1 - s0;
+            const int nch = (T + kThreads - 1) / kThreads;
+            for (int c = 0; c < nch; ++c) {
+                const int s = c * kThreads + tid;
+                const int i = s0 + s;
+                R2 cur[kVec], nxt[kVec];
+                if (s < T) {
+                    int nb[6];
+                    site_nbrs(i, L, p.divL, p.divLL, nb);
+                    R2 h[6];
+#pragma unroll
+                    for (int d = 0; d < 6; ++d) h[d] = hop_of(hop, N, i, d, nb[d]);
+#pragma unroll
+                    for (int v = 0; v < kVec; ++v) {
+                        const R2* cv = rd + (size_t)v * N;
+                        R2 a = c_make<R2>(0, 0);
+#pragma unroll
+                        for (int d = 0; d < 6; ++d) c_fma(a, h[d], vm.ld(cv + nb[d]));
+                        cur[v] = vm.ld(cv + i);
+                        const R2 pv = vm.ld(wr + (size_t)v * N + i);
+                        nxt[v] = c_make<R2>(fma((R)2, a.x, -pv.x), fma((R)2, a.y, -pv.y));
+                        if (m < p.nsteps) vm.st(wr + (size_t)v * N + i, nxt[v]);
+                    }
+                } else {
+#pragma unroll
+                    for (int v = 0; v < kVec; ++v) {
+                        cur[v] = c_make<R2>(0, 0);
+                        nxt[v] = c_make<R2>(0, 0);
+                    }
+                }
+#pragma unroll
+                for (int v = 0; v < kVec; ++v) {
+                    dyn[v * kStage + tid] = make_double2(cur[v].x, cur[v].y);
+                    dyn[(kVec + v) * kStage + tid] = make_double2(nxt[v].x, nxt[v].y);
+                }
+                __syncthreads();
+                gram_smem_acc(dyn, min(kThreads, T - c * kThreads), re, im);
+                __syncthreads();
+            }
+            publish(p, cta, phase + (unsigned)m + 1u);
+            gram_smem_finish(re, im, &red[0][0], prow);
+        }
+    }
+    return true;
+}
+
 // ---------------------------------------------------------------------------
 // the engine
 // ---------------------------------------------------------------------------
 
-template <class R>
-__global__ void __launch_bounds__(kThreads, 1) gfmc_engine(const Params p)
+// One chain on the CTAs [0, p.ncta) of a team; `cta` is this CTA's index in
+// the team.  VARIANT 0: one site per thread with the own-site vectors in
+// registers (a chain spread over the whole GPU).  VARIANT 1: any number of
+// sites per thread with all vectors in memory -- global (L2-resident) or, for
+// a one-CTA team whose lattice fits, shared memory (vec_smem != nullptr).
+// dyn is the CTA's work area in shared memory (FFT buffer, staged vectors).
+template <class R, int VARIANT>
+__device__ __forceinline__ void run_chain(const Params& p, const int cta, double2* dyn,
+                                          typename Cx<R>::T* vec_smem)
 {
     using R2 = typename Cx<R>::T;
-    extern __shared__ double2 dyn[];  // FFT buffer / phases (M double2)
     __shared__ double red[kWarps][kEntries];
     __shared__ double2 s_mu2[kWarps][2][kPairs];
     __shared__ double2 s_mu1[kPairs];
@@ -454,11 +672,11 @@ __global__ void __launch_bounds__(kThreads, 1) gfmc_engine(const Params p)
     __shared__ double s_dom;
     __shared__ int s_acc;
 
-    const int cta = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int N = p.N, L = p.L, M = p.M;
     const int s0 = p.tile_start[cta], s1 = p.tile_start[cta + 1];
     const int i = s0 + tid;
-    const bool active = i < s1;
+    const bool active = VARIANT == 0 && i < s1;
     const R2* hop = nullptr;
     if constexpr (sizeof(R) == 8) hop = (const R2*)p.hop64; else hop = (const R2*)p.hop32;
 
@@ -466,7 +684,7 @@ __global__ void __launch_bounds__(kThreads, 1) gfmc_engine(const Params p)
 #pragma unroll
     for (int d = 0; d < 6; ++d) nb[d] = active ? nbr_site(i, d, L) : 0;
 
-    R2* buf0 = (R2*)p.rbuf;
+    R2* buf0 = vec_smem ? vec_smem : (R2*)p.rbuf;
     R2* buf1 = buf0 + (size_t)kVec * N;
     const long long nupd = (p.mode == MODE_SWEEP) ? p.n_updates : 1;
     unsigned phase = 0;
@@ -509,77 +727,85 @@ __global__ void __launch_bounds__(kThreads, 1) gfmc_engine(const Params p)
         for (int d = 0; d < 6; ++d) h[d] = active ? hop_of(hop, N, i, d, nb[d]) : c_make<R2>(0, 0);
         __syncthreads();
 
-        // ---- phase 0: r_0 = e_{l_v} and r_1 = Htilde e_{l_v} of the own site, kept in registers;
-        //      only r_1 is published (no CTA ever reads another CTA's r_0) ----
-        R2 prv[kVec], cur[kVec];
-#pragma unroll
-        for (int v = 0; v < kVec; ++v) {
-            const int lv = s_loc[v];
-            prv[v] = c_make<R2>((active && i == lv) ? (R)1 : (R)0, (R)0);
-            R2 r1 = c_make<R2>(0, 0);
-#pragma unroll
-            for (int d = 0; d < 6; ++d)
-                if (active && nb[d] == lv) {
-                    r1.x += h[d].x;
-                    r1.y += h[d].y;
-                }
-            cur[v] = r1;
-            if (active) stcg2(buf1 + (size_t)v * N + i, r1);
-        }
-        publish(p, cta, phase + 1);
-
-        // ---- steps m = 1 .. M/2-1: r_{m+1} = 2 Htilde r_m - r_{m-1} and the Gram sums ----
-        for (int m = 1; m <= p.nsteps; ++m) {
-            if (!wait_neighbours(p, cta, phase + (unsigned)m, 100 + m)) return;
-            const R2* rd = (m & 1) ? buf1 : buf0;  // r_m of every site
-            R2* wr = (m & 1) ? buf0 : buf1;        // receives r_{m+1}; held r_{m-1}
-            R2 nxt[kVec];
-            if (active) {
-#pragma unroll
-                for (int v = 0; v < kVec; ++v) {
-                    const R2* cv = rd + (size_t)v * N;
-                    R2 acc = c_make<R2>(0, 0);
-#pragma unroll
-                    for (int d = 0; d < 6; ++d) c_fma(acc, h[d], ldcg2(cv + nb[d]));
-                    nxt[v] = c_make<R2>(fma((R)2, acc.x, -prv[v].x), fma((R)2, acc.y, -prv[v].y));
-                    if (m < p.nsteps) stcg2(wr + (size_t)v * N + i, nxt[v]);
-                }
-            } else {
-#pragma unroll
-                for (int v = 0; v < kVec; ++v) nxt[v] = c_make<R2>(0, 0);
-            }
-            double* prow = p.partial + ((size_t)(m - 1) * p.ncta + cta) * kEntries;
-            if constexpr (sizeof(R) == 8) {
-                // stage r_m, r_{m+1} of the own site for the shared-memory Gram sums
-#pragma unroll
-                for (int v = 0; v < kVec; ++v) {
-                    dyn[v * kStage + tid] = cur[v];
-                    dyn[(kVec + v) * kStage + tid] = nxt[v];
-                }
-            }
-            // r_{m+1} is stored: neighbours may start step m+1 while this CTA forms its dots
-            publish(p, cta, phase + (unsigned)m + 1u);
-            if constexpr (sizeof(R) == 8) {
-                gram_smem_f64(dyn, s1 - s0, &red[0][0], prow);
-            } else {
-                // Gram entries e = 0..55: e < 28 -> conj(r_m^j) r_m^k, else conj(r_m^j) r_{m+1}^k,
-                // (j, k) the upper pair e mod 28; 4 chunks of 14 complex values, warp butterfly.
-                gram_chunk_reduce<R, R2, 0>(cur, nxt, lane, red[warp]);
-                gram_chunk_reduce<R, R2, 1>(cur, nxt, lane, red[warp]);
-                gram_chunk_reduce<R, R2, 2>(cur, nxt, lane, red[warp]);
-                gram_chunk_reduce<R, R2, 3>(cur, nxt, lane, red[warp]);
-                __syncthreads();
-                if (tid < kEntries) {
-                    double sum = 0.0;
-#pragma unroll
-                    for (int w = 0; w < kWarps; ++w) sum += red[w][tid];
-                    prow[tid] = sum;
-                }
-            }
-#pragma unroll
+        if constexpr (VARIANT == 0) {
+            // ---- phase 0: r_0 = e_{l_v} and r_1 = Htilde e_{l_v} of the own site, kept in registers;
+            //      only r_1 is published (no CTA ever reads another CTA's r_0) ----
+            R2 prv[kVec], cur[kVec];
+    #pragma unroll
             for (int v = 0; v < kVec; ++v) {
-                prv[v] = cur[v];
-                cur[v] = nxt[v];
+                const int lv = s_loc[v];
+                prv[v] = c_make<R2>((active && i == lv) ? (R)1 : (R)0, (R)0);
+                R2 r1 = c_make<R2>(0, 0);
+    #pragma unroll
+                for (int d = 0; d < 6; ++d)
+                    if (active && nb[d] == lv) {
+                        r1.x += h[d].x;
+                        r1.y += h[d].y;
+                    }
+                cur[v] = r1;
+                if (active) stcg2(buf1 + (size_t)v * N + i, r1);
+            }
+            publish(p, cta, phase + 1);
+
+            // ---- steps m = 1 .. M/2-1: r_{m+1} = 2 Htilde r_m - r_{m-1} and the Gram sums ----
+            for (int m = 1; m <= p.nsteps; ++m) {
+                if (!wait_neighbours(p, cta, phase + (unsigned)m, 100 + m)) return;
+                const R2* rd = (m & 1) ? buf1 : buf0;  // r_m of every site
+                R2* wr = (m & 1) ? buf0 : buf1;        // receives r_{m+1}; held r_{m-1}
+                R2 nxt[kVec];
+                if (active) {
+    #pragma unroll
+                    for (int v = 0; v < kVec; ++v) {
+                        const R2* cv = rd + (size_t)v * N;
+                        R2 acc = c_make<R2>(0, 0);
+    #pragma unroll
+                        for (int d = 0; d < 6; ++d) c_fma(acc, h[d], ldcg2(cv + nb[d]));
+                        nxt[v] = c_make<R2>(fma((R)2, acc.x, -prv[v].x), fma((R)2, acc.y, -prv[v].y));
+                        if (m < p.nsteps) stcg2(wr + (size_t)v * N + i, nxt[v]);
+                    }
+                } else {
+    #pragma unroll
+                    for (int v = 0; v < kVec; ++v) nxt[v] = c_make<R2>(0, 0);
+                }
+                double* prow = p.partial + ((size_t)(m - 1) * p.ncta + cta) * kEntries;
+                if constexpr (sizeof(R) == 8) {
+                    // stage r_m, r_{m+1} of the own site for the shared-memory Gram sums
+    #pragma unroll
+                    for (int v = 0; v < kVec; ++v) {
+                        dyn[v * kStage + tid] = cur[v];
+                        dyn[(kVec + v) * kStage + tid] = nxt[v];
+                    }
+                }
+                // r_{m+1} is stored: neighbours may start step m+1 while this CTA forms its dots
+                publish(p, cta, phase + (unsigned)m + 1u);
+                if constexpr (sizeof(R) == 8) {
+                    gram_smem_f64(dyn, s1 - s0, &red[0][0], prow);
+                } else {
+                    // Gram entries e = 0..55: e < 28 -> conj(r_m^j) r_m^k, else conj(r_m^j) r_{m+1}^k,
+                    // (j, k) the upper pair e mod 28; 4 chunks of 14 complex values, warp butterfly.
+                    gram_chunk_reduce<R, R2, 0>(cur, nxt, lane, red[warp]);
+                    gram_chunk_reduce<R, R2, 1>(cur, nxt, lane, red[warp]);
+                    gram_chunk_reduce<R, R2, 2>(cur, nxt, lane, red[warp]);
+                    gram_chunk_reduce<R, R2, 3>(cur, nxt, lane, red[warp]);
+                    __syncthreads();
+                    if (tid < kEntries) {
+                        double sum = 0.0;
+    #pragma unroll
+                        for (int w = 0; w < kWarps; ++w) sum += red[w][tid];
+                        prow[tid] = sum;
+                    }
+                }
+    #pragma unroll
+                for (int v = 0; v < kVec; ++v) {
+                    prv[v] = cur[v];
+                    cur[v] = nxt[v];
+                }
+            }
+        } else {
+            if (vec_smem) {
+                if (!team_steps<R>(p, cta, phase, buf0, buf1, s_loc, red, dyn, SmemVec{})) return;
+            } else {
+                if (!team_steps<R>(p, cta, phase, buf0, buf1, s_loc, red, dyn, GlobalVec{})) return;
             }
         }
         phase += (unsigned)p.nsteps + 1u;
@@ -767,14 +993,14 @@ __global__ void __launch_bounds__(kThreads, 1) gfmc_engine(const Params p)
         // ---- magnetisation after each completed sweep ----
         if ((upd + 1ull) % (unsigned long long)N == 0ull) {
             double sx = 0.0, sy = 0.0, sz = 0.0;
-            if (active) {
-                const double th = __ldcg(p.spins + 2 * i), ph = __ldcg(p.spins + 2 * i + 1);
+            for (int si = s0 + tid; si < s1; si += kThreads) {
+                const double th = __ldcg(p.spins + 2 * si), ph = __ldcg(p.spins + 2 * si + 1);
                 double st, ct, sp, cp;
                 sincos(th, &st, &ct);
                 sincos(ph, &sp, &cp);
-                sx = st * cp;
-                sy = st * sp;
-                sz = ct;
+                sx += st * cp;
+                sy += st * sp;
+                sz += ct;
             }
             double a0, b0;
             block_sum_max(sx, 0.0, &a0, &b0);
@@ -800,6 +1026,37 @@ __global__ void __launch_bounds__(kThreads, 1) gfmc_engine(const Params p)
         *p.n_acc = nacc;
         *p.n_mag = nmag;
     }
+}
+
+// A single chain spread over the whole GPU.
+template <class R>
+__global__ void __launch_bounds__(kThreads, 1) gfmc_engine(const Params p)
+{
+    extern __shared__ double2 dyn[];
+    run_chain<R, 0>(p, blockIdx.x, dyn, nullptr);
+}
+
+// A batch of chains, each on its own team of CTAs (jobs sorted by cta0).
+// The dynamic shared memory holds [vector area of vec_bytes][work area].
+template <class R>
+__global__ void __launch_bounds__(kThreads, 1) gfmc_team_engine(const TeamJob* __restrict__ jobs, int njobs,
+                                                                 int vec_bytes)
+{
+    extern __shared__ double2 dyn_all[];
+    __shared__ Params sp;
+    __shared__ int s_job, s_cta, s_vs;
+    if (threadIdx.x == 0) {
+        int j = 0;
+        while (j + 1 < njobs && jobs[j + 1].cta0 <= (int)blockIdx.x) ++j;
+        s_job = j;
+        s_cta = (int)blockIdx.x - jobs[j].cta0;
+        s_vs = jobs[j].vec_smem;
+        sp = jobs[j].p;
+    }
+    __syncthreads();
+    using R2 = typename Cx<R>::T;
+    R2* vs = s_vs ? (R2*)dyn_all : nullptr;
+    run_chain<R, 1>(sp, s_cta, dyn_all + vec_bytes / (int)sizeof(double2), vs);
 }
 
 }  // namespace gfmc

@@ -25,6 +25,7 @@ enum ErrCode : int { ERR_NONE = 0, ERR_TIMEOUT = 4, ERR_NUMERIC = 5 };
 struct Params {
     // lattice and model
     int L, N, M, nsteps, ncta;
+    unsigned divL, divLL;  // ceil(2^32 / L), ceil(2^32 / L^2): exact i / L, i / L^2 for i < N
     double t, chem, beta, a;
 
     // chain state
@@ -78,9 +79,21 @@ struct Params {
     long long* n_mag;          // [1]
 };
 
+// One chain of a batch launch: its parameters (ncta = its team size, tile plan
+// for that team) and its CTAs [cta0, cta0 + p.ncta) of the grid.
+struct TeamJob {
+    Params p;
+    int cta0;
+    int vec_smem;  // the chain's recursion vectors live in the CTA's shared memory
+    int pad[2];
+};
+
 // Launchers (defined in the kernel translation units).
 cudaError_t launch_engine_f64(const Params& p, cudaStream_t s);
 cudaError_t launch_engine_f32(const Params& p, cudaStream_t s);
+cudaError_t launch_team_f64(const TeamJob* d_jobs, int njobs, int grid, int vec_bytes, int smem, cudaStream_t s);
+cudaError_t launch_team_f32(const TeamJob* d_jobs, int njobs, int grid, int vec_bytes, int smem, cudaStream_t s);
+cudaError_t team_max_ctas(int precision, int smem, int* out);
 int engine_smem_bytes(int M);
 cudaError_t engine_max_ctas(int precision, int M, int* out);
 cudaError_t launch_build_hoppings(const Params& p, cudaStream_t s);

@@ -29,3 +29,22 @@ cudaError_t engine_max_ctas_f64(int M, int* out)
 }
 
 }  // namespace gfmc
+
+namespace gfmc {
+
+cudaError_t launch_team_f64(const TeamJob* d_jobs, int njobs, int grid, int vec_bytes, int smem, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(gfmc_team_engine<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    void* args[] = {(void*)&d_jobs, (void*)&njobs, (void*)&vec_bytes};
+    return cudaLaunchCooperativeKernel((void*)gfmc_team_engine<double>, dim3(grid), dim3(kThreads), args, (size_t)smem, s);
+}
+
+cudaError_t team_max_ctas_f64(int smem, int* out)
+{
+    cudaError_t e = cudaFuncSetAttribute(gfmc_team_engine<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, gfmc_team_engine<double>, kThreads, smem);
+}
+
+}  // namespace gfmc

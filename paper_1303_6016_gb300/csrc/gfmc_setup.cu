@@ -10,6 +10,20 @@ namespace gfmc {
 
 cudaError_t engine_max_ctas_f64(int M, int* out);
 cudaError_t engine_max_ctas_f32(int M, int* out);
+cudaError_t team_max_ctas_f64(int smem, int* out);
+cudaError_t team_max_ctas_f32(int smem, int* out);
+
+cudaError_t team_max_ctas(int precision, int smem, int* out)
+{
+    int per_sm = 0;
+    cudaError_t e = precision == 0 ? team_max_ctas_f64(smem, &per_sm) : team_max_ctas_f32(smem, &per_sm);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    *out = per_sm * sms;
+    return cudaSuccess;
+}
 
 // Dynamic shared memory of the engine: the FFT buffer (M double2) or the
 // staged own-site vectors of the FP64 Gram sums (14 x kStage double2).

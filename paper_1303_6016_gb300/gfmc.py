@@ -29,7 +29,7 @@ KERNELS = {"jackson": 0, "lorentz": 1}
 EXPORTS = ("gfmc_default_options", "gfmc_create", "gfmc_moments", "gfmc_delta_omega",
            "gfmc_updates", "gfmc_sweep", "gfmc_get_spins", "gfmc_set_state", "gfmc_get_counter",
            "gfmc_set_wait_budget", "gfmc_inject_stall", "gfmc_last_error", "gfmc_destroy",
-           "gfmc_delta_omega_noalloc")
+           "gfmc_delta_omega_noalloc", "gfmc_run_batch")
 
 
 class GfmcError(RuntimeError):
@@ -81,6 +81,10 @@ def load(path: str = LIB_PATH):
                                            ctypes.c_double, i64, ctypes.c_double, ctypes.c_double, vp, vp,
                                            ctypes.c_char_p, ctypes.c_size_t]
     L.gfmc_delta_omega_noalloc.restype = ctypes.c_int
+    L.gfmc_run_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(u64), ctypes.POINTER(ctypes.POINTER(ctypes.c_uint8)),
+                                 ctypes.POINTER(ctypes.POINTER(ctypes.c_double)), vp]
+    L.gfmc_run_batch.restype = ctypes.c_int
     for name in ("gfmc_create", "gfmc_moments", "gfmc_delta_omega", "gfmc_updates", "gfmc_sweep",
                  "gfmc_get_spins", "gfmc_set_state", "gfmc_get_counter", "gfmc_set_wait_budget",
                  "gfmc_inject_stall"):
@@ -221,3 +225,25 @@ class Chain:
         c = ctypes.c_uint64(0)
         self._check(self._lib.gfmc_get_counter(self._h, ctypes.byref(c)))
         return int(c.value)
+
+
+def run_batch(chains, n_updates, team_ctas=None, trace=True, stream=None) -> list:
+    """One launch over several chains (each on its own team of CTAs).
+    Returns one dict per chain with n_accepted and, if trace, the decisions and
+    Delta Omega trace."""
+    lib = load()
+    n = len(chains)
+    H = (ctypes.c_void_p * n)(*[c._h.value for c in chains])
+    NU = (ctypes.c_int64 * n)(*[int(u) for u in (n_updates if hasattr(n_updates, "__len__") else [n_updates] * n)])
+    TC = (ctypes.c_int * n)(*[int(t) for t in team_ctas]) if team_ctas is not None else None
+    acc = (ctypes.c_uint64 * n)()
+    decs = [np.zeros(int(NU[c]), dtype=np.uint8) for c in range(n)]
+    doms = [np.zeros(int(NU[c]), dtype=np.float64) for c in range(n)]
+    DP = (ctypes.POINTER(ctypes.c_uint8) * n)(*[d.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)) for d in decs])
+    OP = (ctypes.POINTER(ctypes.c_double) * n)(*[_dp(d) for d in doms])
+    if stream is None:
+        stream = current_stream_handle()
+    st = lib.gfmc_run_batch(H, n, NU, TC, acc, DP if trace else None, OP if trace else None, stream)
+    if st != GFMC_OK:
+        raise GfmcError(st, lib.gfmc_last_error(None).decode())
+    return [{"n_accepted": int(acc[c]), "decisions": decs[c], "d_omega": doms[c]} for c in range(n)]
