@@ -199,6 +199,49 @@ def sweep_latency(gfmc, inputs, stream, L, M, precision, sweeps, warmup=2):
             "p99_ms": p99}
 
 
+def run_batching(stream, steps, warmup, updates, flush):
+    """64 independent FP32-mixed chains, L from {8,12,16,24,32}, T ~ U[0.02, 0.2],
+    M = 1024, in team-engine launches planned by the autotuner; a step runs
+    `updates` updates of every chain."""
+    import torch
+    from paper_1303_6016_gb300 import batch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    chains, Ls, Ts = batch.c4_chains(M=1024)
+    tuner = batch.Autotuner(M=1024, precision="fp32_mixed")
+    runner = batch.BatchRunner(chains, tuner)
+    plan = runner.plan([updates] * len(chains))
+    tune_s = time.perf_counter() - t0
+    for _ in range(warmup):
+        runner.run(updates)
+    per = []
+    for k in range(steps):
+        flush.fill_(k)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        runner.run(updates)
+        e.record()
+        e.synchronize()
+        per.append(s.elapsed_time(e))
+    total = sum(per)
+    teams = {}
+    for w, tc in plan:
+        for i, t in zip(w, tc):
+            teams.setdefault(int(Ls[i]), set()).add(int(t))
+    n = len(chains)
+    _, bytes_u = zip(*[update_work(int(L), 1024, 4) for L in Ls])
+    for ch in chains:
+        ch.close()
+    return {"value": n * updates * steps / (total / 1000.0), "unit": UNIT, "chains": n,
+            "updates_per_chain_per_step": updates, "ms_per_step": total / steps,
+            "launches_per_step": len(plan), "team_ctas_by_L": {str(k): sorted(v) for k, v in sorted(teams.items())},
+            "lattice_counts": {str(int(L)): int((Ls == L).sum()) for L in sorted(set(Ls.tolist()))},
+            "stencil_gbs": sum(bytes_u) * updates / (total / steps / 1000.0) / 1e9,
+            "autotune_s": tune_s,
+            "config": "64 chains, L uniform from {8,12,16,24,32} (seed 4), T uniform in [0.02, 0.2] t, "
+                      "mu = -2t, M = 1024, FP32-mixed, spins uniform (seed = chain index)"}
+
+
 def time_device(ch, stream, U, steps, warmup, flush, dist, sampler=None):
     """Device-timed steps: CUDA events on the chain's stream around each step,
     a 256 MiB L2 flush between steps outside the events."""
@@ -321,6 +364,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-latency", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-updates", type=int, default=4)
     ap.add_argument("--latency-sweeps", type=int, default=20)
     args = ap.parse_args()
     if args.warmup < 3:
@@ -397,6 +442,9 @@ def main():
             "gpu_launches": args.steps,
         }
         chm.close()
+
+    if not args.no_batch:
+        line["batching"] = run_batching(stream, max(3, args.steps // 2), 3, args.batch_updates, flush)
 
     if not args.no_latency:
         line["sweep_latency"] = [sweep_latency(gfmc, inputs, stream, 8, M, prec, args.latency_sweeps)
