@@ -79,7 +79,9 @@ void gfmc_default_options(gfmc_options* opt);
 
 /* Create a chain (Sec. 2.1: the spin configuration and H({S}); Sec. 3.3.2:
  * H and the spins are kept resident in device memory).
- *   L      lattice edge, 3 <= L <= 42 (N = L^3 <= 74088).
+ *   L      lattice edge, 3 <= L <= 64 (up to N = 262144; device memory
+ *          permitting).  Chains with more sites than 256 x their CTAs run
+ *          every call on the engine's multi-site variant.
  *   spins  host double[N][2] (theta, phi), copied.
  *   t      hopping amplitude, nonzero and finite.
  *   mu     chemical potential (finite).
@@ -158,6 +160,47 @@ gfmc_status gfmc_get_counter(gfmc_t h, uint64_t* update_counter);
  * not returned by this call. */
 gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_updates, const int* team_ctas,
                            uint64_t* n_accepted, uint8_t** decisions, double** d_omega_trace, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Serving loop: a device-resident request loop over many chains.
+ * A server is one persistent launch whose CTAs are split into slots.  Each
+ * slot runs the jobs posted to it -- "continue this chain by n updates",
+ * FP64 or FP32-mixed as the chain was created -- one after another, while the
+ * other slots run theirs, so jobs that arrive while others are on the GPU
+ * are admitted as soon as a slot is free and their work overlaps on the
+ * device (independent chains, Sec. 3.2).  Chain state stays in device memory
+ * across jobs.  A job gives the same results as gfmc_updates on the same
+ * chain, up to the rounding order of the slot's sums.  A slot that receives no
+ * work for about a second lets the launch end; the next submit or poll
+ * starts it again.
+ * ------------------------------------------------------------------------ */
+typedef struct gfmc_server_ctx* gfmc_server_t;
+
+/* n_slots slots of slot_ctas[k] CTAs each (their sum must fit on the device
+ * at once); max_M bounds the M of the chains the server will run. */
+gfmc_status gfmc_server_create(int n_slots, const int* slot_ctas, int max_M, gfmc_server_t* out);
+
+/* Post a job to an idle slot: n_updates >= 1 updates of chain h from its
+ * counter.  decisions (uint8[n_updates]) and d_omega_trace (double[n_updates])
+ * are host buffers filled when the job is polled done (either may be NULL);
+ * they must stay valid until then.  Until the job is polled done, h must not
+ * be used by any other call.  Returns at once (the job runs asynchronously). */
+gfmc_status gfmc_server_submit(gfmc_server_t s, int slot, gfmc_t h, int64_t n_updates, uint8_t* decisions,
+                               double* d_omega_trace);
+
+/* Non-blocking: *done = 1 when the slot has no job or its job has finished
+ * (then its results are in the buffers given at submit, the chain's counter
+ * has advanced and n_accepted, if not NULL, receives the accepted count);
+ * *done = 0 while the job runs.  A job whose device wait ran out returns
+ * GFMC_ETIMEOUT here. */
+gfmc_status gfmc_server_poll(gfmc_server_t s, int slot, int* done, uint64_t* n_accepted);
+
+/* Message of the last failed server call (NULL: of the last failed create). */
+const char* gfmc_server_last_error(gfmc_server_t s);
+
+/* Stop the server once its slots are idle and free it.  Jobs not yet polled
+ * are abandoned (their chains become usable again). */
+void gfmc_server_destroy(gfmc_server_t s);
 
 /* Budget, in SM clock cycles, of every bounded device wait of h's launches
  * (default 4e9, about two seconds); cycles > 0.  A wait that exceeds it ends

@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
+#include <cstddef>
 #include <cstring>
 #include <algorithm>
 #include <new>
@@ -38,11 +39,21 @@ struct gfmc_ctx {
     long long* d_nmag = nullptr;
     // CTAs the per-CTA buffers (partials, flags, phase sums) are sized for
     int cap_ncta = 0;
+    // more sites than threads of the chain's CTAs: single-chain calls run the
+    // team variant of the engine (several sites per thread) as a one-job launch
+    bool multi_site = false;
+    bool in_server = false;  // submitted to a server slot and not yet polled done
+    gfmc::TeamJob* d_job = nullptr;
     // tile plan of this chain for a team of team_tc CTAs (batch launches)
     int team_tc = 0;
     int* d_team_tiles = nullptr;
     int* d_team_nptr = nullptr;
     int* d_team_nidx = nullptr;
+    struct Plan {
+        int tc;
+        int *tiles, *nptr, *nidx;
+    };
+    std::vector<Plan> plans;  // every team plan built so far
     std::string err;
 };
 
@@ -132,13 +143,7 @@ gfmc_status ensure_trace(gfmc_ctx* h, long long n)
 {
     if (n <= h->trace_cap) return GFMC_OK;
     long long cap = n < 1024 ? 1024 : n;
-    void* bufs[4] = {h->d_dec, h->d_dom, h->d_maxinc, h->d_mag};
-    for (void* b : bufs)
-        if (b) {
-            cudaFree(b);
-            for (auto& a : h->allocs)
-                if (a == b) a = nullptr;
-        }
+    // the old buffers stay allocated until destroy (no device-wide synchronisation)
     h->d_dec = nullptr;
     h->d_dom = h->d_maxinc = h->d_mag = nullptr;
     cudaError_t e;
@@ -165,8 +170,20 @@ gfmc_status run_engine(gfmc_ctx* h, Params& P)
     P.budget = h->budget;
     P.stall = h->stall_next;
     h->stall_next = 0;
-    e = h->precision == GFMC_PREC_FP64 ? gfmc::launch_engine_f64(P, h->stream)
-                                        : gfmc::launch_engine_f32(P, h->stream);
+    if (h->multi_site) {
+        gfmc::TeamJob job{};
+        job.p = P;
+        job.cta0 = 0;
+        job.vec_smem = 0;
+        if ((e = cudaMemcpyAsync(h->d_job, &job, sizeof(job), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
+            return cuda_fail(h, e, "uploading the job");
+        const int smem = gfmc::engine_smem_bytes(P.M);
+        e = h->precision == GFMC_PREC_FP64 ? gfmc::launch_team_f64(h->d_job, 1, P.ncta, 0, smem, h->stream)
+                                            : gfmc::launch_team_f32(h->d_job, 1, P.ncta, 0, smem, h->stream);
+    } else {
+        e = h->precision == GFMC_PREC_FP64 ? gfmc::launch_engine_f64(P, h->stream)
+                                            : gfmc::launch_engine_f32(P, h->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(h, e, "launching the GFMC engine");
     int err[4] = {0, 0, 0, 0};
     if ((e = cudaMemcpyAsync(err, P.err, sizeof(err), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
@@ -181,13 +198,10 @@ gfmc_status run_engine(gfmc_ctx* h, Params& P)
     return GFMC_OK;
 }
 
-void release(gfmc_ctx* h, void* q)
-{
-    if (!q) return;
-    cudaFree(q);
-    for (auto& a : h->allocs)
-        if (a == q) a = nullptr;
-}
+// Retire a device buffer: it stays allocated (and listed in allocs) until the
+// handle is destroyed.  Freeing now would synchronise the whole device, which
+// waits for a running server launch.
+void release(gfmc_ctx*, void*) {}
 
 // Grow the per-CTA buffers of h to hold a team of tc CTAs.
 gfmc_status ensure_team_capacity(gfmc_ctx* h, int tc)
@@ -215,6 +229,38 @@ gfmc_status ensure_team_capacity(gfmc_ctx* h, int tc)
     P.magpart = mp;
     P.flags = fl;
     h->cap_ncta = tc;
+    return GFMC_OK;
+}
+
+// Select (building and uploading it the first time) the tile plan of h for a
+// team of tc CTAs.
+gfmc_status use_team_plan(gfmc_ctx* h, int tc)
+{
+    if (h->team_tc == tc) return GFMC_OK;
+    for (const auto& pl : h->plans)
+        if (pl.tc == tc) {
+            h->d_team_tiles = pl.tiles;
+            h->d_team_nptr = pl.nptr;
+            h->d_team_nidx = pl.nidx;
+            h->team_tc = tc;
+            return GFMC_OK;
+        }
+    std::vector<int> ts, np, ni;
+    gfmc_status st = plan_tiles(h, tc, ts, np, ni);
+    if (st != GFMC_OK) return st;
+    int *t = nullptr, *p = nullptr, *x = nullptr;
+    cudaError_t e;
+    if ((e = dalloc(h, &t, ts.size())) != cudaSuccess || (e = dalloc(h, &p, np.size())) != cudaSuccess ||
+        (e = dalloc(h, &x, ni.size() + 1)) != cudaSuccess ||
+        (e = cudaMemcpy(t, ts.data(), sizeof(int) * ts.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(p, np.data(), sizeof(int) * np.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (!ni.empty() && (e = cudaMemcpy(x, ni.data(), sizeof(int) * ni.size(), cudaMemcpyHostToDevice)) != cudaSuccess))
+        return cuda_fail(h, e, "uploading a team plan");
+    h->plans.push_back({tc, t, p, x});
+    h->d_team_tiles = t;
+    h->d_team_nptr = p;
+    h->d_team_nidx = x;
+    h->team_tc = tc;
     return GFMC_OK;
 }
 
@@ -301,18 +347,20 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
     int maxc = 0;
     if ((e = gfmc::engine_max_ctas(h->precision, M, &maxc)) != cudaSuccess)
         return bail(cuda_fail(h, e, "querying engine occupancy"));
+    int maxt = 0;
+    if ((e = gfmc::team_max_ctas(h->precision, gfmc::engine_smem_bytes(M), &maxt)) != cudaSuccess)
+        return bail(cuda_fail(h, e, "querying team occupancy"));
+    maxc = std::min(maxc, maxt);
     const int N = h->N;
-    const int need = (N + gfmc::kThreads - 1) / gfmc::kThreads;
     int ncta = opt.num_ctas;
     if (ncta <= 0) {
         ncta = N / 64;
-        if (ncta < need) ncta = need;
         if (ncta > maxc) ncta = maxc;
         if (ncta < 1) ncta = 1;
     }
-    if (ncta < need || ncta > maxc || ncta > N)
-        return bail(fail(h, GFMC_EINVAL, "num_ctas = %d: need %d <= num_ctas <= min(%d resident, N = %d)", ncta, need,
-                         maxc, N));
+    if (ncta > maxc || ncta > N)
+        return bail(fail(h, GFMC_EINVAL, "num_ctas = %d: need 1 <= num_ctas <= min(%d resident, N = %d)", ncta, maxc, N));
+    h->multi_site = (long long)ncta * gfmc::kThreads < N;
     std::vector<int> tstart, nptr, nidx;
     if ((st = plan_tiles(h, ncta, tstart, nptr, nidx)) != GFMC_OK) return bail(st);
 
@@ -369,6 +417,7 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
         return bail(cuda_fail(h, e, "building quadrature tables"));
     if ((st = refresh_hoppings(h)) != GFMC_OK) return bail(st);
     if ((st = ensure_trace(h, 1024)) != GFMC_OK) return bail(st);
+    if (h->multi_site && (e = dalloc(h, &h->d_job, 1)) != cudaSuccess) return bail(cuda_fail(h, e, "allocating a job"));
     *out = h;
     return GFMC_OK;
 }
@@ -586,27 +635,7 @@ gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_update
         gfmc_status st = ensure_trace(h, std::max<int64_t>(n_updates[c], 1));
         if (st == GFMC_OK) st = ensure_team_capacity(h, tc);
         if (st != GFMC_OK) return fail(nullptr, st, "chain %d: %s", c, h->err.c_str());
-        if (h->team_tc != tc) {
-            std::vector<int> ts, np, ni;
-            if ((st = plan_tiles(h, tc, ts, np, ni)) != GFMC_OK) return fail(nullptr, st, "chain %d: %s", c, h->err.c_str());
-            for (int* q : {h->d_team_tiles, h->d_team_nptr, h->d_team_nidx})
-                if (q) {
-                    cudaFree(q);
-                    for (auto& a : h->allocs)
-                        if (a == q) a = nullptr;
-                }
-            h->d_team_tiles = h->d_team_nptr = h->d_team_nidx = nullptr;
-            h->team_tc = 0;
-            if ((e = dalloc(h, &h->d_team_tiles, ts.size())) != cudaSuccess ||
-                (e = dalloc(h, &h->d_team_nptr, np.size())) != cudaSuccess ||
-                (e = dalloc(h, &h->d_team_nidx, ni.size() + 1)) != cudaSuccess ||
-                (e = cudaMemcpy(h->d_team_tiles, ts.data(), sizeof(int) * ts.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-                (e = cudaMemcpy(h->d_team_nptr, np.data(), sizeof(int) * np.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
-                (!ni.empty() && (e = cudaMemcpy(h->d_team_nidx, ni.data(), sizeof(int) * ni.size(),
-                                                 cudaMemcpyHostToDevice)) != cudaSuccess))
-                return cuda_fail(nullptr, e, "uploading a team plan");
-            h->team_tc = tc;
-        }
+        if ((st = use_team_plan(h, tc)) != GFMC_OK) return fail(nullptr, st, "chain %d: %s", c, h->err.c_str());
         Params P = h->P;
         P.ncta = tc;
         P.tile_start = h->d_team_tiles;
@@ -673,6 +702,252 @@ gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_update
         h->counter += (uint64_t)n_updates[c];
     }
     return result;
+}
+
+// ---------------------------------------------------------------------------
+// serving loop
+// ---------------------------------------------------------------------------
+
+struct gfmc_server_ctx {
+    int device = 0, nslots = 0, grid = 0, smem = 0, maxM = 0;
+    std::vector<int> slot_ctas, slot_cta0;
+    cudaStream_t run_stream = nullptr, post_stream = nullptr;
+    gfmc::SlotCtl* d_slots = nullptr;
+    unsigned* d_shutdown = nullptr;
+    volatile unsigned* h_done = nullptr;
+    unsigned* d_done = nullptr;
+    std::vector<unsigned> posted;
+    std::vector<gfmc_ctx*> chain;
+    std::vector<int64_t> nupd;
+    std::vector<uint8_t*> dec;
+    std::vector<double*> dom;
+    bool running = false;
+    long long idle_budget = 2000000000LL;
+    std::string err;
+};
+
+namespace {
+
+gfmc_status sfail(gfmc_server_ctx* s, gfmc_status st, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    if (s) s->err = buf;
+    g_err = buf;
+    return st;
+}
+
+// Relaunch the server if its previous launch ended (idle or never started).
+gfmc_status server_ensure_running(gfmc_server_ctx* s)
+{
+    cudaError_t e;
+    if (s->running) {
+        e = cudaStreamQuery(s->run_stream);
+        if (e == cudaErrorNotReady) return GFMC_OK;
+        if (e != cudaSuccess) return sfail(s, GFMC_ECUDA, "server execution: %s", cudaGetErrorString(e));
+        s->running = false;
+    }
+    for (int k = 0; k < s->nslots; ++k) {
+        const unsigned v = s->h_done[k];
+        if ((e = cudaMemcpyAsync(&s->d_slots[k].cmd, &v, sizeof(unsigned), cudaMemcpyHostToDevice, s->post_stream)) !=
+                cudaSuccess ||
+            (e = cudaStreamSynchronize(s->post_stream)) != cudaSuccess)
+            return sfail(s, GFMC_ECUDA, "resetting slot commands: %s", cudaGetErrorString(e));
+    }
+    gfmc::ServerArgs a;
+    a.slots = s->d_slots;
+    a.done = s->d_done;
+    a.shutdown = s->d_shutdown;
+    a.nslots = s->nslots;
+    a.idle_budget = s->idle_budget;
+    if ((e = gfmc::launch_server(a, s->grid, s->smem, s->run_stream)) != cudaSuccess)
+        return sfail(s, GFMC_ECUDA, "launching the server: %s", cudaGetErrorString(e));
+    s->running = true;
+    return GFMC_OK;
+}
+
+}  // namespace
+
+gfmc_status gfmc_server_create(int n_slots, const int* slot_ctas, int max_M, gfmc_server_t* out)
+{
+    if (!out) return fail(nullptr, GFMC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_slots < 1 || !slot_ctas) return fail(nullptr, GFMC_EINVAL, "need n_slots >= 1 and slot_ctas");
+    if (max_M < 16 || max_M > 4096 || (max_M & (max_M - 1)))
+        return fail(nullptr, GFMC_EINVAL, "max_M = %d must be a power of two in [16, 4096]", max_M);
+    gfmc_server_ctx* s = new (std::nothrow) gfmc_server_ctx;
+    if (!s) return fail(nullptr, GFMC_ENOMEM, "host allocation failed");
+    auto bail = [&](gfmc_status st) {
+        gfmc_server_destroy(s);
+        return st;
+    };
+    cudaError_t e;
+    if ((e = cudaGetDevice(&s->device)) != cudaSuccess) return bail(sfail(nullptr, GFMC_ECUDA, "cudaGetDevice"));
+    s->nslots = n_slots;
+    s->maxM = max_M;
+    s->smem = gfmc::engine_smem_bytes(max_M);
+    for (int k = 0; k < n_slots; ++k) {
+        if (slot_ctas[k] < 1 || slot_ctas[k] > 1024) return bail(sfail(nullptr, GFMC_EINVAL, "slot_ctas[%d] = %d", k, slot_ctas[k]));
+        s->slot_ctas.push_back(slot_ctas[k]);
+        s->slot_cta0.push_back(s->grid);
+        s->grid += slot_ctas[k];
+    }
+    int maxc = 0;
+    if ((e = gfmc::server_max_ctas(s->smem, &maxc)) != cudaSuccess) return bail(sfail(nullptr, GFMC_ECUDA, "server occupancy"));
+    if (s->grid > maxc)
+        return bail(sfail(nullptr, GFMC_EINVAL, "slots need %d co-resident CTAs, the device holds %d", s->grid, maxc));
+    if ((e = cudaStreamCreateWithFlags(&s->run_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&s->post_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaMalloc(&s->d_slots, sizeof(gfmc::SlotCtl) * n_slots)) != cudaSuccess ||
+        (e = cudaMalloc(&s->d_shutdown, sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaHostAlloc((void**)&s->h_done, sizeof(unsigned) * n_slots, cudaHostAllocMapped)) != cudaSuccess ||
+        (e = cudaHostGetDevicePointer((void**)&s->d_done, (void*)s->h_done, 0)) != cudaSuccess)
+        return bail(sfail(nullptr, e == cudaErrorMemoryAllocation ? GFMC_ENOMEM : GFMC_ECUDA, "server set-up: %s",
+                          cudaGetErrorString(e)));
+    std::vector<gfmc::SlotCtl> init(n_slots);
+    std::memset(init.data(), 0, sizeof(gfmc::SlotCtl) * n_slots);
+    for (int k = 0; k < n_slots; ++k) {
+        init[k].cta0 = s->slot_cta0[k];
+        s->h_done[k] = 0;
+    }
+    const unsigned zero = 0;
+    if ((e = cudaMemcpy(s->d_slots, init.data(), sizeof(gfmc::SlotCtl) * n_slots, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(s->d_shutdown, &zero, sizeof(zero), cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(sfail(nullptr, GFMC_ECUDA, "server set-up: %s", cudaGetErrorString(e)));
+    s->posted.assign(n_slots, 0);
+    s->chain.assign(n_slots, nullptr);
+    s->nupd.assign(n_slots, 0);
+    s->dec.assign(n_slots, nullptr);
+    s->dom.assign(n_slots, nullptr);
+    *out = s;
+    return GFMC_OK;
+}
+
+gfmc_status gfmc_server_submit(gfmc_server_t s, int slot, gfmc_t h, int64_t n_updates, uint8_t* decisions,
+                               double* d_omega_trace)
+{
+    if (!s) return fail(nullptr, GFMC_EINVAL, "invalid server");
+    if (slot < 0 || slot >= s->nslots) return sfail(s, GFMC_EINVAL, "slot %d outside [0, %d)", slot, s->nslots);
+    if (!h) return sfail(s, GFMC_EINVAL, "chain is NULL");
+    if (s->chain[slot]) return sfail(s, GFMC_EINVAL, "slot %d is busy", slot);
+    if (h->in_server) return sfail(s, GFMC_EINVAL, "the chain already has a job in a server");
+    if (h->device != s->device) return sfail(s, GFMC_EINVAL, "the chain lives on another device");
+    if (h->M > s->maxM) return sfail(s, GFMC_EINVAL, "chain M = %d above the server's %d", h->M, s->maxM);
+    if (n_updates < 1) return sfail(s, GFMC_EINVAL, "n_updates = %lld < 1", (long long)n_updates);
+    const int tc = s->slot_ctas[slot];
+    if (tc > h->N) return sfail(s, GFMC_EINVAL, "slot of %d CTAs for a chain of %d sites", tc, h->N);
+    gfmc_status st = ensure_trace(h, n_updates);
+    if (st == GFMC_OK) st = ensure_team_capacity(h, tc);
+    if (st != GFMC_OK) return sfail(s, st, "%s", h->err.c_str());
+    cudaError_t e;
+    if ((st = use_team_plan(h, tc)) != GFMC_OK) return sfail(s, st, "%s", h->err.c_str());
+    Params P = h->P;
+    P.ncta = tc;
+    P.tile_start = h->d_team_tiles;
+    P.nbr_ptr = h->d_team_nptr;
+    P.nbr_idx = h->d_team_nidx;
+    P.mode = gfmc::MODE_SWEEP;
+    P.upd0 = h->counter;
+    P.n_updates = n_updates;
+    P.dec_out = h->d_dec;
+    P.domega_out = h->d_dom;
+    P.maxinc_out = h->d_maxinc;
+    P.mag_out = h->d_mag;
+    P.n_acc = h->d_nacc;
+    P.n_mag = h->d_nmag;
+    P.budget = h->budget;
+    P.stall = 0;
+    // Clear the chain's control words and post the job with copies only: a
+    // memset kernel could wait for an SM the running server occupies.
+    static const unsigned zeros[256] = {};
+    unsigned long long zacc = 0;
+    struct Post {
+        int prec, cta0;
+        Params job;
+    } post{h->precision, s->slot_cta0[slot], P};
+    const unsigned seq = s->posted[slot] + 1u;
+    const size_t off = offsetof(gfmc::SlotCtl, prec);
+    static_assert(offsetof(gfmc::SlotCtl, cta0) == offsetof(gfmc::SlotCtl, prec) + sizeof(int), "layout");
+    static_assert(offsetof(gfmc::SlotCtl, job) == offsetof(Post, job) + offsetof(gfmc::SlotCtl, prec), "layout");
+    for (int at = 0; at < tc; at += 256) {
+        const int n = std::min(256, tc - at);
+        if ((e = cudaMemcpyAsync(P.flags + at, zeros, sizeof(unsigned) * n, cudaMemcpyHostToDevice, s->post_stream)) !=
+            cudaSuccess)
+            return sfail(s, GFMC_ECUDA, "clearing flags: %s", cudaGetErrorString(e));
+    }
+    if ((e = cudaMemcpyAsync(P.bar, zeros, sizeof(unsigned) * 2, cudaMemcpyHostToDevice, s->post_stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(P.err, zeros, sizeof(int) * 4, cudaMemcpyHostToDevice, s->post_stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(P.n_acc, &zacc, sizeof(zacc), cudaMemcpyHostToDevice, s->post_stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync((char*)(s->d_slots + slot) + off, &post, sizeof(post), cudaMemcpyHostToDevice,
+                             s->post_stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&s->d_slots[slot].seq, &seq, sizeof(seq), cudaMemcpyHostToDevice, s->post_stream)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(s->post_stream)) != cudaSuccess)
+        return sfail(s, GFMC_ECUDA, "posting the job: %s", cudaGetErrorString(e));
+    s->posted[slot] = seq;
+    s->chain[slot] = h;
+    s->nupd[slot] = n_updates;
+    s->dec[slot] = decisions;
+    s->dom[slot] = d_omega_trace;
+    h->in_server = true;
+    return server_ensure_running(s);
+}
+
+gfmc_status gfmc_server_poll(gfmc_server_t s, int slot, int* done, uint64_t* n_accepted)
+{
+    if (!s) return fail(nullptr, GFMC_EINVAL, "invalid server");
+    if (slot < 0 || slot >= s->nslots || !done) return sfail(s, GFMC_EINVAL, "bad slot %d or done pointer", slot);
+    *done = 0;
+    gfmc_ctx* h = s->chain[slot];
+    if (!h) {
+        *done = 1;
+        return GFMC_OK;
+    }
+    if (s->h_done[slot] != s->posted[slot]) return server_ensure_running(s);
+    cudaError_t e;
+    int err[4];
+    unsigned long long nacc = 0;
+    if ((e = cudaMemcpyAsync(err, h->P.err, sizeof(err), cudaMemcpyDeviceToHost, s->post_stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(&nacc, h->d_nacc, sizeof(nacc), cudaMemcpyDeviceToHost, s->post_stream)) != cudaSuccess ||
+        (s->dec[slot] && (e = cudaMemcpyAsync(s->dec[slot], h->d_dec, (size_t)s->nupd[slot], cudaMemcpyDeviceToHost,
+                                              s->post_stream)) != cudaSuccess) ||
+        (s->dom[slot] && (e = cudaMemcpyAsync(s->dom[slot], h->d_dom, sizeof(double) * s->nupd[slot],
+                                              cudaMemcpyDeviceToHost, s->post_stream)) != cudaSuccess) ||
+        (e = cudaStreamSynchronize(s->post_stream)) != cudaSuccess)
+        return sfail(s, GFMC_ECUDA, "reading the job: %s", cudaGetErrorString(e));
+    s->chain[slot] = nullptr;
+    h->in_server = false;
+    *done = 1;
+    if (err[0] != 0)
+        return sfail(s, err[0] == gfmc::ERR_TIMEOUT ? GFMC_ETIMEOUT : err[0] == gfmc::ERR_NUMERIC ? GFMC_ENUMERIC : GFMC_ECUDA,
+                     "job in slot %d: device error %d at stage %d", slot, err[0], err[1]);
+    h->counter += (uint64_t)s->nupd[slot];
+    if (n_accepted) *n_accepted = nacc;
+    return GFMC_OK;
+}
+
+const char* gfmc_server_last_error(gfmc_server_t s) { return s ? s->err.c_str() : g_err.c_str(); }
+
+void gfmc_server_destroy(gfmc_server_t s)
+{
+    if (!s) return;
+    if (s->d_shutdown && s->post_stream) {
+        const unsigned one = 1;
+        cudaMemcpyAsync(s->d_shutdown, &one, sizeof(one), cudaMemcpyHostToDevice, s->post_stream);
+        cudaStreamSynchronize(s->post_stream);
+    }
+    if (s->run_stream) cudaStreamSynchronize(s->run_stream);
+    for (int k = 0; k < s->nslots; ++k)
+        if (s->chain[k]) s->chain[k]->in_server = false;
+    if (s->d_slots) cudaFree(s->d_slots);
+    if (s->d_shutdown) cudaFree(s->d_shutdown);
+    if (s->h_done) cudaFreeHost((void*)s->h_done);
+    if (s->run_stream) cudaStreamDestroy(s->run_stream);
+    if (s->post_stream) cudaStreamDestroy(s->post_stream);
+    delete s;
 }
 
 const char* gfmc_last_error(gfmc_t h)

@@ -15,7 +15,7 @@ constexpr int kVec = 7;                  // local vectors: o and its 6 neighbour
 constexpr int kPairs = 28;               // upper-triangle pairs (j <= k) of the 7x7 block
 constexpr int kEntries = 112;            // 2 Gram blocks x 28 pairs x (re, im)
 constexpr int kMaxNbrCta = 64;           // neighbour CTAs a tile may depend on
-constexpr int kMaxL = 42;                // N = L^3 <= kThreads * SMs
+constexpr int kMaxL = 64;                // larger than kThreads x CTAs sites: team variant
 constexpr int kStage = kThreads + 1;     // row stride of the staged vectors (bank spread)
 
 enum Mode : int { MODE_MOMENTS = 0, MODE_DELTA = 1, MODE_SWEEP = 2 };
@@ -88,12 +88,32 @@ struct TeamJob {
     int pad[2];
 };
 
+// Mailbox of one slot of the serving loop (device memory).  The host writes
+// [prec, cta0, job] and then seq; the slot's CTA 0 relays seq through cmd.
+struct SlotCtl {
+    unsigned seq;  // sequence number of the last posted job (host)
+    unsigned cmd;  // slot CTA 0 -> the slot's other CTAs: job to run, or exit
+    int prec;      // 0 FP64, 1 FP32-mixed
+    int cta0;      // first CTA of the slot in the grid
+    Params job;
+};
+
+struct ServerArgs {
+    SlotCtl* slots;
+    unsigned* done;           // host-mapped: last completed sequence number per slot
+    const unsigned* shutdown; // nonzero: every slot exits when idle
+    int nslots;
+    long long idle_budget;    // cycles a slot waits for work before the launch ends
+};
+
 // Launchers (defined in the kernel translation units).
 cudaError_t launch_engine_f64(const Params& p, cudaStream_t s);
 cudaError_t launch_engine_f32(const Params& p, cudaStream_t s);
 cudaError_t launch_team_f64(const TeamJob* d_jobs, int njobs, int grid, int vec_bytes, int smem, cudaStream_t s);
 cudaError_t launch_team_f32(const TeamJob* d_jobs, int njobs, int grid, int vec_bytes, int smem, cudaStream_t s);
 cudaError_t team_max_ctas(int precision, int smem, int* out);
+cudaError_t launch_server(const ServerArgs& a, int grid, int smem, cudaStream_t s);
+cudaError_t server_max_ctas(int smem, int* out);
 int engine_smem_bytes(int M);
 cudaError_t engine_max_ctas(int precision, int M, int* out);
 cudaError_t launch_build_hoppings(const Params& p, cudaStream_t s);

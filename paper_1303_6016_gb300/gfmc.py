@@ -29,7 +29,8 @@ KERNELS = {"jackson": 0, "lorentz": 1}
 EXPORTS = ("gfmc_default_options", "gfmc_create", "gfmc_moments", "gfmc_delta_omega",
            "gfmc_updates", "gfmc_sweep", "gfmc_get_spins", "gfmc_set_state", "gfmc_get_counter",
            "gfmc_set_wait_budget", "gfmc_inject_stall", "gfmc_last_error", "gfmc_destroy",
-           "gfmc_delta_omega_noalloc", "gfmc_run_batch")
+           "gfmc_delta_omega_noalloc", "gfmc_run_batch", "gfmc_server_create", "gfmc_server_submit",
+           "gfmc_server_poll", "gfmc_server_last_error", "gfmc_server_destroy")
 
 
 class GfmcError(RuntimeError):
@@ -85,6 +86,16 @@ def load(path: str = LIB_PATH):
                                  ctypes.POINTER(u64), ctypes.POINTER(ctypes.POINTER(ctypes.c_uint8)),
                                  ctypes.POINTER(ctypes.POINTER(ctypes.c_double)), vp]
     L.gfmc_run_batch.restype = ctypes.c_int
+    L.gfmc_server_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(vp)]
+    L.gfmc_server_create.restype = ctypes.c_int
+    L.gfmc_server_submit.argtypes = [vp, ctypes.c_int, vp, i64, ctypes.POINTER(ctypes.c_uint8), d]
+    L.gfmc_server_submit.restype = ctypes.c_int
+    L.gfmc_server_poll.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(u64)]
+    L.gfmc_server_poll.restype = ctypes.c_int
+    L.gfmc_server_last_error.argtypes = [vp]
+    L.gfmc_server_last_error.restype = ctypes.c_char_p
+    L.gfmc_server_destroy.argtypes = [vp]
+    L.gfmc_server_destroy.restype = None
     for name in ("gfmc_create", "gfmc_moments", "gfmc_delta_omega", "gfmc_updates", "gfmc_sweep",
                  "gfmc_get_spins", "gfmc_set_state", "gfmc_get_counter", "gfmc_set_wait_budget",
                  "gfmc_inject_stall"):
@@ -247,3 +258,64 @@ def run_batch(chains, n_updates, team_ctas=None, trace=True, stream=None) -> lis
     if st != GFMC_OK:
         raise GfmcError(st, lib.gfmc_last_error(None).decode())
     return [{"n_accepted": int(acc[c]), "decisions": decs[c], "d_omega": doms[c]} for c in range(n)]
+
+
+class Server:
+    """A device-resident request loop (gfmc_server_t) with n slots of CTAs."""
+
+    def __init__(self, slot_ctas, max_M: int = 2048):
+        self._lib = load()
+        self.slot_ctas = [int(c) for c in slot_ctas]
+        arr = (ctypes.c_int * len(self.slot_ctas))(*self.slot_ctas)
+        h = ctypes.c_void_p()
+        st = self._lib.gfmc_server_create(len(self.slot_ctas), arr, int(max_M), ctypes.byref(h))
+        if st != GFMC_OK:
+            raise GfmcError(st, self._lib.gfmc_server_last_error(None).decode())
+        self._h = h
+        self._bufs = {}
+
+    def _check(self, st):
+        if st != GFMC_OK:
+            raise GfmcError(st, self._lib.gfmc_server_last_error(self._h).decode())
+
+    def submit(self, slot: int, chain: "Chain", n_updates: int, trace: bool = True):
+        n = int(n_updates)
+        dec = np.zeros(n if trace else 0, dtype=np.uint8)
+        dom = np.zeros(n if trace else 0, dtype=np.float64)
+        self._check(self._lib.gfmc_server_submit(
+            self._h, int(slot), chain._h, n,
+            dec.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)) if trace else None,
+            _dp(dom) if trace else None))
+        # the library writes into these buffers when the job is polled done:
+        # keep them alive until then (only once the submit has succeeded)
+        self._bufs[slot] = (dec, dom)
+
+    def poll(self, slot: int):
+        """None while the slot's job runs; else a dict with its results."""
+        done = ctypes.c_int(0)
+        acc = ctypes.c_uint64(0)
+        st = self._lib.gfmc_server_poll(self._h, int(slot), ctypes.byref(done), ctypes.byref(acc))
+        if st != GFMC_OK:
+            self._bufs.pop(slot, None)
+            raise GfmcError(st, self._lib.gfmc_server_last_error(self._h).decode())
+        if not done.value:
+            return None
+        dec, dom = self._bufs.pop(slot, (np.zeros(0, np.uint8), np.zeros(0)))
+        return {"n_accepted": int(acc.value), "decisions": dec, "d_omega": dom}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gfmc_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
