@@ -365,8 +365,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-latency", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--batch-updates", type=int, default=4)
-    ap.add_argument("--latency-sweeps", type=int, default=20)
+    ap.add_argument("--latency-sweeps", type=int, default=5)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -445,6 +446,10 @@ def main():
 
     if not args.no_batch:
         line["batching"] = run_batching(stream, max(3, args.steps // 2), 3, args.batch_updates, flush)
+
+    if not args.no_serving:
+        from paper_1303_6016_gb300 import serving
+        line["serving"] = serving.sweep(rates=(10, 100), seconds=3.0, K=2, drain_s=8.0)
 
     if not args.no_latency:
         line["sweep_latency"] = [sweep_latency(gfmc, inputs, stream, 8, M, prec, args.latency_sweeps)
