@@ -153,13 +153,17 @@ gfmc_status gfmc_get_counter(gfmc_t h, uint64_t* update_counter);
  *   n_accepted   host uint64[n_chains] or NULL.
  *   decisions    host array of n_chains pointers to uint8[n_updates[c]] (the array
  *                or any entry may be NULL); d_omega_trace likewise with double.
+ *   magnetization host array of n_chains pointers to double[n_updates[c]/N + 1]:
+ *                |sum_i S_i| / N after each sweep the chain completes in this call
+ *                (Algorithm 1); n_mag (host int64[n_chains]) receives how many.
+ *                Either may be NULL.
  *   stream       cudaStream_t (NULL: the legacy default stream).
  * The sum of team_ctas must fit on the device at once (GFMC_EINVAL otherwise,
  * with the capacity); a chain whose device wait runs out reports GFMC_ETIMEOUT
- * and the other chains still complete.  Magnetisations of completed sweeps are
- * not returned by this call. */
+ * and the other chains still complete. */
 gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_updates, const int* team_ctas,
-                           uint64_t* n_accepted, uint8_t** decisions, double** d_omega_trace, void* stream);
+                           uint64_t* n_accepted, uint8_t** decisions, double** d_omega_trace,
+                           double** magnetization, int64_t* n_mag, void* stream);
 
 /* ------------------------------------------------------------------------
  * Serving loop: a device-resident request loop over many chains.

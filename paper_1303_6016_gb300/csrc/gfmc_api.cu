@@ -580,7 +580,8 @@ gfmc_status gfmc_inject_stall(gfmc_t h, int enable)
 }
 
 gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_updates, const int* team_ctas,
-                           uint64_t* n_accepted, uint8_t** decisions, double** d_omega_trace, void* stream)
+                           uint64_t* n_accepted, uint8_t** decisions, double** d_omega_trace,
+                           double** magnetization, int64_t* n_mag, void* stream)
 {
     if (!chains || n_chains < 1 || !n_updates) return fail(nullptr, GFMC_EINVAL, "need chains, n_chains >= 1, n_updates");
     const int prec = chains[0] ? chains[0]->precision : -1;
@@ -659,7 +660,8 @@ gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_update
         if ((e = cudaMemsetAsync(P.flags, 0, sizeof(unsigned) * tc, s)) != cudaSuccess ||
             (e = cudaMemsetAsync(P.bar, 0, sizeof(unsigned) * 2, s)) != cudaSuccess ||
             (e = cudaMemsetAsync(P.err, 0, sizeof(int) * 4, s)) != cudaSuccess ||
-            (e = cudaMemsetAsync(P.n_acc, 0, sizeof(unsigned long long), s)) != cudaSuccess)
+            (e = cudaMemsetAsync(P.n_acc, 0, sizeof(unsigned long long), s)) != cudaSuccess ||
+            (e = cudaMemsetAsync(P.n_mag, 0, sizeof(long long), s)) != cudaSuccess)
             return cuda_fail(nullptr, e, "clearing control words");
     }
     gfmc::TeamJob* d_jobs = nullptr;
@@ -699,6 +701,14 @@ gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_update
             (e = cudaMemcpy(d_omega_trace[c], h->d_dom, sizeof(double) * n_updates[c], cudaMemcpyDeviceToHost)) !=
                 cudaSuccess)
             return cuda_fail(nullptr, e, "copying Delta Omega traces");
+        long long nm = 0;
+        if ((e = cudaMemcpy(&nm, h->d_nmag, sizeof(nm), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(nullptr, e, "reading magnetisation count");
+        if (n_updates[c] == 0) nm = 0;
+        if (n_mag) n_mag[c] = nm;
+        if (magnetization && magnetization[c] && nm > 0 &&
+            (e = cudaMemcpy(magnetization[c], h->d_mag, sizeof(double) * nm, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(nullptr, e, "copying magnetisations");
         h->counter += (uint64_t)n_updates[c];
     }
     return result;

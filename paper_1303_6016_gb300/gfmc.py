@@ -84,7 +84,8 @@ def load(path: str = LIB_PATH):
     L.gfmc_delta_omega_noalloc.restype = ctypes.c_int
     L.gfmc_run_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(u64), ctypes.POINTER(ctypes.POINTER(ctypes.c_uint8)),
-                                 ctypes.POINTER(ctypes.POINTER(ctypes.c_double)), vp]
+                                 ctypes.POINTER(ctypes.POINTER(ctypes.c_double)),
+                                 ctypes.POINTER(ctypes.POINTER(ctypes.c_double)), ctypes.POINTER(i64), vp]
     L.gfmc_run_batch.restype = ctypes.c_int
     L.gfmc_server_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(vp)]
     L.gfmc_server_create.restype = ctypes.c_int
@@ -252,12 +253,16 @@ def run_batch(chains, n_updates, team_ctas=None, trace=True, stream=None) -> lis
     doms = [np.zeros(int(NU[c]), dtype=np.float64) for c in range(n)]
     DP = (ctypes.POINTER(ctypes.c_uint8) * n)(*[d.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)) for d in decs])
     OP = (ctypes.POINTER(ctypes.c_double) * n)(*[_dp(d) for d in doms])
+    mags = [np.zeros(int(NU[c]) // chains[c].N + 2, dtype=np.float64) for c in range(n)]
+    MP = (ctypes.POINTER(ctypes.c_double) * n)(*[_dp(m) for m in mags])
+    NM = (ctypes.c_int64 * n)()
     if stream is None:
         stream = current_stream_handle()
-    st = lib.gfmc_run_batch(H, n, NU, TC, acc, DP if trace else None, OP if trace else None, stream)
+    st = lib.gfmc_run_batch(H, n, NU, TC, acc, DP if trace else None, OP if trace else None, MP, NM, stream)
     if st != GFMC_OK:
         raise GfmcError(st, lib.gfmc_last_error(None).decode())
-    return [{"n_accepted": int(acc[c]), "decisions": decs[c], "d_omega": doms[c]} for c in range(n)]
+    return [{"n_accepted": int(acc[c]), "decisions": decs[c], "d_omega": doms[c],
+             "magnetization": mags[c][: int(NM[c])]} for c in range(n)]
 
 
 class Server:
