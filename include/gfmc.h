@@ -54,6 +54,14 @@ typedef enum {
 
 enum { GFMC_PREC_FP64 = 0, GFMC_PREC_FP32_MIXED = 1 };
 enum { GFMC_KERNEL_JACKSON = 0, GFMC_KERNEL_LORENTZ = 1 };
+/* Vectors the Chebyshev recursion of an update runs on (Sec. 2.2, Eq. recursive):
+ * UNIT_VECTORS -- the 7 unit vectors of o and its neighbours, all 7x7 moments
+ *                 (independent of the proposal);
+ * PROPOSAL     -- the proposal's vectors |o> and |v> = Delta~|o> only: the
+ *                 paper's recursion on o, v, o+v, o+iv (Algorithm 1, Fig. 2)
+ *                 with the last two formed by linearity, so two recursions and
+ *                 <o|T_n|v> give all four sequences. */
+enum { GFMC_RECURSION_UNIT_VECTORS = 0, GFMC_RECURSION_PROPOSAL = 1 };
 
 typedef struct {
     /* GFMC_PREC_FP64: recursion vectors, stencil, moments and quadrature in FP64.
@@ -71,10 +79,14 @@ typedef struct {
     uint32_t chain_id;     /* second key word (XORed with the seed's high word) */
     void* stream;          /* cudaStream_t to run on; NULL = the legacy default stream */
     int num_ctas;          /* <= 0: chosen by the library */
+    /* GFMC_RECURSION_*: used by gfmc_delta_omega and gfmc_updates/gfmc_sweep of
+     * chains on at most 256 sites per CTA; gfmc_moments, batches and servers
+     * always use the unit vectors. */
+    int recursion;
 } gfmc_options;
 
 /* Fill *opt with the defaults (FP64, Jackson, a = 6.05|t|, seed 1, chain 0,
- * default stream, automatic CTA count). */
+ * default stream, automatic CTA count, unit-vector recursion). */
 void gfmc_default_options(gfmc_options* opt);
 
 /* Create a chain (Sec. 2.1: the spin configuration and H({S}); Sec. 3.3.2:

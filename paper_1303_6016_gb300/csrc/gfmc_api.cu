@@ -27,6 +27,7 @@ struct gfmc_ctx {
     uint64_t counter = 0;
     long long budget = 4000000000LL;
     int stall_next = 0;
+    int recursion = 0;  // GFMC_RECURSION_*
     Params P{};
     std::vector<void*> allocs;
     // growable output buffers of the sweep mode
@@ -181,8 +182,9 @@ gfmc_status run_engine(gfmc_ctx* h, Params& P)
         e = h->precision == GFMC_PREC_FP64 ? gfmc::launch_team_f64(h->d_job, 1, P.ncta, 0, smem, h->stream)
                                             : gfmc::launch_team_f32(h->d_job, 1, P.ncta, 0, smem, h->stream);
     } else {
-        e = h->precision == GFMC_PREC_FP64 ? gfmc::launch_engine_f64(P, h->stream)
-                                            : gfmc::launch_engine_f32(P, h->stream);
+        const int nv = (h->recursion == GFMC_RECURSION_PROPOSAL && P.mode != gfmc::MODE_MOMENTS) ? 2 : gfmc::kVec;
+        e = h->precision == GFMC_PREC_FP64 ? gfmc::launch_engine_f64(P, nv, h->stream)
+                                            : gfmc::launch_engine_f32(P, nv, h->stream);
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "launching the GFMC engine");
     int err[4] = {0, 0, 0, 0};
@@ -288,6 +290,7 @@ void gfmc_default_options(gfmc_options* opt)
     opt->chain_id = 0;
     opt->stream = nullptr;
     opt->num_ctas = 0;
+    opt->recursion = GFMC_RECURSION_UNIT_VECTORS;
 }
 
 gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double beta, int M,
@@ -308,6 +311,8 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
         return fail(nullptr, GFMC_EINVAL, "unknown precision %d", opt.precision);
     if (opt.kernel != GFMC_KERNEL_JACKSON && opt.kernel != GFMC_KERNEL_LORENTZ)
         return fail(nullptr, GFMC_EINVAL, "unknown kernel %d", opt.kernel);
+    if (opt.recursion != GFMC_RECURSION_UNIT_VECTORS && opt.recursion != GFMC_RECURSION_PROPOSAL)
+        return fail(nullptr, GFMC_EINVAL, "unknown recursion %d", opt.recursion);
     const double a = opt.spectral_scale > 0 ? opt.spectral_scale : 6.05 * std::fabs(t);
     if (!std::isfinite(a) || !(a > 6.0 * std::fabs(t)))
         return fail(nullptr, GFMC_EINVAL, "spectral scale a = %g must exceed 6|t| = %g", a, 6.0 * std::fabs(t));
@@ -329,6 +334,7 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
     h->seed = opt.seed;
     h->chain_id = opt.chain_id;
     h->stream = (cudaStream_t)opt.stream;
+    h->recursion = opt.recursion;
 
     gfmc_status st = check_spins(h, spins, h->N);
     if (st != GFMC_OK) {

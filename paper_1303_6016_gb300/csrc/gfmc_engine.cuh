@@ -251,6 +251,35 @@ template <class R> __device__ __forceinline__ R warp_reduce_scatter32(R (&v)[32]
     return v[0];
 }
 
+// Butterfly reduce-scatter of 8 values over a warp: on return lanes 4j..4j+3
+// hold the warp-wide sum of value j.
+template <class R> __device__ __forceinline__ R warp_reduce_scatter8(R (&v)[8], int lane)
+{
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const bool up = lane & 16;
+        R send = up ? v[i] : v[i + 4];
+        R keep = up ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool up = lane & 8;
+        R send = up ? v[i] : v[i + 2];
+        R keep = up ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    {
+        const bool up = lane & 4;
+        R send = up ? v[0] : v[1];
+        R keep = up ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    return v[0];
+}
+
 // Deterministic CTA-wide sum (and max) of one double per thread.
 __device__ __forceinline__ void block_sum_max(double s, double mx, double* out_s, double* out_m)
 {
@@ -658,10 +687,16 @@ __device__ bool team_steps(const Params& p, int cta, unsigned phase, typename Cx
 // sites per thread with all vectors in memory -- global (L2-resident) or, for
 // a one-CTA team whose lattice fits, shared memory (vec_smem != nullptr).
 // dyn is the CTA's work area in shared memory (FFT buffer, staged vectors).
-template <class R, int VARIANT>
+// NV: 7 -- the recursion runs on the 7 unit vectors of o and its neighbours
+// (proposal independent; all 7x7 moments).  2 -- it runs on the proposal's two
+// vectors |o> and |v> = Delta~|o> only: the paper's recursion on the
+// combined vectors o, v, o+v, o+iv (Algorithm 1) reduced by linearity to two
+// recursions and the cross product <o|T_n|v>; single-chain variant only.
+template <class R, int VARIANT, int NV = kVec>
 __device__ __forceinline__ void run_chain(const Params& p, const int cta, double2* dyn,
                                           typename Cx<R>::T* vec_smem)
 {
+    static_assert(NV == kVec || (NV == 2 && VARIANT == 0), "two-vector recursion: single-chain variant only");
     using R2 = typename Cx<R>::T;
     __shared__ double red[kWarps][kEntries];
     __shared__ double2 s_mu2[kWarps][2][kPairs];
@@ -671,6 +706,8 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
     __shared__ double s_draw[3];
     __shared__ double s_dom;
     __shared__ int s_acc;
+    __shared__ double s_vv0, s_vv1;
+    __shared__ double2 s_ov1;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int N = p.N, L = p.L, M = p.M;
@@ -727,7 +764,93 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
         for (int d = 0; d < 6; ++d) h[d] = active ? hop_of(hop, N, i, d, nb[d]) : c_make<R2>(0, 0);
         __syncthreads();
 
-        if constexpr (VARIANT == 0) {
+        if constexpr (VARIANT == 0 && NV == 2) {
+            // ---- phase 0: r_0^o = e_o, r_0^v = v = sum_k c_k e_{l_k}, r_1 = Htilde r_0 at the own site ----
+            const int lo = s_loc[0];
+            R2 cv6[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) cv6[k] = c_make<R2>((R)s_c[k + 1].x, (R)s_c[k + 1].y);
+            R2 prv[2], cur[2];
+            prv[0] = c_make<R2>((active && i == lo) ? (R)1 : (R)0, (R)0);
+            prv[1] = c_make<R2>(0, 0);
+            cur[0] = c_make<R2>(0, 0);
+            cur[1] = c_make<R2>(0, 0);
+            if (active) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k)
+                    if (i == s_loc[k + 1]) {
+                        prv[1].x += cv6[k].x;
+                        prv[1].y += cv6[k].y;
+                    }
+#pragma unroll
+                for (int d = 0; d < 6; ++d) {
+                    if (nb[d] == lo) {
+                        cur[0].x += h[d].x;
+                        cur[0].y += h[d].y;
+                    }
+#pragma unroll
+                    for (int k = 0; k < 6; ++k)
+                        if (nb[d] == s_loc[k + 1]) {
+                            const R2 hc = c_make<R2>(h[d].x * cv6[k].x - h[d].y * cv6[k].y,
+                                                     h[d].x * cv6[k].y + h[d].y * cv6[k].x);
+                            cur[1].x += hc.x;
+                            cur[1].y += hc.y;
+                        }
+                }
+                stcg2(buf1 + i, cur[0]);
+                stcg2(buf1 + (size_t)N + i, cur[1]);
+            }
+            publish(p, cta, phase + 1);
+
+            // ---- steps: two recursions and the 8 real products of the doubling ----
+            for (int m = 1; m <= p.nsteps; ++m) {
+                if (!wait_neighbours(p, cta, phase + (unsigned)m, 100 + m)) return;
+                const R2* rd = (m & 1) ? buf1 : buf0;
+                R2* wr = (m & 1) ? buf0 : buf1;
+                R2 nxt[2];
+                if (active) {
+#pragma unroll
+                    for (int v = 0; v < 2; ++v) {
+                        const R2* cv = rd + (size_t)v * N;
+                        R2 acc = c_make<R2>(0, 0);
+#pragma unroll
+                        for (int d = 0; d < 6; ++d) c_fma(acc, h[d], ldcg2(cv + nb[d]));
+                        nxt[v] = c_make<R2>(fma((R)2, acc.x, -prv[v].x), fma((R)2, acc.y, -prv[v].y));
+                        if (m < p.nsteps) stcg2(wr + (size_t)v * N + i, nxt[v]);
+                    }
+                } else {
+                    nxt[0] = c_make<R2>(0, 0);
+                    nxt[1] = c_make<R2>(0, 0);
+                }
+                double* prow = p.partial + ((size_t)(m - 1) * p.ncta + cta) * kEntries;
+                publish(p, cta, phase + (unsigned)m + 1u);
+                // |r_m^o|^2, |r_m^v|^2, <r_m^o|r_m^v>, Re<r_m^o|r_m+1^o>, Re<r_m^v|r_m+1^v>, <r_m^o|r_m+1^v>
+                const R2 a = cur[0], b = cur[1], na = nxt[0], nbv = nxt[1];
+                R v8[8];
+                v8[0] = fma(a.x, a.x, a.y * a.y);
+                v8[1] = fma(b.x, b.x, b.y * b.y);
+                v8[2] = fma(a.x, b.x, a.y * b.y);
+                v8[3] = fma(a.x, b.y, -(a.y * b.x));
+                v8[4] = fma(a.x, na.x, a.y * na.y);
+                v8[5] = fma(b.x, nbv.x, b.y * nbv.y);
+                v8[6] = fma(a.x, nbv.x, a.y * nbv.y);
+                v8[7] = fma(a.x, nbv.y, -(a.y * nbv.x));
+                const R s8 = warp_reduce_scatter8(v8, lane);
+                if ((lane & 3) == 0) red[warp][lane >> 2] = (double)s8;
+                __syncthreads();
+                if (tid < 8) {
+                    double sum = 0.0;
+#pragma unroll
+                    for (int w = 0; w < kWarps; ++w) sum += red[w][tid];
+                    prow[tid] = sum;
+                }
+#pragma unroll
+                for (int v = 0; v < 2; ++v) {
+                    prv[v] = cur[v];
+                    cur[v] = nxt[v];
+                }
+            }
+        } else if constexpr (VARIANT == 0) {
             // ---- phase 0: r_0 = e_{l_v} and r_1 = Htilde e_{l_v} of the own site, kept in registers;
             //      only r_1 is published (no CTA ever reads another CTA's r_0) ----
             R2 prv[kVec], cur[kVec];
@@ -824,6 +947,57 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
             s_mu1[tid] = s;
         }
         __syncthreads();
+        if constexpr (NV == 2) {
+            if (tid == 0) {
+                double v0 = 0.0;
+                double2 o1 = make_double2(0.0, 0.0);
+                for (int k = 1; k < 7; ++k) {
+                    v0 += s_c[k].x * s_c[k].x + s_c[k].y * s_c[k].y;  // <v|v>
+                    o1 = dadd(o1, dmul(s_c[k], s_mu1[k]));           // <o|Htilde|v>
+                }
+                s_vv0 = v0;
+                s_vv1 = combined_moment(1, s_mu1, s_c);             // <v|Htilde|v>
+                s_ov1 = o1;
+            }
+            __syncthreads();
+            const int gw = cta * kWarps + warp, TW = p.ncta * kWarps;
+            for (int item = gw; item <= p.nsteps; item += TW) {
+                double oo[2], vv[2];
+                double2 X[2];
+                if (item == 0) {
+                    oo[0] = 1.0;
+                    vv[0] = s_vv0;
+                    X[0] = make_double2(0.0, 0.0);
+                    oo[1] = 0.0;
+                    vv[1] = s_vv1;
+                    X[1] = s_ov1;
+                } else {
+                    const double* src = p.partial + (size_t)(item - 1) * p.ncta * kEntries;
+                    if (lane < 8) {
+                        double sum = 0.0;
+                        for (int c = 0; c < p.ncta; ++c) sum += __ldcg(src + (size_t)c * kEntries + lane);
+                        red[warp][lane] = sum;
+                    }
+                    __syncwarp();
+                    const double* e = red[warp];
+                    oo[0] = 2.0 * e[0] - 1.0;
+                    vv[0] = 2.0 * e[1] - s_vv0;
+                    X[0] = make_double2(2.0 * e[2], 2.0 * e[3]);
+                    oo[1] = 2.0 * e[4];
+                    vv[1] = 2.0 * e[5] - s_vv1;
+                    X[1] = make_double2(2.0 * e[6] - s_ov1.x, 2.0 * e[7] - s_ov1.y);
+                }
+                if (lane < 8) {
+                    const int sgn = lane >> 2, V = lane & 3, n = 2 * item + sgn;
+                    const double val = V == 0 ? oo[sgn] : V == 1 ? vv[sgn]
+                                     : V == 2 ? oo[sgn] + vv[sgn] + 2.0 * X[sgn].x
+                                              : oo[sgn] + vv[sgn] - 2.0 * X[sgn].y;
+                    const double gn = __ldcg(p.gker + n) * (n == 0 ? 0.5 : 1.0);
+                    p.fftin[(size_t)V * M + n] = dscale(gn * val, __ldcg(p.twc + n));
+                }
+                __syncwarp();
+            }
+        } else
         {
             const int gw = cta * kWarps + warp, TW = p.ncta * kWarps;
             for (int item = gw; item <= p.nsteps; item += TW) {
@@ -1029,11 +1203,11 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
 }
 
 // A single chain spread over the whole GPU.
-template <class R>
+template <class R, int NV = kVec>
 __global__ void __launch_bounds__(kThreads, 1) gfmc_engine(const Params p)
 {
     extern __shared__ double2 dyn[];
-    run_chain<R, 0>(p, blockIdx.x, dyn, nullptr);
+    run_chain<R, 0, NV>(p, blockIdx.x, dyn, nullptr);
 }
 
 // A batch of chains, each on its own team of CTAs (jobs sorted by cta0).

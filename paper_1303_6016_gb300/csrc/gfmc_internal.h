@@ -109,6 +109,9 @@ struct ServerArgs {
 // Launchers (defined in the kernel translation units).
 cudaError_t launch_engine_f64(const Params& p, cudaStream_t s);
 cudaError_t launch_engine_f32(const Params& p, cudaStream_t s);
+// nv = 7: recursion on the 7 unit vectors; nv = 2: on the proposal's vectors o and v
+cudaError_t launch_engine_f64(const Params& p, int nv, cudaStream_t s);
+cudaError_t launch_engine_f32(const Params& p, int nv, cudaStream_t s);
 cudaError_t launch_team_f64(const TeamJob* d_jobs, int njobs, int grid, int vec_bytes, int smem, cudaStream_t s);
 cudaError_t launch_team_f32(const TeamJob* d_jobs, int njobs, int grid, int vec_bytes, int smem, cudaStream_t s);
 cudaError_t team_max_ctas(int precision, int smem, int* out);

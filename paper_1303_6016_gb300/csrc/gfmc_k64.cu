@@ -3,16 +3,23 @@
 
 namespace gfmc {
 
-cudaError_t launch_engine_f64(const Params& p, cudaStream_t s)
+template <int NV>
+static cudaError_t launch_nv_f64(const Params& p, cudaStream_t s)
 {
     const int smem = engine_smem_bytes(p.M);
-    cudaError_t e = cudaFuncSetAttribute(gfmc_engine<double>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(gfmc_engine<double, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     Params q = p;
     void* args[] = {(void*)&q};
-    return cudaLaunchCooperativeKernel((void*)gfmc_engine<double>, dim3(p.ncta), dim3(kThreads), args,
+    return cudaLaunchCooperativeKernel((void*)gfmc_engine<double, NV>, dim3(p.ncta), dim3(kThreads), args,
                                        (size_t)smem, s);
+}
+
+cudaError_t launch_engine_f64(const Params& p, cudaStream_t s) { return launch_nv_f64<kVec>(p, s); }
+
+cudaError_t launch_engine_f64(const Params& p, int nv, cudaStream_t s)
+{
+    return nv == 2 ? launch_nv_f64<2>(p, s) : launch_nv_f64<kVec>(p, s);
 }
 
 cudaError_t engine_max_ctas_f64(int M, int* out)

@@ -24,6 +24,7 @@ LIB_PATH = os.path.join(_HERE, "libgfmc.so")
 GFMC_OK, GFMC_EINVAL, GFMC_ENOMEM, GFMC_ECUDA, GFMC_ETIMEOUT, GFMC_ENUMERIC = range(6)
 PRECISIONS = {"fp64": 0, "fp32_mixed": 1}
 KERNELS = {"jackson": 0, "lorentz": 1}
+RECURSIONS = {"unit_vectors": 0, "proposal": 1}
 
 # Names exported by libgfmc.so; include/gfmc.h declares exactly these.
 EXPORTS = ("gfmc_default_options", "gfmc_create", "gfmc_moments", "gfmc_delta_omega",
@@ -43,7 +44,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("lorentz_lambda", ctypes.c_double), ("spectral_scale", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("chain_id", ctypes.c_uint32),
-                ("stream", ctypes.c_void_p), ("num_ctas", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("num_ctas", ctypes.c_int), ("recursion", ctypes.c_int)]
 
 
 _lib = None
@@ -126,7 +127,7 @@ class Chain:
     def __init__(self, L: int, spins, t: float = 1.0, mu: float = -2.0, beta: float = 20.0,
                  M: int = 256, precision: str = "fp64", kernel: str = "jackson",
                  lorentz_lambda: float = 4.0, spectral_scale: float = 0.0, seed: int = 1,
-                 chain_id: int = 0, stream=None, num_ctas: int = 0):
+                 chain_id: int = 0, stream=None, num_ctas: int = 0, recursion: str = "unit_vectors"):
         lib = load()
         self.L, self.N, self.M = int(L), int(L) ** 3, int(M)
         self.t, self.mu, self.beta = float(t), float(mu), float(beta)
@@ -142,6 +143,7 @@ class Chain:
         s = current_stream_handle() if stream is None else stream
         opt.stream = s if s else None
         opt.num_ctas = int(num_ctas)
+        opt.recursion = RECURSIONS[recursion]
         sp = np.ascontiguousarray(spins, dtype=np.float64).reshape(-1, 2)
         if sp.shape[0] != self.N:
             raise ValueError(f"spins has {sp.shape[0]} rows, expected N = {self.N}")

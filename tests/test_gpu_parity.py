@@ -247,3 +247,39 @@ def test_bad_site_and_timeout_status(G):
         # the handle stays usable and gives the same answer afterwards
         ch.set_wait_budget(4_000_000_000)
         assert ch.delta_omega(3, 1.0, 1.0) == ref
+
+
+# ---------------------------------------------------------------------------
+# the paper's recursion on the proposal's vectors (o, v; o+v and o+iv by linearity)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L,M,ncta,prec", [(4, 256, 0, "fp64"), (6, 128, 3, "fp64"), (8, 256, 0, "fp64"),
+                                           (8, 256, 0, "fp32_mixed")])
+def test_proposal_recursion_delta_omega_matches_oracle(G, L, M, ncta, prec):
+    sp = inputs.uniform_sphere(L, 11)
+    rng = np.random.default_rng(12)
+    with chain(G, L, sp, M, num_ctas=ncta, recursion="proposal", precision=prec) as ch:
+        for o in (0, L ** 3 // 2, L ** 3 - 1):
+            th, ph = float(np.arccos(1 - 2 * rng.random())), float(2 * np.pi * rng.random())
+            got = ch.delta_omega(o, th, ph)
+            ref = O.delta_omega(L, sp, o, th, ph, M, beta=20.0, chem=-2.0)
+            tol = dom_tol(ref) if prec == "fp64" else 1e-4
+            assert abs(got - ref) <= tol, (o, got, ref)
+        # the 7x7 moments call still runs on the unit vectors
+        assert np.abs(ch.moments(5) - O.moments(L, sp, 5, M)).max() <= (MOM_TOL if prec == "fp64" else 2e-5)
+
+
+def test_proposal_recursion_sweep_matches_oracle(G):
+    L, M = 6, 128
+    sp = inputs.uniform_sphere(L, 13)
+    with chain(G, L, sp, M, seed=2, recursion="proposal") as ch:
+        out = ch.sweep(1)
+    check_trace_against_oracle(L, sp, M, out, L ** 3, seed=2)
+
+
+def test_proposal_recursion_full_size_fp64(G):
+    L, M, n = 32, 1024, 3
+    sp = inputs.uniform_sphere(L, 0)
+    with chain(G, L, sp, M, seed=1, recursion="proposal") as ch:
+        out = ch.updates(n)
+    check_trace_against_oracle(L, sp, M, out, n)
