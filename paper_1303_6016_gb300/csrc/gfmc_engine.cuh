@@ -877,14 +877,31 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 R2* wr = (m & 1) ? buf0 : buf1;        // receives r_{m+1}; held r_{m-1}
                 R2 nxt[kVec];
                 if (active) {
+                    if constexpr (sizeof(R) == 4) {
+                        // issue all 42 neighbour loads before the first use (latency-bound path)
+                        R2 nv[kVec][6];
     #pragma unroll
-                    for (int v = 0; v < kVec; ++v) {
-                        const R2* cv = rd + (size_t)v * N;
-                        R2 acc = c_make<R2>(0, 0);
+                        for (int v = 0; v < kVec; ++v)
     #pragma unroll
-                        for (int d = 0; d < 6; ++d) c_fma(acc, h[d], ldcg2(cv + nb[d]));
-                        nxt[v] = c_make<R2>(fma((R)2, acc.x, -prv[v].x), fma((R)2, acc.y, -prv[v].y));
-                        if (m < p.nsteps) stcg2(wr + (size_t)v * N + i, nxt[v]);
+                            for (int d = 0; d < 6; ++d) nv[v][d] = ldcg2(rd + (size_t)v * N + nb[d]);
+    #pragma unroll
+                        for (int v = 0; v < kVec; ++v) {
+                            R2 acc = c_make<R2>(0, 0);
+    #pragma unroll
+                            for (int d = 0; d < 6; ++d) c_fma(acc, h[d], nv[v][d]);
+                            nxt[v] = c_make<R2>(fma((R)2, acc.x, -prv[v].x), fma((R)2, acc.y, -prv[v].y));
+                            if (m < p.nsteps) stcg2(wr + (size_t)v * N + i, nxt[v]);
+                        }
+                    } else {
+    #pragma unroll
+                        for (int v = 0; v < kVec; ++v) {
+                            const R2* cv = rd + (size_t)v * N;
+                            R2 acc = c_make<R2>(0, 0);
+    #pragma unroll
+                            for (int d = 0; d < 6; ++d) c_fma(acc, h[d], ldcg2(cv + nb[d]));
+                            nxt[v] = c_make<R2>(fma((R)2, acc.x, -prv[v].x), fma((R)2, acc.y, -prv[v].y));
+                            if (m < p.nsteps) stcg2(wr + (size_t)v * N + i, nxt[v]);
+                        }
                     }
                 } else {
     #pragma unroll
