@@ -199,7 +199,7 @@ def sweep_latency(gfmc, inputs, stream, L, M, precision, sweeps, warmup=2):
             "p99_ms": p99}
 
 
-def run_batching(stream, steps, warmup, updates, flush):
+def run_batching(stream, steps, warmup, updates, flush, recursion="unit_vectors"):
     """64 independent FP32-mixed chains, L from {8,12,16,24,32}, T ~ U[0.02, 0.2],
     M = 1024, in team-engine launches planned by the autotuner; a step runs
     `updates` updates of every chain."""
@@ -207,8 +207,8 @@ def run_batching(stream, steps, warmup, updates, flush):
     from paper_1303_6016_gb300 import batch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    chains, Ls, Ts = batch.c4_chains(M=1024)
-    tuner = batch.Autotuner(M=1024, precision="fp32_mixed")
+    chains, Ls, Ts = batch.c4_chains(M=1024, recursion=recursion)
+    tuner = batch.Autotuner(M=1024, precision="fp32_mixed", recursion=recursion)
     runner = batch.BatchRunner(chains, tuner)
     plan = runner.plan([updates] * len(chains))
     tune_s = time.perf_counter() - t0
@@ -237,7 +237,7 @@ def run_batching(stream, steps, warmup, updates, flush):
             "launches_per_step": len(plan), "team_ctas_by_L": {str(k): sorted(v) for k, v in sorted(teams.items())},
             "lattice_counts": {str(int(L)): int((Ls == L).sum()) for L in sorted(set(Ls.tolist()))},
             "stencil_gbs": sum(bytes_u) * updates / (total / steps / 1000.0) / 1e9,
-            "autotune_s": tune_s,
+            "autotune_s": tune_s, "recursion": recursion,
             "config": "64 chains, L uniform from {8,12,16,24,32} (seed 4), T uniform in [0.02, 0.2] t, "
                       "mu = -2t, M = 1024, FP32-mixed, spins uniform (seed = chain index)"}
 
@@ -468,6 +468,9 @@ def main():
 
     if not args.no_batch:
         line["batching"] = run_batching(stream, max(3, args.steps // 2), 3, args.batch_updates, flush)
+        if not args.no_variant:
+            line["batching_proposal_recursion"] = run_batching(stream, max(3, args.steps // 2), 3,
+                                                               args.batch_updates, flush, "proposal")
 
     if not args.no_serving:
         from paper_1303_6016_gb300 import serving

@@ -173,6 +173,7 @@ gfmc_status run_engine(gfmc_ctx* h, Params& P)
     h->stall_next = 0;
     if (h->multi_site) {
         gfmc::TeamJob job{};
+        P.nv = (h->recursion == GFMC_RECURSION_PROPOSAL && P.mode != gfmc::MODE_MOMENTS) ? 2 : gfmc::kVec;
         job.p = P;
         job.cta0 = 0;
         job.vec_smem = 0;
@@ -378,6 +379,7 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
     P.ncta = ncta;
     P.divL = (unsigned)(((1ull << 32) + (unsigned long long)L - 1) / (unsigned long long)L);
     P.divLL = (unsigned)(((1ull << 32) + (unsigned long long)L * L - 1) / ((unsigned long long)L * L));
+    P.nv = gfmc::kVec;
     P.t = t;
     P.chem = mu;
     P.beta = beta;
@@ -619,7 +621,8 @@ gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_update
     std::vector<int> resident(n_chains, 0);
     for (int c = 0; c < n_chains; ++c) {
         const int tc = team_ctas ? team_ctas[c] : 1;
-        const size_t vb = 2 * (size_t)gfmc::kVec * chains[c]->N * vsz;
+        const int nvc = chains[c]->recursion == GFMC_RECURSION_PROPOSAL ? 2 : gfmc::kVec;
+        const size_t vb = 2 * (size_t)nvc * chains[c]->N * vsz;
         if (tc == 1 && vb + work + reserve <= (size_t)dev_smem) {
             resident[c] = 1;
             vec_bytes = std::max(vec_bytes, (vb + 255) & ~(size_t)255);
@@ -659,6 +662,7 @@ gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_update
         P.n_mag = h->d_nmag;
         P.budget = h->budget;
         P.stall = 0;
+        P.nv = h->recursion == GFMC_RECURSION_PROPOSAL ? 2 : gfmc::kVec;
         jobs[c].p = P;
         jobs[c].cta0 = cta0;
         jobs[c].vec_smem = resident[c];
@@ -876,6 +880,7 @@ gfmc_status gfmc_server_submit(gfmc_server_t s, int slot, gfmc_t h, int64_t n_up
     P.n_mag = h->d_nmag;
     P.budget = h->budget;
     P.stall = 0;
+    P.nv = h->recursion == GFMC_RECURSION_PROPOSAL ? 2 : gfmc::kVec;
     // Clear the chain's control words and post the job with copies only: a
     // memset kernel could wait for an SM the running server occupies.
     static const unsigned zeros[256] = {};

@@ -677,6 +677,112 @@ __device__ bool team_steps(const Params& p, int cta, unsigned phase, typename Cx
     return true;
 }
 
+// Phase 0 and the steps of one update of a team CTA for the recursion on the
+// proposal's vectors o and v (any number of sites per thread, vectors in vm).
+template <class R, class V>
+__device__ bool team_steps2(const Params& p, int cta, unsigned phase, typename Cx<R>::T* buf0,
+                            typename Cx<R>::T* buf1, const int* s_loc, const double2* s_c,
+                            double (*red)[kEntries], V vm)
+{
+    using R2 = typename Cx<R>::T;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int N = p.N, L = p.L;
+    const int s0 = p.tile_start[cta], s1 = p.tile_start[cta + 1];
+    const R2* hop;
+    if constexpr (sizeof(R) == 8) hop = (const R2*)p.hop64; else hop = (const R2*)p.hop32;
+    R2 cv6[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) cv6[k] = c_make<R2>((R)s_c[k + 1].x, (R)s_c[k + 1].y);
+    const int lo = s_loc[0];
+
+    for (int i = s0 + tid; i < s1; i += kThreads) {
+        int nb[6];
+        site_nbrs(i, L, p.divL, p.divLL, nb);
+        R2 r0o = c_make<R2>(i == lo ? (R)1 : (R)0, (R)0), r0v = c_make<R2>(0, 0);
+        R2 r1o = c_make<R2>(0, 0), r1v = c_make<R2>(0, 0);
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (i == s_loc[k + 1]) {
+                r0v.x += cv6[k].x;
+                r0v.y += cv6[k].y;
+            }
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            const bool ho = nb[d] == lo;
+            bool hv = false;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) hv |= nb[d] == s_loc[k + 1];
+            if (ho || hv) {
+                const R2 h = hop_of(hop, N, i, d, nb[d]);
+                if (ho) {
+                    r1o.x += h.x;
+                    r1o.y += h.y;
+                }
+#pragma unroll
+                for (int k = 0; k < 6; ++k)
+                    if (nb[d] == s_loc[k + 1]) c_fma(r1v, h, cv6[k]);
+            }
+        }
+        vm.st(buf0 + i, r0o);
+        vm.st(buf0 + (size_t)N + i, r0v);
+        vm.st(buf1 + i, r1o);
+        vm.st(buf1 + (size_t)N + i, r1v);
+    }
+    publish(p, cta, phase + 1);
+
+    for (int m = 1; m <= p.nsteps; ++m) {
+        if (!wait_neighbours(p, cta, phase + (unsigned)m, 100 + m)) return false;
+        const R2* rd = (m & 1) ? buf1 : buf0;
+        R2* wr = (m & 1) ? buf0 : buf1;
+        double* prow = p.partial + ((size_t)(m - 1) * p.ncta + cta) * kEntries;
+        R acc[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) acc[e] = (R)0;
+        for (int i = s0 + tid; i < s1; i += kThreads) {
+            int nb[6];
+            site_nbrs(i, L, p.divL, p.divLL, nb);
+            R2 h[6], nv[2][6];
+#pragma unroll
+            for (int d = 0; d < 6; ++d) h[d] = hop_of(hop, N, i, d, nb[d]);
+#pragma unroll
+            for (int v = 0; v < 2; ++v)
+#pragma unroll
+                for (int d = 0; d < 6; ++d) nv[v][d] = vm.ld(rd + (size_t)v * N + nb[d]);
+            R2 cur[2], nxt[2];
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+                cur[v] = vm.ld(rd + (size_t)v * N + i);
+                const R2 pv = vm.ld(wr + (size_t)v * N + i);
+                R2 a = c_make<R2>(0, 0);
+#pragma unroll
+                for (int d = 0; d < 6; ++d) c_fma(a, h[d], nv[v][d]);
+                nxt[v] = c_make<R2>(fma((R)2, a.x, -pv.x), fma((R)2, a.y, -pv.y));
+                if (m < p.nsteps) vm.st(wr + (size_t)v * N + i, nxt[v]);
+            }
+            const R2 a = cur[0], b = cur[1], na = nxt[0], nbv = nxt[1];
+            acc[0] = fma(a.x, a.x, fma(a.y, a.y, acc[0]));
+            acc[1] = fma(b.x, b.x, fma(b.y, b.y, acc[1]));
+            acc[2] = fma(a.x, b.x, fma(a.y, b.y, acc[2]));
+            acc[3] = fma(a.x, b.y, fma(-a.y, b.x, acc[3]));
+            acc[4] = fma(a.x, na.x, fma(a.y, na.y, acc[4]));
+            acc[5] = fma(b.x, nbv.x, fma(b.y, nbv.y, acc[5]));
+            acc[6] = fma(a.x, nbv.x, fma(a.y, nbv.y, acc[6]));
+            acc[7] = fma(a.x, nbv.y, fma(-a.y, nbv.x, acc[7]));
+        }
+        publish(p, cta, phase + (unsigned)m + 1u);
+        const R s8 = warp_reduce_scatter8(acc, lane);
+        if ((lane & 3) == 0) red[warp][lane >> 2] = (double)s8;
+        __syncthreads();
+        if (tid < 8) {
+            double sum = 0.0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) sum += red[w][tid];
+            prow[tid] = sum;
+        }
+    }
+    return true;
+}
+
 // ---------------------------------------------------------------------------
 // the engine
 // ---------------------------------------------------------------------------
@@ -696,7 +802,7 @@ template <class R, int VARIANT, int NV = kVec>
 __device__ __forceinline__ void run_chain(const Params& p, const int cta, double2* dyn,
                                           typename Cx<R>::T* vec_smem)
 {
-    static_assert(NV == kVec || (NV == 2 && VARIANT == 0), "two-vector recursion: single-chain variant only");
+    static_assert(NV == kVec || NV == 2, "recursion on 7 unit vectors or on o and v");
     using R2 = typename Cx<R>::T;
     __shared__ double red[kWarps][kEntries];
     __shared__ double2 s_mu2[kWarps][2][kPairs];
@@ -722,7 +828,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
     for (int d = 0; d < 6; ++d) nb[d] = active ? nbr_site(i, d, L) : 0;
 
     R2* buf0 = vec_smem ? vec_smem : (R2*)p.rbuf;
-    R2* buf1 = buf0 + (size_t)kVec * N;
+    R2* buf1 = buf0 + (size_t)NV * N;
     const long long nupd = (p.mode == MODE_SWEEP) ? p.n_updates : 1;
     unsigned phase = 0;
     long long nmag = 0;
@@ -940,6 +1046,12 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                     prv[v] = cur[v];
                     cur[v] = nxt[v];
                 }
+            }
+        } else if constexpr (NV == 2) {
+            if (vec_smem) {
+                if (!team_steps2<R>(p, cta, phase, buf0, buf1, s_loc, s_c, red, SmemVec{})) return;
+            } else {
+                if (!team_steps2<R>(p, cta, phase, buf0, buf1, s_loc, s_c, red, GlobalVec{})) return;
             }
         } else {
             if (vec_smem) {
@@ -1247,7 +1359,8 @@ __global__ void __launch_bounds__(kThreads, 1) gfmc_team_engine(const TeamJob* _
     __syncthreads();
     using R2 = typename Cx<R>::T;
     R2* vs = s_vs ? (R2*)dyn_all : nullptr;
-    run_chain<R, 1>(sp, s_cta, dyn_all + vec_bytes / (int)sizeof(double2), vs);
+    if (sp.nv == 2) run_chain<R, 1, 2>(sp, s_cta, dyn_all + vec_bytes / (int)sizeof(double2), vs);
+    else run_chain<R, 1>(sp, s_cta, dyn_all + vec_bytes / (int)sizeof(double2), vs);
 }
 
 }  // namespace gfmc

@@ -60,6 +60,7 @@ struct Params {
     int* err;         // [4]     code, where, cta, aux
     long long budget; // clock64 cycles a single wait may spin before giving up
     int stall;        // test hook: CTA 0 withholds its completion flags
+    int nv;           // recursion vectors of team launches: 7 (unit vectors) or 2 (o and v)
 
     // work description
     int mode;

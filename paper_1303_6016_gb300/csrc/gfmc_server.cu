@@ -86,8 +86,13 @@ __global__ void __launch_bounds__(kThreads, 1) gfmc_server_kernel(ServerArgs a)
         const unsigned cmd = s_cmd;
         if (cmd == kExit) return;
         last = cmd;
-        if (s_prec == 0) run_chain<double, 1>(sp, s_cta, work, nullptr);
-        else run_chain<float, 1>(sp, s_cta, work, nullptr);
+        if (s_prec == 0) {
+            if (sp.nv == 2) run_chain<double, 1, 2>(sp, s_cta, work, nullptr);
+            else run_chain<double, 1>(sp, s_cta, work, nullptr);
+        } else {
+            if (sp.nv == 2) run_chain<float, 1, 2>(sp, s_cta, work, nullptr);
+            else run_chain<float, 1>(sp, s_cta, work, nullptr);
+        }
         grid_barrier(sp, 9);  // every CTA of the slot is done with the job
         if (s_cta == 0 && threadIdx.x == 0) {
             __threadfence_system();

@@ -10,6 +10,9 @@ their chain are free, and their work overlaps on the device.
 
     python -m paper_1303_6016_gb300.serving --rates 10 100 1000 --seconds 6
 
+Jobs compute Delta Omega and decisions only, so the chains use the recursion
+on the proposal's vectors by default (identical results, see gfmc.h).
+
 Reported per arrival rate: requests completed, p50 / p99 latency (arrival to
 completion, host clock), aggregate spin updates/s, requests left waiting when
 admission stops (``drain`` seconds after the last arrival).
@@ -68,8 +71,10 @@ def arrivals(rate: float, seconds: float, n_chains: int, seed: int = 5):
 
 
 class Scheduler:
-    def __init__(self, specs, hbm_budget: float, K: int = 2, slots=SLOTS, max_M: int = 2048):
+    def __init__(self, specs, hbm_budget: float, K: int = 2, slots=SLOTS, max_M: int = 2048,
+                 recursion: str = "proposal"):
         self.specs = specs
+        self.recursion = recursion
         self.K = K
         self.budget = hbm_budget
         self.used = 0.0
@@ -94,7 +99,7 @@ class Scheduler:
             return False
         self.chains[c] = gfmc.Chain(sp["L"], inputs.uniform_sphere(sp["L"], 100 + c), M=sp["M"],
                                     precision=sp["precision"], beta=20.0, mu=-2.0, seed=1, chain_id=c,
-                                    stream=0)
+                                    stream=0, recursion=self.recursion)
         self.used += fb
         return True
 
@@ -151,11 +156,11 @@ class Scheduler:
 
 
 def sweep(rates=(10, 100, 1000), seconds: float = 6.0, K: int = 2, n_chains: int = 24,
-          hbm_budget_gb: float = 4.0, drain_s: float = 30.0):
+          hbm_budget_gb: float = 4.0, drain_s: float = 30.0, recursion: str = "proposal"):
     specs = pool_specs(n_chains)
     out = []
     for r in rates:
-        sch = Scheduler(specs, hbm_budget_gb * 1e9, K=K)
+        sch = Scheduler(specs, hbm_budget_gb * 1e9, K=K, recursion=recursion)
         try:
             res = sch.run(arrivals(r, seconds, n_chains), seconds, drain_s)
         finally:
@@ -164,7 +169,7 @@ def sweep(rates=(10, 100, 1000), seconds: float = 6.0, K: int = 2, n_chains: int
         out.append(res)
     return {"requests": f"continue one of {n_chains} chains by K={K} updates; L uniform in 8..48, "
                         "M in {512,1024,2048}, FP64 or FP32-mixed 50/50 (seed 5); Poisson arrivals",
-            "slots": SLOTS, "hbm_budget_gb": hbm_budget_gb, "results": out}
+            "slots": SLOTS, "hbm_budget_gb": hbm_budget_gb, "recursion": recursion, "results": out}
 
 
 def main(argv=None):
@@ -175,10 +180,11 @@ def main(argv=None):
     ap.add_argument("--chains", type=int, default=24)
     ap.add_argument("--hbm-gb", type=float, default=4.0)
     ap.add_argument("--drain", type=float, default=30.0)
+    ap.add_argument("--recursion", default="proposal", choices=["proposal", "unit_vectors"])
     a = ap.parse_args(argv)
     from . import build
     build.build()
-    print(json.dumps(sweep(a.rates, a.seconds, a.K, a.chains, a.hbm_gb, a.drain)))
+    print(json.dumps(sweep(a.rates, a.seconds, a.K, a.chains, a.hbm_gb, a.drain, a.recursion)))
 
 
 if __name__ == "__main__":

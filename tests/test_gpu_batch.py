@@ -144,3 +144,22 @@ def test_temperature_scan_orders_at_low_temperature(G):
     res = mt_scan.scan(Ls=(4,), Ts=(0.02, 2.0), sweeps=14, warmup=6, M=64, start="cold")
     m = {p["T"]: p["M_mean"] for p in res["points"]}
     assert m[0.02] > 0.8 and m[2.0] < 0.4, m
+
+
+def test_proposal_recursion_batch_matches_oracle(G):
+    """Chains with the recursion on the proposal's vectors, in one batch with
+    unit-vector chains, shared-memory and L2 teams; each replayed by the oracle."""
+    specs = [(4, 20.0, 1, "proposal"), (6, 12.0, 2, "proposal"), (8, 20.0, 1, "unit_vectors"),
+             (8, 9.0, 3, "proposal"), (12, 15.0, 1, "proposal")]
+    M = 64
+    chains, sps = [], []
+    for c, (L, beta, _, rec) in enumerate(specs):
+        sp = inputs.uniform_sphere(L, 60 + c)
+        sps.append(sp)
+        chains.append(G.Chain(L, sp, M=M, beta=beta, mu=-2.0, seed=4, chain_id=c, recursion=rec))
+    n = 50
+    outs = G.run_batch(chains, n, team_ctas=[t for (_, _, t, _) in specs])
+    for c, (L, beta, _, _) in enumerate(specs):
+        oracle_replay(L, sps[c], M, beta, 4, c, outs[c])
+    for ch in chains:
+        ch.close()

@@ -115,3 +115,24 @@ def test_busy_slot_and_busy_chain_are_rejected(G):
         wait_all(srv, [0])
     a.close()
     b.close()
+
+
+def test_proposal_recursion_jobs_match_oracle(G):
+    specs = [(6, "fp64", 2), (8, "fp64", 1)]
+    M, n = 64, 30
+    chains = [G.Chain(L, inputs.uniform_sphere(L, 90 + c), M=M, precision=prec, seed=3, chain_id=c,
+                      recursion="proposal") for c, (L, prec, _) in enumerate(specs)]
+    with G.Server([tc for (_, _, tc) in specs], max_M=M) as srv:
+        for k, ch in enumerate(chains):
+            srv.submit(k, ch, n)
+        res = wait_all(srv, [0, 1])
+    for c, (L, _, _) in enumerate(specs):
+        out = res[c]
+        ref = O.updates(L, inputs.uniform_sphere(L, 90 + c), n, M, beta=20.0, chem=-2.0, seed=3, chain_id=c,
+                        forced=out["decisions"].astype(np.int8))
+        for q in range(n):
+            assert abs(out["d_omega"][q] - ref["d_omega"][q]) <= dom_tol(ref["d_omega"][q])
+            if bool(ref["ratio"][q] > ref["u"][q]) != bool(out["decisions"][q]):
+                assert abs(ref["ratio"][q] - ref["u"][q]) < 1e-9
+    for ch in chains:
+        ch.close()
