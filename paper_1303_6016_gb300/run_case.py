@@ -23,13 +23,19 @@ def main(argv=None):
     ap.add_argument("--beta", type=float, default=20.0)
     ap.add_argument("--mu", type=float, default=-2.0)
     ap.add_argument("--num-ctas", type=int, default=0)
+    ap.add_argument("--recursion", default="unit_vectors", choices=sorted(gfmc.RECURSIONS))
+    ap.add_argument("--team", type=int, default=0,
+                    help="run the updates as a one-chain batch on a team of this many CTAs")
     a = ap.parse_args(argv)
     build.build()
     sp = inputs.make(a.spins, a.L, seed=0 if a.spins != "vmf" else 2)
     with gfmc.Chain(a.L, sp, M=a.M, beta=a.beta, mu=a.mu, precision=a.precision,
-                    num_ctas=a.num_ctas) as ch:
+                    num_ctas=a.num_ctas, recursion=a.recursion) as ch:
         t0 = time.perf_counter()
-        out = ch.updates(a.updates)
+        if a.team > 0:
+            out = gfmc.run_batch([ch], [a.updates], team_ctas=[a.team])[0]
+        else:
+            out = ch.updates(a.updates)
         dt = time.perf_counter() - t0
     print(f"L={a.L} M={a.M} {a.precision}: {a.updates} updates in {dt * 1e3:.2f} ms, "
           f"{out['n_accepted']} accepted, first dOmega {out['d_omega'][0]:.6e}")
