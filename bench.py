@@ -54,6 +54,32 @@ def update_work(L: int, M: int, real_bytes: int):
     return steps * N * FLOP_PER_SITE_STEP, steps * N * bytes_per_site_step(real_bytes)
 
 
+# DRAM bytes per update of the engine kernels from one ncu capture each
+# (profiles/gfmc_engine_L32_M1024.md), valid only for the engine sources they
+# were taken from: bench.py reports them as roofline.traffic while the hash of
+# those sources is unchanged, and null otherwise.
+TRAFFIC_SOURCES = ("gfmc_engine.cuh", "gfmc_k64.cu", "gfmc_k32.cu", "gfmc_internal.h")
+TRAFFIC_HASH = "096ec36c75936037"
+TRAFFIC_PER_UPDATE = {"fp64": 27.920896e6, "fp32_mixed": 34.402816e6}
+
+
+def engine_sources_hash() -> str:
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1303_6016_gb300", "csrc")
+    inner = "".join(hashlib.sha256(open(os.path.join(csrc, f), "rb").read()).hexdigest() + "  " +
+                    os.path.join("paper_1303_6016_gb300", "csrc", f) + "\n" for f in TRAFFIC_SOURCES)
+    return hashlib.sha256(inner.encode()).hexdigest()[:16]
+
+
+def traffic_per_launch(precision: str, updates: int):
+    try:
+        if engine_sources_hash() != TRAFFIC_HASH:
+            return None
+    except OSError:
+        return None
+    return TRAFFIC_PER_UPDATE[precision] * updates
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -159,21 +185,32 @@ def aggregate(world: int, steps: int, updates_per_step: int, max_total_ms: float
     return world * steps * updates_per_step / (max_total_ms / 1000.0)
 
 
-def l2_copy_gbs(n_bytes: int = 16 << 20, reps: int = 200) -> float:
-    """Measured L2-resident copy bandwidth (read + write bytes) with CUDA events."""
+def l2_copy_gbs(n_bytes: int = 32 << 20, copies: int = 40, replays: int = 10) -> float:
+    """Measured L2-resident copy bandwidth (read + write bytes): `copies` copies
+    of a 32 MiB buffer into another (64 MiB in all, inside the 129 MB L2)
+    captured in a CUDA graph so no launch gaps are timed; CUDA events."""
     import torch
-    x = torch.empty(n_bytes // 4, dtype=torch.float32, device="cuda")
+    x = torch.ones(n_bytes // 4, dtype=torch.float32, device="cuda")
     y = torch.empty_like(x)
-    for _ in range(10):
-        y.copy_(x)
-    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            y.copy_(x)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(copies):
+            y.copy_(x)
+    g.replay()
     torch.cuda.synchronize()
-    s.record()
-    for _ in range(reps):
-        y.copy_(x)
-    e.record()
-    e.synchronize()
-    return 2.0 * n_bytes * reps / (s.elapsed_time(e) / 1000.0) / 1e9
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(replays):
+        g.replay()
+    b.record()
+    b.synchronize()
+    return 2.0 * n_bytes * copies * replays / (a.elapsed_time(b) / 1000.0) / 1e9
 
 
 def sweep_latency(gfmc, inputs, stream, L, M, precision, sweeps, warmup=2):
@@ -413,7 +450,8 @@ def main():
         "stencil_gbs": U * bytes_u / launch_s / 1e9,
         "latency_ms_per_update": {"p50": statistics.median(per) / U, "p99": sorted(per)[-1] / U},
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
-                     "frac": achieved_tf / peak_tf, "traffic": None,
+                     "frac": achieved_tf / peak_tf, "traffic": traffic_per_launch("fp64", U),
+                     "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
                      "peak_source": "FP64 vector peak derived from 152 SMs x max SM clock x 2 FMA lanes "
                                     "(1.25 TFLOP/s class); not in MEASURED_PEAKS.json"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -436,9 +474,9 @@ def main():
             "ms_per_step": tot_m / args.steps, "stencil_gbs": gbs,
             "latency_ms_per_update": {"p50": statistics.median(perm) / Um, "p99": sorted(perm)[-1] / Um},
             "roofline": {"bound": "l2", "achieved": gbs, "peak": l2, "unit": "GB/s",
-                         "frac": gbs / l2, "traffic": None,
-                         "peak_source": "measured in this run: torch copy of a 16 MiB L2-resident buffer "
-                                        "(read + write bytes, CUDA events)",
+                         "frac": gbs / l2, "traffic": traffic_per_launch("fp32_mixed", Um),
+                         "peak_source": "measured in this run: graph-replayed copies of a 32 MiB "
+                                        "L2-resident buffer (read + write bytes, CUDA events)",
                          "hbm_frac": gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None},
             "alu_tflops": Um * flop_m / launch_m / 1e12, "clocks": clocks_m,
             "gpu_launches": args.steps,
