@@ -283,3 +283,47 @@ def test_proposal_recursion_full_size_fp64(G):
     with chain(G, L, sp, M, seed=1, recursion="proposal") as ch:
         out = ch.updates(n)
     check_trace_against_oracle(L, sp, M, out, n)
+
+
+# ---------------------------------------------------------------------------
+# edges: chains with more sites than threads per CTA, extreme M, Lorentz sweep
+# ---------------------------------------------------------------------------
+
+def test_multi_site_chain_matches_oracle(G):
+    """L = 36 (N = 46656 > 256 x 152 CTAs): every call of the chain runs the
+    engine's multi-site variant."""
+    L, M = 36, 64
+    sp = inputs.uniform_sphere(L, 21)
+    with chain(G, L, sp, M, seed=5) as ch:
+        o = 30000
+        assert np.abs(ch.moments(o) - O.moments(L, sp, o, M)).max() <= MOM_TOL
+        d = ch.delta_omega(o, 0.9, 5.5)
+        dref = O.delta_omega(L, sp, o, 0.9, 5.5, M, beta=20.0, chem=-2.0)
+        assert abs(d - dref) <= dom_tol(dref)
+        out = ch.updates(3)
+    check_trace_against_oracle(L, sp, M, out, 3, seed=5)
+
+
+@pytest.mark.parametrize("M", [16, 4096])
+def test_extreme_M(G, M):
+    L = 4
+    sp = inputs.uniform_sphere(L, 22)
+    with chain(G, L, sp, M) as ch:
+        assert np.abs(ch.moments(9) - O.moments(L, sp, 9, M)).max() <= MOM_TOL
+        d = ch.delta_omega(9, 2.0, 1.0)
+    dref = O.delta_omega(L, sp, 9, 2.0, 1.0, M, beta=20.0, chem=-2.0)
+    assert abs(d - dref) <= dom_tol(dref)
+
+
+def test_lorentz_sweep_matches_oracle(G):
+    L, M = 5, 128
+    sp = inputs.uniform_sphere(L, 23)
+    with chain(G, L, sp, M, kernel="lorentz", lorentz_lambda=3.0, seed=9) as ch:
+        out = ch.sweep(1)
+    res = O.updates(L, sp, L ** 3, M, beta=20.0, chem=-2.0, seed=9, kernel_kind=1, lam=3.0,
+                    forced=out["decisions"].astype(np.int8))
+    own = res["ratio"] > res["u"]
+    for q in range(L ** 3):
+        assert abs(out["d_omega"][q] - res["d_omega"][q]) <= dom_tol(res["d_omega"][q])
+        if own[q] != bool(out["decisions"][q]):
+            assert abs(res["ratio"][q] - res["u"][q]) < TIE
