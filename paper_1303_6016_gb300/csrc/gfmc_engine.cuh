@@ -436,6 +436,20 @@ __device__ __forceinline__ void gram_chunk_reduce(const R2 (&rc)[kVec], const R2
     if (lane < 28) dst[28 * C + lane] = (double)s;
 }
 
+// As gram_chunk_reduce, but adding the chunk's warp sums to dst.
+template <class R, class R2, int C>
+__device__ __forceinline__ void gram_chunk_accumulate(const R2 (&rc)[kVec], const R2 (&rn)[kVec], int lane,
+                                                      double* dst)
+{
+    R vals[32];
+    gram_fill<R, R2, C, 0>(rc, rn, vals);
+#pragma unroll
+    for (int qq = 28; qq < 32; ++qq) vals[qq] = (R)0;
+    const R s = warp_reduce_scatter32(vals, lane);
+    if (lane < 28) dst[28 * C + lane] += (double)s;
+}
+
+
 // FP64 Gram sums of one CTA from shared memory: thread (entry e, group g)
 // accumulates conj(x_j) y_k over the sites s = g, g+4, ... of the tile with
 // fused multiply-adds only; the four groups are added in order.  sr holds
@@ -499,31 +513,6 @@ __device__ __forceinline__ void gram_smem_finish(double re, double im, double* g
     }
     __syncthreads();
     if (tid < kEntries) out[tid] = ((gsum[tid] + gsum[kEntries + tid]) + gsum[2 * kEntries + tid]) + gsum[3 * kEntries + tid];
-}
-
-// Per-thread FP32 Gram accumulation of one site's 56 entries, compile-time indexed.
-template <class R, class R2, int E>
-__device__ __forceinline__ void gram_acc(const R2 (&rc)[kVec], const R2 (&rn)[kVec], R (&acc)[kEntries])
-{
-    constexpr int g = E / kPairs, pp = E % kPairs;
-    constexpr int j = pair_j(pp), k = pair_k(pp);
-    const R2 x = rc[j];
-    const R2 y = (g == 0) ? rc[k] : rn[k];
-    acc[2 * E] = fma(x.x, y.x, fma(x.y, y.y, acc[2 * E]));
-    if constexpr (!(g == 0 && j == k)) acc[2 * E + 1] = fma(x.x, y.y, fma(-x.y, y.x, acc[2 * E + 1]));
-    if constexpr (E + 1 < 2 * kPairs) gram_acc<R, R2, E + 1>(rc, rn, acc);
-}
-
-template <class R, int C>
-__device__ __forceinline__ void acc_chunk_reduce(const R (&acc)[kEntries], int lane, double* dst)
-{
-    R vals[32];
-#pragma unroll
-    for (int q = 0; q < 28; ++q) vals[q] = acc[28 * C + q];
-#pragma unroll
-    for (int q = 28; q < 32; ++q) vals[q] = (R)0;
-    const R s = warp_reduce_scatter32(vals, lane);
-    if (lane < 28) dst[28 * C + lane] = (double)s;
 }
 
 // Vector storage of a team: L2-resident global memory or the CTA's shared memory.
@@ -594,35 +583,48 @@ __device__ bool team_steps(const Params& p, int cta, unsigned phase, typename Cx
         R2* wr = (m & 1) ? buf0 : buf1;        // r_{m-1}, overwritten by r_{m+1}
         double* prow = p.partial + ((size_t)(m - 1) * p.ncta + cta) * kEntries;
         if constexpr (sizeof(R) == 4) {
-            R acc[kEntries];
-#pragma unroll
-            for (int e = 0; e < kEntries; ++e) acc[e] = (R)0;
-            for (int i = s0 + tid; i < s1; i += kThreads) {
-                int nb[6];
-                site_nbrs(i, L, p.divL, p.divLL, nb);
-                R2 h[6];
-#pragma unroll
-                for (int d = 0; d < 6; ++d) h[d] = hop_of(hop, N, i, d, nb[d]);
+            // chunks of kThreads sites, one per thread: all loads issued before the first use,
+            // Gram sums by warp butterfly per chunk into this warp's FP64 row of red
+            for (int e = lane; e < kEntries; e += 32) red[warp][e] = 0.0;
+            const int T = s1 - s0;
+            const int nch = (T + kThreads - 1) / kThreads;
+            for (int c = 0; c < nch; ++c) {
+                const int i = s0 + c * kThreads + tid;
                 R2 cur[kVec], nxt[kVec];
+                if (i < s1) {
+                    int nb[6];
+                    site_nbrs(i, L, p.divL, p.divLL, nb);
+                    R2 h[6], nv[kVec][6], pv[kVec];
 #pragma unroll
-                for (int v = 0; v < kVec; ++v) {
-                    const R2* cv = rd + (size_t)v * N;
-                    R2 a = c_make<R2>(0, 0);
+                    for (int d = 0; d < 6; ++d) h[d] = hop_of(hop, N, i, d, nb[d]);
 #pragma unroll
-                    for (int d = 0; d < 6; ++d) c_fma(a, h[d], vm.ld(cv + nb[d]));
-                    cur[v] = vm.ld(cv + i);
-                    const R2 pv = vm.ld(wr + (size_t)v * N + i);
-                    nxt[v] = c_make<R2>(fma((R)2, a.x, -pv.x), fma((R)2, a.y, -pv.y));
-                    if (m < p.nsteps) vm.st(wr + (size_t)v * N + i, nxt[v]);
+                    for (int v = 0; v < kVec; ++v) {
+#pragma unroll
+                        for (int d = 0; d < 6; ++d) nv[v][d] = vm.ld(rd + (size_t)v * N + nb[d]);
+                        cur[v] = vm.ld(rd + (size_t)v * N + i);
+                        pv[v] = vm.ld(wr + (size_t)v * N + i);
+                    }
+#pragma unroll
+                    for (int v = 0; v < kVec; ++v) {
+                        R2 a = c_make<R2>(0, 0);
+#pragma unroll
+                        for (int d = 0; d < 6; ++d) c_fma(a, h[d], nv[v][d]);
+                        nxt[v] = c_make<R2>(fma((R)2, a.x, -pv[v].x), fma((R)2, a.y, -pv[v].y));
+                        if (m < p.nsteps) vm.st(wr + (size_t)v * N + i, nxt[v]);
+                    }
+                } else {
+#pragma unroll
+                    for (int v = 0; v < kVec; ++v) {
+                        cur[v] = c_make<R2>(0, 0);
+                        nxt[v] = c_make<R2>(0, 0);
+                    }
                 }
-                gram_acc<R, R2, 0>(cur, nxt, acc);
+                gram_chunk_accumulate<R, R2, 0>(cur, nxt, lane, red[warp]);
+                gram_chunk_accumulate<R, R2, 1>(cur, nxt, lane, red[warp]);
+                gram_chunk_accumulate<R, R2, 2>(cur, nxt, lane, red[warp]);
+                gram_chunk_accumulate<R, R2, 3>(cur, nxt, lane, red[warp]);
             }
             publish(p, cta, phase + (unsigned)m + 1u);
-            acc_chunk_reduce<R, 0>(acc, lane, red[warp]);
-            acc_chunk_reduce<R, 1>(acc, lane, red[warp]);
-            acc_chunk_reduce<R, 2>(acc, lane, red[warp]);
-            acc_chunk_reduce<R, 3>(acc, lane, red[warp]);
-            __syncthreads();
             if (tid < kEntries) {
                 double sum = 0.0;
 #pragma unroll
