@@ -177,6 +177,23 @@ gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_update
                            uint64_t* n_accepted, uint8_t** decisions, double** d_omega_trace,
                            double** magnetization, int64_t* n_mag, void* stream);
 
+/* Run chains that use the recursion on the proposal's vectors
+ * (GFMC_RECURSION_PROPOSAL), each on one thread-block cluster of
+ * cluster_ctas[c] CTAs (1, 2, 4, 8 or 16; it must divide N) that holds the
+ * chain's whole lattice -- both vectors' two recursion buffers and the
+ * forward bonds -- in its shared memory and reads neighbours in other CTAs of
+ * the cluster over distributed shared memory; one hardware cluster barrier
+ * per recursion step (Eq. recursive), no global-memory exchange.  Clusters are
+ * independent: chains of the same precision and cluster size share a launch,
+ * launches of different groups overlap, and clusters need not all be resident
+ * at once.  Results as gfmc_updates would give them (up to the rounding order
+ * of the sums); the outputs are as for gfmc_run_batch.  GFMC_EINVAL when a
+ * chain's lattice does not fit in the shared memory of its cluster (about
+ * 7 x N/C x 8 bytes FP32, x 16 FP64, plus a 16 x M byte work area per CTA). */
+gfmc_status gfmc_run_clusters(gfmc_t* chains, int n_chains, const int64_t* n_updates, const int* cluster_ctas,
+                              uint64_t* n_accepted, uint8_t** decisions, double** d_omega_trace,
+                              double** magnetization, int64_t* n_mag, void* stream);
+
 /* ------------------------------------------------------------------------
  * Serving loop: a device-resident request loop over many chains.
  * A server is one persistent launch whose CTAs are split into slots.  Each

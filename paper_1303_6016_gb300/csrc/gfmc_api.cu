@@ -724,6 +724,182 @@ gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_update
     return result;
 }
 
+gfmc_status gfmc_run_clusters(gfmc_t* chains, int n_chains, const int64_t* n_updates, const int* cluster_ctas,
+                              uint64_t* n_accepted, uint8_t** decisions, double** d_omega_trace,
+                              double** magnetization, int64_t* n_mag, void* stream)
+{
+    if (!chains || n_chains < 1 || !n_updates || !cluster_ctas)
+        return fail(nullptr, GFMC_EINVAL, "need chains, n_chains >= 1, n_updates and cluster_ctas");
+    const int dev = chains[0] ? chains[0]->device : -1;
+    int dev_smem = 0;
+    cudaError_t e;
+    for (int c = 0; c < n_chains; ++c) {
+        gfmc_ctx* h = chains[c];
+        if (!h) return fail(nullptr, GFMC_EINVAL, "chain %d is NULL", c);
+        for (int d = 0; d < c; ++d)
+            if (chains[d] == h) return fail(nullptr, GFMC_EINVAL, "chain %d appears twice", c);
+        if (h->device != dev) return fail(nullptr, GFMC_EINVAL, "chain %d lives on another device", c);
+        if (h->recursion != GFMC_RECURSION_PROPOSAL)
+            return fail(nullptr, GFMC_EINVAL, "chain %d: clusters run the recursion on the proposal's vectors", c);
+        const int C = cluster_ctas[c];
+        if (C != 1 && C != 2 && C != 4 && C != 8 && C != 16)
+            return fail(nullptr, GFMC_EINVAL, "cluster_ctas[%d] = %d not in {1, 2, 4, 8, 16}", c, C);
+        if (h->N % C != 0) return fail(nullptr, GFMC_EINVAL, "chain %d: %d sites do not split over %d CTAs", c, h->N, C);
+        if (n_updates[c] < 0) return fail(nullptr, GFMC_EINVAL, "n_updates[%d] < 0", c);
+    }
+    if ((e = cudaSetDevice(dev)) != cudaSuccess) return cuda_fail(nullptr, e, "cudaSetDevice");
+    if ((e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+        return cuda_fail(nullptr, e, "querying shared memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    // groups of chains with the same precision and cluster size: one launch each
+    struct Group {
+        int prec, C;
+        size_t vec_bytes;
+        int work;
+        std::vector<int> members;
+    };
+    std::vector<Group> groups;
+    std::vector<gfmc::TeamJob> jobs(n_chains);
+    for (int c = 0; c < n_chains; ++c) {
+        gfmc_ctx* h = chains[c];
+        const int C = cluster_ctas[c];
+        const int T = h->N / C;
+        if ((unsigned long long)h->N * (unsigned long long)T >= (1ull << 32))
+            return fail(nullptr, GFMC_EINVAL, "chain %d: %d sites per CTA are too many for a cluster", c, T);
+        const size_t vsz = h->precision == GFMC_PREC_FP64 ? sizeof(double2) : sizeof(float2);
+        const size_t vb = (7 * (size_t)T * vsz + 255) & ~(size_t)255;
+        const int work = h->M * (int)sizeof(double2);
+        if (vb + work + 12 * 1024 > (size_t)dev_smem)
+            return fail(nullptr, GFMC_EINVAL, "chain %d: %zu B of lattice and %d B of work area per CTA exceed the "
+                        "%d B of shared memory; use a larger cluster", c, vb, work, dev_smem);
+        Group* g = nullptr;
+        for (auto& x : groups)
+            if (x.prec == h->precision && x.C == C) g = &x;
+        if (!g) {
+            groups.push_back({h->precision, C, 0, 0, {}});
+            g = &groups.back();
+        }
+        g->vec_bytes = std::max(g->vec_bytes, vb);
+        g->work = std::max(g->work, work);
+        g->members.push_back(c);
+        gfmc_status st = ensure_trace(h, std::max<int64_t>(n_updates[c], 1));
+        if (st == GFMC_OK) st = ensure_team_capacity(h, C);
+        if (st != GFMC_OK) return fail(nullptr, st, "chain %d: %s", c, h->err.c_str());
+        Params P = h->P;
+        P.ncta = C;
+        P.divT = (unsigned)(((1ull << 32) + (unsigned long long)T - 1) / (unsigned long long)T);
+        P.nv = 2;
+        P.mode = gfmc::MODE_SWEEP;
+        P.upd0 = h->counter;
+        P.n_updates = n_updates[c];
+        P.dec_out = h->d_dec;
+        P.domega_out = h->d_dom;
+        P.maxinc_out = h->d_maxinc;
+        P.mag_out = h->d_mag;
+        P.n_acc = h->d_nacc;
+        P.n_mag = h->d_nmag;
+        P.budget = h->budget;
+        P.stall = 0;
+        jobs[c].p = P;
+        jobs[c].cta0 = 0;
+        jobs[c].vec_smem = 1;
+        if ((e = cudaMemsetAsync(P.err, 0, sizeof(int) * 4, s)) != cudaSuccess ||
+            (e = cudaMemsetAsync(P.n_acc, 0, sizeof(unsigned long long), s)) != cudaSuccess ||
+            (e = cudaMemsetAsync(P.n_mag, 0, sizeof(long long), s)) != cudaSuccess)
+            return cuda_fail(nullptr, e, "clearing control words");
+    }
+    for (const auto& g : groups) {
+        int active = 0;
+        const int smem = (int)g.vec_bytes + g.work;
+        if ((e = gfmc::cluster_max_active(g.prec, g.C, smem, &active)) != cudaSuccess)
+            return cuda_fail(nullptr, e, "cluster occupancy");
+        if (active < 1)
+            return fail(nullptr, GFMC_EINVAL, "a cluster of %d CTAs with %d B of shared memory each cannot be scheduled",
+                        g.C, smem);
+    }
+    // one launch per group, each on its own stream, joined back into s
+    std::vector<gfmc::TeamJob> gjobs;
+    std::vector<size_t> goff;
+    for (const auto& g : groups) {
+        goff.push_back(gjobs.size());
+        for (int c : g.members) gjobs.push_back(jobs[c]);
+    }
+    gfmc::TeamJob* d_jobs = nullptr;
+    if ((e = cudaMalloc(&d_jobs, sizeof(gfmc::TeamJob) * gjobs.size())) != cudaSuccess)
+        return cuda_fail(nullptr, e, "allocating the job table");
+    struct Free {
+        void* p;
+        ~Free() { cudaFree(p); }
+    } guard{d_jobs};
+    if ((e = cudaMemcpyAsync(d_jobs, gjobs.data(), sizeof(gfmc::TeamJob) * gjobs.size(), cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+        return cuda_fail(nullptr, e, "uploading the job table");
+    std::vector<cudaStream_t> gs(groups.size(), nullptr);
+    std::vector<cudaEvent_t> ev(groups.size() + 1, nullptr);
+    struct Cleanup {
+        std::vector<cudaStream_t>& gs;
+        std::vector<cudaEvent_t>& ev;
+        ~Cleanup()
+        {
+            for (auto x : gs)
+                if (x) cudaStreamDestroy(x);
+            for (auto x : ev)
+                if (x) cudaEventDestroy(x);
+        }
+    } cleanup{gs, ev};
+    if ((e = cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventRecord(ev[0], s)) != cudaSuccess)
+        return cuda_fail(nullptr, e, "ordering the cluster launches");
+    for (size_t k = 0; k < groups.size(); ++k) {
+        const auto& g = groups[k];
+        const int smem = (int)g.vec_bytes + g.work;
+        if ((e = cudaStreamCreateWithFlags(&gs[k], cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(gs[k], ev[0], 0)) != cudaSuccess)
+            return cuda_fail(nullptr, e, "ordering the cluster launches");
+        e = g.prec == GFMC_PREC_FP64
+                ? gfmc::launch_cluster_f64(d_jobs + goff[k], (int)g.members.size(), g.C, (int)g.vec_bytes, smem, gs[k])
+                : gfmc::launch_cluster_f32(d_jobs + goff[k], (int)g.members.size(), g.C, (int)g.vec_bytes, smem, gs[k]);
+        if (e != cudaSuccess) return cuda_fail(nullptr, e, "launching clusters");
+        if ((e = cudaEventCreateWithFlags(&ev[k + 1], cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventRecord(ev[k + 1], gs[k])) != cudaSuccess || (e = cudaStreamWaitEvent(s, ev[k + 1], 0)) != cudaSuccess)
+            return cuda_fail(nullptr, e, "joining the cluster launches");
+    }
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(nullptr, e, "cluster execution");
+    gfmc_status result = GFMC_OK;
+    for (int c = 0; c < n_chains; ++c) {
+        gfmc_ctx* h = chains[c];
+        int err[4];
+        unsigned long long nacc = 0;
+        long long nm = 0;
+        if ((e = cudaMemcpy(err, h->P.err, sizeof(err), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+            (e = cudaMemcpy(&nacc, h->d_nacc, sizeof(nacc), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+            (e = cudaMemcpy(&nm, h->d_nmag, sizeof(nm), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(nullptr, e, "reading cluster status");
+        if (err[0] != 0) {
+            if (result == GFMC_OK) {
+                result = err[0] == gfmc::ERR_NUMERIC ? GFMC_ENUMERIC : GFMC_ECUDA;
+                fail(nullptr, result, "chain %d: device error %d at stage %d", c, err[0], err[1]);
+            }
+            continue;
+        }
+        if (n_updates[c] == 0) nm = 0;
+        if (n_accepted) n_accepted[c] = nacc;
+        if (n_mag) n_mag[c] = nm;
+        if (decisions && decisions[c] && n_updates[c] > 0 &&
+            (e = cudaMemcpy(decisions[c], h->d_dec, (size_t)n_updates[c], cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(nullptr, e, "copying decisions");
+        if (d_omega_trace && d_omega_trace[c] && n_updates[c] > 0 &&
+            (e = cudaMemcpy(d_omega_trace[c], h->d_dom, sizeof(double) * n_updates[c], cudaMemcpyDeviceToHost)) !=
+                cudaSuccess)
+            return cuda_fail(nullptr, e, "copying Delta Omega traces");
+        if (magnetization && magnetization[c] && nm > 0 &&
+            (e = cudaMemcpy(magnetization[c], h->d_mag, sizeof(double) * nm, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(nullptr, e, "copying magnetisations");
+        h->counter += (uint64_t)n_updates[c];
+    }
+    return result;
+}
+
 // ---------------------------------------------------------------------------
 // serving loop
 // ---------------------------------------------------------------------------

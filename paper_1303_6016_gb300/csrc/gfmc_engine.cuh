@@ -33,6 +33,7 @@
 // records GFMC_ETIMEOUT in p.err and all CTAs leave at their next wait.
 #pragma once
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -785,6 +786,151 @@ __device__ bool team_steps2(const Params& p, int cta, unsigned phase, typename C
     return true;
 }
 
+// Phase 0 and the steps of one update for a chain held by one thread-block
+// cluster: the recursion on the proposal's vectors o and v with every vector
+// value and forward bond of the lattice in the cluster's shared memory (CTA
+// `rank` holds sites [rank T, (rank+1) T), T = N / C).  Neighbour values and
+// backward bonds of sites held by other CTAs are read over DSMEM; one
+// hardware cluster barrier per step separates the steps (reads of step m are
+// done before step m+1 overwrites, writes of step m visible before step m+1
+// reads).  vs: [buffer][vector][T] values, then [3][T] forward bonds.
+template <class R>
+__device__ bool cluster_steps2(const Params& p, int rank, typename Cx<R>::T* vs, const int* s_loc,
+                               const double2* s_c, double (*red)[kEntries])
+{
+    namespace cg = cooperative_groups;
+    using R2 = typename Cx<R>::T;
+    cg::cluster_group cl = cg::this_cluster();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int N = p.N, L = p.L, C = p.ncta, T = N / C;
+    const int s0 = rank * T;
+    R2* fb = vs + 4 * (size_t)T;
+    const R2* hop;
+    if constexpr (sizeof(R) == 8) hop = (const R2*)p.hop64; else hop = (const R2*)p.hop32;
+    for (int sl = tid; sl < T; sl += kThreads)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) fb[a * T + sl] = ldcg2(hop + (size_t)a * N + s0 + sl);
+    cl.sync();
+
+    // the copy held by the owner of site j of the array that starts at base in every CTA
+    auto at = [&](R2* base, int j) -> R2* {
+        const int owner = (int)__umulhi((unsigned)j, p.divT);
+        return cl.map_shared_rank(base + (j - owner * T), owner);
+    };
+    auto bond = [&](int sl, int d, int nbj) -> R2 {  // Htilde_{i, nbr(i, d)}
+        const int a = d >> 1;
+        if ((d & 1) == 0) return fb[a * T + sl];
+        R2 h = *at(fb + (size_t)a * T, nbj);
+        h.y = -h.y;
+        return h;
+    };
+    R2 cv6[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) cv6[k] = c_make<R2>((R)s_c[k + 1].x, (R)s_c[k + 1].y);
+    const int lo = s_loc[0];
+
+    for (int sl = tid; sl < T; sl += kThreads) {
+        const int i = s0 + sl;
+        int nb[6];
+        site_nbrs(i, L, p.divL, p.divLL, nb);
+        R2 r0o = c_make<R2>(i == lo ? (R)1 : (R)0, (R)0), r0v = c_make<R2>(0, 0);
+        R2 r1o = c_make<R2>(0, 0), r1v = c_make<R2>(0, 0);
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            if (i == s_loc[k + 1]) {
+                r0v.x += cv6[k].x;
+                r0v.y += cv6[k].y;
+            }
+#pragma unroll
+        for (int d = 0; d < 6; ++d) {
+            const bool ho = nb[d] == lo;
+            bool hv = false;
+#pragma unroll
+            for (int k = 0; k < 6; ++k) hv |= nb[d] == s_loc[k + 1];
+            if (ho || hv) {
+                const R2 h = bond(sl, d, nb[d]);
+                if (ho) {
+                    r1o.x += h.x;
+                    r1o.y += h.y;
+                }
+#pragma unroll
+                for (int k = 0; k < 6; ++k)
+                    if (nb[d] == s_loc[k + 1]) c_fma(r1v, h, cv6[k]);
+            }
+        }
+        vs[sl] = r0o;
+        vs[T + sl] = r0v;
+        vs[2 * T + sl] = r1o;
+        vs[3 * T + sl] = r1v;
+    }
+    cl.sync();
+
+    for (int m = 1; m <= p.nsteps; ++m) {
+        R2* rd = vs + (size_t)((m & 1) ? 2 : 0) * T;  // [vector][T] of r_m
+        R2* wr = vs + (size_t)((m & 1) ? 0 : 2) * T;  // r_{m-1}, overwritten by r_{m+1}
+        double* prow = p.partial + ((size_t)(m - 1) * C + rank) * kEntries;
+        R acc[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) acc[e] = (R)0;
+        for (int sl = tid; sl < T; sl += kThreads) {
+            const int i = s0 + sl;
+            int nb[6];
+            site_nbrs(i, L, p.divL, p.divLL, nb);
+            R2 h[6], nv[2][6];
+#pragma unroll
+            for (int d = 0; d < 6; ++d) {
+                h[d] = bond(sl, d, nb[d]);
+                nv[0][d] = *at(rd, nb[d]);
+                nv[1][d] = *at(rd + T, nb[d]);
+            }
+            R2 cur[2], nxt[2];
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+                cur[v] = rd[v * T + sl];
+                const R2 pv = wr[v * T + sl];
+                R2 a = c_make<R2>(0, 0);
+#pragma unroll
+                for (int d = 0; d < 6; ++d) c_fma(a, h[d], nv[v][d]);
+                nxt[v] = c_make<R2>(fma((R)2, a.x, -pv.x), fma((R)2, a.y, -pv.y));
+                wr[v * T + sl] = nxt[v];
+            }
+            const R2 a = cur[0], b = cur[1], na = nxt[0], nbv = nxt[1];
+            acc[0] = fma(a.x, a.x, fma(a.y, a.y, acc[0]));
+            acc[1] = fma(b.x, b.x, fma(b.y, b.y, acc[1]));
+            acc[2] = fma(a.x, b.x, fma(a.y, b.y, acc[2]));
+            acc[3] = fma(a.x, b.y, fma(-a.y, b.x, acc[3]));
+            acc[4] = fma(a.x, na.x, fma(a.y, na.y, acc[4]));
+            acc[5] = fma(b.x, nbv.x, fma(b.y, nbv.y, acc[5]));
+            acc[6] = fma(a.x, nbv.x, fma(a.y, nbv.y, acc[6]));
+            acc[7] = fma(a.x, nbv.y, fma(-a.y, nbv.x, acc[7]));
+        }
+        const R s8 = warp_reduce_scatter8(acc, lane);
+        if ((lane & 3) == 0) red[warp][lane >> 2] = (double)s8;
+        __syncthreads();
+        if (tid < 8) {
+            double sum = 0.0;
+#pragma unroll
+            for (int w = 0; w < kWarps; ++w) sum += red[w][tid];
+            prow[tid] = sum;
+        }
+        cl.sync();
+    }
+    return true;
+}
+
+// Barrier of all CTAs of a chain: the grid barrier of a cooperative team, or
+// the hardware barrier of the chain's cluster (VARIANT 2; no wait can time out,
+// so every CTA of a cluster always runs the same sequence of barriers).
+template <int VARIANT> __device__ __forceinline__ bool chain_barrier(const Params& p, int where)
+{
+    if constexpr (VARIANT == 2) {
+        cooperative_groups::this_cluster().sync();
+        return true;
+    } else {
+        return grid_barrier(p, where);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // the engine
 // ---------------------------------------------------------------------------
@@ -805,6 +951,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                                           typename Cx<R>::T* vec_smem)
 {
     static_assert(NV == kVec || NV == 2, "recursion on 7 unit vectors or on o and v");
+    static_assert(VARIANT != 2 || NV == 2, "cluster variant: recursion on o and v");
     using R2 = typename Cx<R>::T;
     __shared__ double red[kWarps][kEntries];
     __shared__ double2 s_mu2[kWarps][2][kPairs];
@@ -819,7 +966,8 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int N = p.N, L = p.L, M = p.M;
-    const int s0 = p.tile_start[cta], s1 = p.tile_start[cta + 1];
+    const int s0 = VARIANT == 2 ? cta * (p.N / p.ncta) : p.tile_start[cta];
+    const int s1 = VARIANT == 2 ? s0 + p.N / p.ncta : p.tile_start[cta + 1];
     const int i = s0 + tid;
     const bool active = VARIANT == 0 && i < s1;
     const R2* hop = nullptr;
@@ -1049,6 +1197,8 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                     cur[v] = nxt[v];
                 }
             }
+        } else if constexpr (VARIANT == 2) {
+            cluster_steps2<R>(p, cta, vec_smem, s_loc, s_c, red);
         } else if constexpr (NV == 2) {
             if (vec_smem) {
                 if (!team_steps2<R>(p, cta, phase, buf0, buf1, s_loc, s_c, red, SmemVec{})) return;
@@ -1063,7 +1213,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
             }
         }
         phase += (unsigned)p.nsteps + 1u;
-        if (!grid_barrier(p, 1)) return;
+        if (!chain_barrier<VARIANT>(p, 1)) return;
 
         // ---- reduce: partial Gram sums -> mu_n -> damped, twisted combined sequences ----
         if (tid < kPairs) {
@@ -1171,7 +1321,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 __syncwarp();
             }
         }
-        if (!grid_barrier(p, 2)) return;
+        if (!chain_barrier<VARIANT>(p, 2)) return;
         if (p.mode == MODE_MOMENTS) return;
 
         // ---- FFT of the four sequences and G_V at the nodes ----
@@ -1203,7 +1353,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 __syncthreads();
             }
         }
-        if (!grid_barrier(p, 3)) return;
+        if (!chain_barrier<VARIANT>(p, 3)) return;
 
         // ---- d_k, continuous phase, Chebyshev-Gauss partial sums ----
         {
@@ -1245,7 +1395,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 p.qpart[2 * cta + 1] = pm;
             }
         }
-        if (!grid_barrier(p, 4)) return;
+        if (!chain_barrier<VARIANT>(p, 4)) return;
 
         // ---- Delta Omega, Metropolis decision, patch ----
         if (tid == 0) {
@@ -1293,7 +1443,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 p.hop32[at] = make_float2((float)hv.x, (float)hv.y);
             }
         }
-        if (!grid_barrier(p, 5)) return;
+        if (!chain_barrier<VARIANT>(p, 5)) return;
 
         // ---- magnetisation after each completed sweep ----
         if ((upd + 1ull) % (unsigned long long)N == 0ull) {
@@ -1314,7 +1464,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
             if (tid == 0) p.magpart[3 * cta + 1] = a0;
             block_sum_max(sz, 0.0, &a0, &b0);
             if (tid == 0) p.magpart[3 * cta + 2] = a0;
-            if (!grid_barrier(p, 6)) return;
+            if (!chain_barrier<VARIANT>(p, 6)) return;
             if (cta == 0 && tid == 0) {
                 double X = 0.0, Y = 0.0, Z = 0.0;
                 for (int c = 0; c < p.ncta; ++c) {
@@ -1363,6 +1513,24 @@ __global__ void __launch_bounds__(kThreads, 1) gfmc_team_engine(const TeamJob* _
     R2* vs = s_vs ? (R2*)dyn_all : nullptr;
     if (sp.nv == 2) run_chain<R, 1, 2>(sp, s_cta, dyn_all + vec_bytes / (int)sizeof(double2), vs);
     else run_chain<R, 1>(sp, s_cta, dyn_all + vec_bytes / (int)sizeof(double2), vs);
+}
+
+// A batch of chains, one thread-block cluster per chain (cluster size C = the
+// chains' p.ncta), all on the recursion of the proposal's vectors; the
+// dynamic shared memory holds [vector area of vec_bytes][work area].
+template <class R>
+__global__ void __launch_bounds__(kThreads, 1) gfmc_cluster_engine(const TeamJob* __restrict__ jobs, int vec_bytes)
+{
+    extern __shared__ double2 dyn_all[];
+    __shared__ Params sp;
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int job = (int)(blockIdx.x / cl.dim_blocks().x);
+    if (threadIdx.x == 0) sp = jobs[job].p;
+    __syncthreads();
+    using R2 = typename Cx<R>::T;
+    run_chain<R, 2, 2>(sp, rank, dyn_all + vec_bytes / (int)sizeof(double2), (R2*)dyn_all);
 }
 
 }  // namespace gfmc

@@ -26,6 +26,7 @@ struct Params {
     // lattice and model
     int L, N, M, nsteps, ncta;
     unsigned divL, divLL;  // ceil(2^32 / L), ceil(2^32 / L^2): exact i / L, i / L^2 for i < N
+    unsigned divT;         // cluster variant: ceil(2^32 / (N / ncta)), the owner of a site
     double t, chem, beta, a;
 
     // chain state
@@ -117,6 +118,10 @@ cudaError_t launch_team_f64(const TeamJob* d_jobs, int njobs, int grid, int vec_
 cudaError_t launch_team_f32(const TeamJob* d_jobs, int njobs, int grid, int vec_bytes, int smem, cudaStream_t s);
 cudaError_t team_max_ctas(int precision, int smem, int* out);
 cudaError_t launch_server(const ServerArgs& a, int grid, int smem, cudaStream_t s);
+// one cluster of C CTAs per job (recursion on the proposal's vectors)
+cudaError_t launch_cluster_f64(const TeamJob* d_jobs, int njobs, int C, int vec_bytes, int smem, cudaStream_t s);
+cudaError_t launch_cluster_f32(const TeamJob* d_jobs, int njobs, int C, int vec_bytes, int smem, cudaStream_t s);
+cudaError_t cluster_max_active(int precision, int C, int smem, int* out);
 cudaError_t server_max_ctas(int smem, int* out);
 int engine_smem_bytes(int M);
 cudaError_t engine_max_ctas(int precision, int M, int* out);

@@ -56,3 +56,52 @@ cudaError_t team_max_ctas_f32(int smem, int* out)
 }
 
 }  // namespace gfmc
+
+namespace gfmc {
+
+static cudaError_t cluster_config_f32(int C, int smem)
+{
+    cudaError_t e = cudaFuncSetAttribute(gfmc_cluster_engine<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess && C > 8)
+        e = cudaFuncSetAttribute(gfmc_cluster_engine<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+
+cudaError_t launch_cluster_f32(const TeamJob* d_jobs, int njobs, int C, int vec_bytes, int smem, cudaStream_t s)
+{
+    cudaError_t e = cluster_config_f32(C, smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(C * njobs));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, gfmc_cluster_engine<float>, d_jobs, vec_bytes);
+}
+
+cudaError_t cluster_max_active_f32(int C, int smem, int* out)
+{
+    cudaError_t e = cluster_config_f32(C, smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)C);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(out, gfmc_cluster_engine<float>, &cfg);
+}
+
+}  // namespace gfmc

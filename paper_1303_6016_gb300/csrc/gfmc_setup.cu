@@ -34,6 +34,14 @@ int engine_smem_bytes(int M)
     return fft > stage ? fft : stage;
 }
 
+cudaError_t cluster_max_active_f64(int C, int smem, int* out);
+cudaError_t cluster_max_active_f32(int C, int smem, int* out);
+
+cudaError_t cluster_max_active(int precision, int C, int smem, int* out)
+{
+    return precision == 0 ? cluster_max_active_f64(C, smem, out) : cluster_max_active_f32(C, smem, out);
+}
+
 cudaError_t engine_max_ctas(int precision, int M, int* out)
 {
     int per_sm = 0;

@@ -30,7 +30,8 @@ RECURSIONS = {"unit_vectors": 0, "proposal": 1}
 EXPORTS = ("gfmc_default_options", "gfmc_create", "gfmc_moments", "gfmc_delta_omega",
            "gfmc_updates", "gfmc_sweep", "gfmc_get_spins", "gfmc_set_state", "gfmc_get_counter",
            "gfmc_set_wait_budget", "gfmc_inject_stall", "gfmc_last_error", "gfmc_destroy",
-           "gfmc_delta_omega_noalloc", "gfmc_run_batch", "gfmc_server_create", "gfmc_server_submit",
+           "gfmc_delta_omega_noalloc", "gfmc_run_batch", "gfmc_run_clusters", "gfmc_server_create",
+           "gfmc_server_submit",
            "gfmc_server_poll", "gfmc_server_last_error", "gfmc_server_destroy")
 
 
@@ -88,6 +89,8 @@ def load(path: str = LIB_PATH):
                                  ctypes.POINTER(ctypes.POINTER(ctypes.c_double)),
                                  ctypes.POINTER(ctypes.POINTER(ctypes.c_double)), ctypes.POINTER(i64), vp]
     L.gfmc_run_batch.restype = ctypes.c_int
+    L.gfmc_run_clusters.argtypes = L.gfmc_run_batch.argtypes
+    L.gfmc_run_clusters.restype = ctypes.c_int
     L.gfmc_server_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(vp)]
     L.gfmc_server_create.restype = ctypes.c_int
     L.gfmc_server_submit.argtypes = [vp, ctypes.c_int, vp, i64, ctypes.POINTER(ctypes.c_uint8), d]
@@ -241,7 +244,13 @@ class Chain:
         return int(c.value)
 
 
-def run_batch(chains, n_updates, team_ctas=None, trace=True, stream=None) -> list:
+def run_clusters(chains, n_updates, cluster_ctas, trace=True, stream=None) -> list:
+    """Chains on the proposal-vector recursion, each on one thread-block
+    cluster holding its lattice in shared memory (gfmc_run_clusters)."""
+    return run_batch(chains, n_updates, cluster_ctas, trace, stream, _fn="gfmc_run_clusters")
+
+
+def run_batch(chains, n_updates, team_ctas=None, trace=True, stream=None, _fn="gfmc_run_batch") -> list:
     """One launch over several chains (each on its own team of CTAs).
     Returns one dict per chain with n_accepted and, if trace, the decisions and
     Delta Omega trace."""
@@ -260,7 +269,7 @@ def run_batch(chains, n_updates, team_ctas=None, trace=True, stream=None) -> lis
     NM = (ctypes.c_int64 * n)()
     if stream is None:
         stream = current_stream_handle()
-    st = lib.gfmc_run_batch(H, n, NU, TC, acc, DP if trace else None, OP if trace else None, MP, NM, stream)
+    st = getattr(lib, _fn)(H, n, NU, TC, acc, DP if trace else None, OP if trace else None, MP, NM, stream)
     if st != GFMC_OK:
         raise GfmcError(st, lib.gfmc_last_error(None).decode())
     return [{"n_accepted": int(acc[c]), "decisions": decs[c], "d_omega": doms[c],
