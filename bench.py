@@ -279,6 +279,38 @@ def run_batching(stream, steps, warmup, updates, flush, recursion="unit_vectors"
                       "mu = -2t, M = 1024, FP32-mixed, spins uniform (seed = chain index)"}
 
 
+def run_batching_clusters(stream, steps, warmup, updates, flush):
+    """The 64-chain batching workload on thread-block clusters (proposal-vector
+    recursion, FP32-mixed): each chain's lattice in the shared memory of the
+    smallest cluster that holds it; a step runs `updates` updates of every
+    chain."""
+    import torch
+    from paper_1303_6016_gb300 import batch
+    chains, Ls, Ts = batch.c4_chains(M=1024, recursion="proposal")
+    runner = batch.ClusterRunner(chains)
+    for _ in range(warmup):
+        runner.run(updates)
+    per = []
+    for k in range(steps):
+        flush.fill_(k)
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        runner.run(updates)
+        e.record()
+        e.synchronize()
+        per.append(s.elapsed_time(e))
+    total = sum(per)
+    n = len(chains)
+    by_L = {str(int(L)): c for L, c in sorted(zip(Ls, runner.cluster_ctas))}
+    for ch in chains:
+        ch.close()
+    return {"value": n * updates * steps / (total / 1000.0), "unit": UNIT, "chains": n,
+            "updates_per_chain_per_step": updates, "ms_per_step": total / steps,
+            "cluster_ctas_by_L": by_L, "recursion": "proposal",
+            "config": "the batching workload (64 chains, L from {8,12,16,24,32}, M = 1024, FP32-mixed), "
+                      "each chain on one thread-block cluster holding its lattice in shared memory"}
+
+
 def time_device(ch, stream, U, steps, warmup, flush, dist, sampler=None):
     """Device-timed steps: CUDA events on the chain's stream around each step,
     a 256 MiB L2 flush between steps outside the events."""
@@ -509,6 +541,8 @@ def main():
         if not args.no_variant:
             line["batching_proposal_recursion"] = run_batching(stream, max(3, args.steps // 2), 3,
                                                                args.batch_updates, flush, "proposal")
+            line["batching_clusters"] = run_batching_clusters(stream, max(3, args.steps // 2), 3,
+                                                              args.batch_updates, flush)
 
     if not args.no_serving:
         from paper_1303_6016_gb300 import serving

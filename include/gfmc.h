@@ -179,20 +179,28 @@ gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_update
 
 /* Run chains that use the recursion on the proposal's vectors
  * (GFMC_RECURSION_PROPOSAL), each on one thread-block cluster of
- * cluster_ctas[c] CTAs (1, 2, 4, 8 or 16; it must divide N) that holds the
- * chain's whole lattice -- both vectors' two recursion buffers and the
- * forward bonds -- in its shared memory and reads neighbours in other CTAs of
- * the cluster over distributed shared memory; one hardware cluster barrier
+ * cluster_ctas[c] CTAs (1, 2, 4, 8 or 16; it must divide L: each CTA holds a
+ * slab of L / C whole z-planes) that holds the chain's whole lattice -- both
+ * vectors' two recursion buffers and the forward bonds -- in its shared memory
+ * and reads the z-neighbours held by the CTAs below and above over
+ * distributed shared memory; one hardware cluster barrier
  * per recursion step (Eq. recursive), no global-memory exchange.  Clusters are
  * independent: chains of the same precision and cluster size share a launch,
  * launches of different groups overlap, and clusters need not all be resident
  * at once.  Results as gfmc_updates would give them (up to the rounding order
  * of the sums); the outputs are as for gfmc_run_batch.  GFMC_EINVAL when a
- * chain's lattice does not fit in the shared memory of its cluster (about
- * 7 x N/C x 8 bytes FP32, x 16 FP64, plus a 16 x M byte work area per CTA). */
+ * chain's lattice does not fit in the shared memory of its cluster (80 bytes
+ * per site FP32, 112 FP64, N / C sites per CTA, plus a 16 x M byte work area
+ * per CTA). */
 gfmc_status gfmc_run_clusters(gfmc_t* chains, int n_chains, const int64_t* n_updates, const int* cluster_ctas,
                               uint64_t* n_accepted, uint8_t** decisions, double** d_omega_trace,
                               double** magnetization, int64_t* n_mag, void* stream);
+
+/* The smallest cluster size (1, 2, 4, 8 or 16 CTAs, dividing L) whose shared
+ * memory holds a chain of side L with M moments in the given precision on the
+ * current device, for gfmc_run_clusters.  GFMC_EINVAL (and 0) when none does
+ * or the arguments are out of range (L in [3, 64], M a power of two >= 16). */
+gfmc_status gfmc_cluster_min_ctas(int L, int M, int precision, int* cluster_ctas);
 
 /* ------------------------------------------------------------------------
  * Serving loop: a device-resident request loop over many chains.

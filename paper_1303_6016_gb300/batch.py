@@ -2,7 +2,10 @@
 
 Independent Monte Carlo chains share nothing (Sec. 3.2: the sweep loop splits
 into independent chains), so a batch runs all of them in one launch of the
-team engine, each chain on its own team of CTAs (``gfmc_run_batch``).
+team engine, each chain on its own team of CTAs (``gfmc_run_batch``), or --
+for chains on the proposal-vector recursion -- each on one thread-block
+cluster that holds its lattice in shared memory (``ClusterRunner``,
+``gfmc_run_clusters``).
 
 The autotuner measures, on the device, the time of one update of a probe
 chain of each lattice size at candidate team sizes, then shares the device's
@@ -128,6 +131,24 @@ class BatchRunner:
             for k, i in enumerate(w):
                 out[i] = dict(res[k], team_ctas=tc[k])
         return out
+
+
+class ClusterRunner:
+    """Runs chains with the recursion on the proposal's vectors on
+    thread-block clusters (gfmc_run_clusters): each chain on the smallest
+    cluster whose shared memory holds its lattice -- the fewest SMs per chain,
+    hence the most chains in flight -- all chains in one call (one launch per
+    cluster size and precision, the launches overlapping)."""
+
+    def __init__(self, chains):
+        self.chains = list(chains)
+        self.cluster_ctas = [gfmc.cluster_min_ctas(c.L, c.M, c.precision) for c in self.chains]
+
+    def run(self, updates_per_chain, trace: bool = False):
+        n = len(self.chains)
+        updates = list(updates_per_chain) if hasattr(updates_per_chain, "__len__") else [updates_per_chain] * n
+        res = gfmc.run_clusters(self.chains, updates, self.cluster_ctas, trace=trace)
+        return [dict(r, cluster_ctas=c) for r, c in zip(res, self.cluster_ctas)]
 
 
 def c4_chains(n_chains: int = 64, M: int = 1024, precision: str = "fp32_mixed", seed: int = 4,

@@ -724,6 +724,43 @@ gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_update
     return result;
 }
 
+// Bytes of shared memory a CTA of a cluster of C CTAs needs for a chain of
+// side L with M moments: its slab of the lattice (two recursion buffers of
+// (o, v) and three forward bonds per site) plus the work area of the tail.
+static size_t cluster_lattice_bytes(int L, int C, int precision)
+{
+    const size_t per_site = precision == GFMC_PREC_FP64 ? 2 * 32 + 3 * 16 : 2 * 16 + 3 * 16;
+    const size_t T = (size_t)L * L * L / (size_t)C;
+    return (per_site * T + 255) & ~(size_t)255;
+}
+static constexpr int kClusterStaticReserve = 12 * 1024;  // the engine's static shared memory, rounded up
+
+static bool cluster_fits(int L, int M, int C, int precision, int dev_smem)
+{
+    return L % C == 0 && cluster_lattice_bytes(L, C, precision) + (size_t)M * sizeof(double2) + kClusterStaticReserve <=
+                             (size_t)dev_smem;
+}
+
+gfmc_status gfmc_cluster_min_ctas(int L, int M, int precision, int* cluster_ctas)
+{
+    if (!cluster_ctas || L < 3 || L > gfmc::kMaxL || M < 16 || (M & (M - 1)) != 0 ||
+        (precision != GFMC_PREC_FP64 && precision != GFMC_PREC_FP32_MIXED))
+        return fail(nullptr, GFMC_EINVAL, "need 3 <= L <= %d, M a power of two >= 16, a precision and an output",
+                    gfmc::kMaxL);
+    int dev = 0, dev_smem = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+        return cuda_fail(nullptr, e, "querying shared memory");
+    for (int C = 1; C <= 16; C *= 2)
+        if (cluster_fits(L, M, C, precision, dev_smem)) {
+            *cluster_ctas = C;
+            return GFMC_OK;
+        }
+    *cluster_ctas = 0;
+    return fail(nullptr, GFMC_EINVAL, "no cluster of up to 16 CTAs holds an L=%d lattice with M=%d", L, M);
+}
+
 gfmc_status gfmc_run_clusters(gfmc_t* chains, int n_chains, const int64_t* n_updates, const int* cluster_ctas,
                               uint64_t* n_accepted, uint8_t** decisions, double** d_omega_trace,
                               double** magnetization, int64_t* n_mag, void* stream)
@@ -744,7 +781,8 @@ gfmc_status gfmc_run_clusters(gfmc_t* chains, int n_chains, const int64_t* n_upd
         const int C = cluster_ctas[c];
         if (C != 1 && C != 2 && C != 4 && C != 8 && C != 16)
             return fail(nullptr, GFMC_EINVAL, "cluster_ctas[%d] = %d not in {1, 2, 4, 8, 16}", c, C);
-        if (h->N % C != 0) return fail(nullptr, GFMC_EINVAL, "chain %d: %d sites do not split over %d CTAs", c, h->N, C);
+        if (h->L % C != 0)
+            return fail(nullptr, GFMC_EINVAL, "chain %d: %d z-planes do not split over %d CTAs", c, h->L, C);
         if (n_updates[c] < 0) return fail(nullptr, GFMC_EINVAL, "n_updates[%d] < 0", c);
     }
     if ((e = cudaSetDevice(dev)) != cudaSuccess) return cuda_fail(nullptr, e, "cudaSetDevice");
@@ -766,10 +804,9 @@ gfmc_status gfmc_run_clusters(gfmc_t* chains, int n_chains, const int64_t* n_upd
         const int T = h->N / C;
         if ((unsigned long long)h->N * (unsigned long long)T >= (1ull << 32))
             return fail(nullptr, GFMC_EINVAL, "chain %d: %d sites per CTA are too many for a cluster", c, T);
-        const size_t vsz = h->precision == GFMC_PREC_FP64 ? sizeof(double2) : sizeof(float2);
-        const size_t vb = (7 * (size_t)T * vsz + 255) & ~(size_t)255;
+        const size_t vb = cluster_lattice_bytes(h->L, C, h->precision);
         const int work = h->M * (int)sizeof(double2);
-        if (vb + work + 12 * 1024 > (size_t)dev_smem)
+        if (!cluster_fits(h->L, h->M, C, h->precision, dev_smem))
             return fail(nullptr, GFMC_EINVAL, "chain %d: %zu B of lattice and %d B of work area per CTA exceed the "
                         "%d B of shared memory; use a larger cluster", c, vb, work, dev_smem);
         Group* g = nullptr;

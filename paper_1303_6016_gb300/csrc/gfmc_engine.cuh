@@ -786,41 +786,213 @@ __device__ bool team_steps2(const Params& p, int cta, unsigned phase, typename C
     return true;
 }
 
+// ---------------------------------------------------------------------------
+// distributed shared memory of a cluster (explicit shared::cluster accesses)
+// ---------------------------------------------------------------------------
+
+// Per site, the values of |o> and |v> split by real and imaginary part:
+// re = (Re o, Re v), im = (Im o, Im v), so that one packed FP32 FMA advances
+// both vectors (FP64 uses the same layout with scalar FMAs).
+template <class R> struct alignas(4 * sizeof(R)) SOV {
+    typename Cx<R>::T re, im;
+};
+// A stored forward bond Htilde_{i, i+e_alpha}: FP32 with each part
+// duplicated, (re, re) and (im, im), the operands of the packed FMAs.
+template <class R> struct BondSm;
+template <> struct alignas(16) BondSm<float> {
+    float2 re2, im2;
+};
+template <> struct alignas(16) BondSm<double> {
+    double re, im;
+};
+__device__ __forceinline__ BondSm<float> make_bond(float2 h) { return {make_float2(h.x, h.x), make_float2(h.y, h.y)}; }
+__device__ __forceinline__ BondSm<double> make_bond(double2 h) { return {h.x, h.y}; }
+__device__ __forceinline__ float2 bond_value(const BondSm<float>& b) { return make_float2(b.re2.x, b.im2.x); }
+__device__ __forceinline__ double2 bond_value(const BondSm<double>& b) { return make_double2(b.re, b.im); }
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// the shared::cluster address of shared::cta address a in CTA `rank` of the cluster
+__device__ __forceinline__ unsigned cluster_addr(unsigned a, int rank)
+{
+    unsigned r;
+    asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+// Loads from shared::cluster addresses (this CTA or another CTA of the
+// cluster).  volatile: never moved across the cluster barriers, which are
+// volatile asm too.
+__device__ __forceinline__ void ld_dsm(unsigned a, SOV<float>& q)
+{
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(q.re.x), "=f"(q.re.y), "=f"(q.im.x), "=f"(q.im.y) : "r"(a));
+}
+__device__ __forceinline__ void ld_dsm(unsigned a, SOV<double>& q)
+{
+    asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(q.re.x), "=d"(q.re.y) : "r"(a));
+    asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2+16];" : "=d"(q.im.x), "=d"(q.im.y) : "r"(a));
+}
+__device__ __forceinline__ void ld_dsm(unsigned a, BondSm<float>& b)
+{
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(b.re2.x), "=f"(b.re2.y), "=f"(b.im2.x), "=f"(b.im2.y) : "r"(a));
+}
+__device__ __forceinline__ void ld_dsm(unsigned a, BondSm<double>& b)
+{
+    asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(b.re), "=d"(b.im) : "r"(a));
+}
+
+// Htilde r summed over the 6 bonds of a site, for both vectors at once:
+// P = sum Re h * re, Q = sum Re h * im, S = sum Im h * im, W = sum Im h * re,
+// forward (stored) and backward (conjugated: Im h enters with a minus) bonds
+// kept apart; then (Htilde r).re = P - S, (Htilde r).im = Q + W.
+template <class R> struct Stencil;
+template <> struct Stencil<float> {
+    float2 P = {0.f, 0.f}, Q = {0.f, 0.f}, Sf = {0.f, 0.f}, Sb = {0.f, 0.f}, Wf = {0.f, 0.f}, Wb = {0.f, 0.f};
+    __device__ __forceinline__ void add(const BondSm<float>& b, const SOV<float>& r, bool fwd)
+    {
+        P = __ffma2_rn(b.re2, r.re, P);
+        Q = __ffma2_rn(b.re2, r.im, Q);
+        if (fwd) {
+            Sf = __ffma2_rn(b.im2, r.im, Sf);
+            Wf = __ffma2_rn(b.im2, r.re, Wf);
+        } else {
+            Sb = __ffma2_rn(b.im2, r.im, Sb);
+            Wb = __ffma2_rn(b.im2, r.re, Wb);
+        }
+    }
+    // r_{m+1} = 2 Htilde r_m - r_{m-1}
+    __device__ __forceinline__ SOV<float> next(const SOV<float>& prv) const
+    {
+        const float2 m1 = make_float2(-1.f, -1.f);
+        const float2 hre = __fadd2_rn(__ffma2_rn(Sf, m1, P), Sb);  // P - Sf + Sb
+        const float2 him = __ffma2_rn(Wb, m1, __fadd2_rn(Q, Wf));  // Q + Wf - Wb
+        SOV<float> n;
+        n.re = __ffma2_rn(prv.re, m1, __fadd2_rn(hre, hre));
+        n.im = __ffma2_rn(prv.im, m1, __fadd2_rn(him, him));
+        return n;
+    }
+};
+template <> struct Stencil<double> {
+    double2 P = {0.0, 0.0}, Q = {0.0, 0.0}, S = {0.0, 0.0}, W = {0.0, 0.0};
+    __device__ __forceinline__ void add(const BondSm<double>& b, const SOV<double>& r, bool fwd)
+    {
+        const double hi = fwd ? b.im : -b.im;
+        P.x = fma(b.re, r.re.x, P.x);
+        P.y = fma(b.re, r.re.y, P.y);
+        Q.x = fma(b.re, r.im.x, Q.x);
+        Q.y = fma(b.re, r.im.y, Q.y);
+        S.x = fma(hi, r.im.x, S.x);
+        S.y = fma(hi, r.im.y, S.y);
+        W.x = fma(hi, r.re.x, W.x);
+        W.y = fma(hi, r.re.y, W.y);
+    }
+    __device__ __forceinline__ SOV<double> next(const SOV<double>& prv) const
+    {
+        SOV<double> n;
+        n.re.x = fma(2.0, P.x - S.x, -prv.re.x);
+        n.re.y = fma(2.0, P.y - S.y, -prv.re.y);
+        n.im.x = fma(2.0, Q.x + W.x, -prv.im.x);
+        n.im.y = fma(2.0, Q.y + W.y, -prv.im.y);
+        return n;
+    }
+};
+
+// The 8 Gram sums of one site (a = o, b = v at step m; na, nb at m+1):
+// |a|^2, |b|^2, Re a*b, Im a*b, Re a*na, Re b*nb, Re a*nb, Im a*nb.
+template <class R> struct GramAcc;
+template <> struct GramAcc<float> {
+    float2 X1 = {0.f, 0.f}, X2 = {0.f, 0.f};  // (|a|^2, |b|^2), (Re a*na, Re b*nb)
+    float c2 = 0.f, c3 = 0.f, c6 = 0.f, c7 = 0.f;
+    __device__ __forceinline__ void add(const SOV<float>& c, const SOV<float>& n)
+    {
+        X1 = __ffma2_rn(c.re, c.re, X1);
+        X1 = __ffma2_rn(c.im, c.im, X1);
+        X2 = __ffma2_rn(c.re, n.re, X2);
+        X2 = __ffma2_rn(c.im, n.im, X2);
+        c2 = fmaf(c.re.x, c.re.y, fmaf(c.im.x, c.im.y, c2));
+        c3 = fmaf(c.re.x, c.im.y, fmaf(-c.im.x, c.re.y, c3));
+        c6 = fmaf(c.re.x, n.re.y, fmaf(c.im.x, n.im.y, c6));
+        c7 = fmaf(c.re.x, n.im.y, fmaf(-c.im.x, n.re.y, c7));
+    }
+    __device__ __forceinline__ void out(float (&v)[8]) const
+    {
+        v[0] = X1.x; v[1] = X1.y; v[2] = c2; v[3] = c3;
+        v[4] = X2.x; v[5] = X2.y; v[6] = c6; v[7] = c7;
+    }
+};
+template <> struct GramAcc<double> {
+    double v[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    __device__ __forceinline__ void add(const SOV<double>& c, const SOV<double>& n)
+    {
+        v[0] = fma(c.re.x, c.re.x, fma(c.im.x, c.im.x, v[0]));
+        v[1] = fma(c.re.y, c.re.y, fma(c.im.y, c.im.y, v[1]));
+        v[2] = fma(c.re.x, c.re.y, fma(c.im.x, c.im.y, v[2]));
+        v[3] = fma(c.re.x, c.im.y, fma(-c.im.x, c.re.y, v[3]));
+        v[4] = fma(c.re.x, n.re.x, fma(c.im.x, n.im.x, v[4]));
+        v[5] = fma(c.re.y, n.re.y, fma(c.im.y, n.im.y, v[5]));
+        v[6] = fma(c.re.x, n.re.y, fma(c.im.x, n.im.y, v[6]));
+        v[7] = fma(c.re.x, n.im.y, fma(-c.im.x, n.re.y, v[7]));
+    }
+    __device__ __forceinline__ void out(double (&o)[8]) const
+    {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) o[e] = v[e];
+    }
+};
+
 // Phase 0 and the steps of one update for a chain held by one thread-block
-// cluster: the recursion on the proposal's vectors o and v with every vector
-// value and forward bond of the lattice in the cluster's shared memory (CTA
-// `rank` holds sites [rank T, (rank+1) T), T = N / C).  Neighbour values and
-// backward bonds of sites held by other CTAs are read over DSMEM; one
-// hardware cluster barrier per step separates the steps (reads of step m are
-// done before step m+1 overwrites, writes of step m visible before step m+1
-// reads).  vs: [buffer][vector][T] values, then [3][T] forward bonds.
+// cluster of C CTAs: the recursion on the proposal's vectors o and v with
+// every vector value and forward bond of the lattice in the cluster's shared
+// memory.  The lattice is cut into slabs of P = L / C whole z-planes; CTA
+// `rank` holds planes [rank P, (rank+1) P), T = P L^2 sites, so that the +-x
+// and +-y neighbours of a site are in its own CTA and only the +-z neighbours
+// of the first and last plane (and the backward z bond of the first) are read
+// from the CTA below or above over DSMEM.  One hardware cluster barrier per
+// step separates the steps (reads of step m are done before step m+1
+// overwrites, writes of step m visible before step m+1 reads).
+// vs: [buffer][T] of SOV, then [3][T] stored forward bonds.
+// Per step each warp writes its 8 Gram sums (type R) to its own slot of the
+// step's partial row, [C][kWarps][8] in the rows of kEntries doubles; the
+// reduce phase adds them over warps and CTAs in FP64, so a step has no CTA
+// barrier and no FP64 arithmetic.  The cluster barrier is split: a CTA
+// arrives once its stores of r_{m+1} are issued, reduces its warps' sums,
+// then waits.  U sites per thread have all their loads issued before any
+// arithmetic.
 template <class R>
 __device__ bool cluster_steps2(const Params& p, int rank, typename Cx<R>::T* vs, const int* s_loc,
                                const double2* s_c, double (*red)[kEntries])
 {
     namespace cg = cooperative_groups;
     using R2 = typename Cx<R>::T;
+    using Q = SOV<R>;
+    using B = BondSm<R>;
+    constexpr int U = sizeof(R) == 4 ? 2 : 1;
     cg::cluster_group cl = cg::this_cluster();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int N = p.N, L = p.L, C = p.ncta, T = N / C;
+    const int N = p.N, L = p.L, C = p.ncta, LL = L * L, T = N / C, P = L / C;
     const int s0 = rank * T;
-    R2* fb = vs + 4 * (size_t)T;
+    Q* vq = (Q*)vs;
+    B* fb = (B*)(vq + 2 * (size_t)T);
+    const unsigned base = smem_u32(vq);
+    const unsigned fb_off = 2u * (unsigned)T * (unsigned)sizeof(Q);
+    const unsigned base_up = cluster_addr(base, rank + 1 == C ? 0 : rank + 1);
+    const unsigned base_dn = cluster_addr(base, rank == 0 ? C - 1 : rank - 1);
     const R2* hop;
     if constexpr (sizeof(R) == 8) hop = (const R2*)p.hop64; else hop = (const R2*)p.hop32;
     for (int sl = tid; sl < T; sl += kThreads)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) fb[a * T + sl] = ldcg2(hop + (size_t)a * N + s0 + sl);
+        for (int a = 0; a < 3; ++a) fb[a * T + sl] = make_bond(ldcg2(hop + (size_t)a * N + s0 + sl));
     cl.sync();
 
-    // the copy held by the owner of site j of the array that starts at base in every CTA
-    auto at = [&](R2* base, int j) -> R2* {
-        const int owner = (int)__umulhi((unsigned)j, p.divT);
-        return cl.map_shared_rank(base + (j - owner * T), owner);
-    };
-    auto bond = [&](int sl, int d, int nbj) -> R2 {  // Htilde_{i, nbr(i, d)}
+    // Htilde_{i, nbr(i, d)} for the set-up of r_0 and r_1 (a few sites only)
+    auto bond = [&](int sl, int d, int nbj) -> R2 {
         const int a = d >> 1;
-        if ((d & 1) == 0) return fb[a * T + sl];
-        R2 h = *at(fb + (size_t)a * T, nbj);
+        if ((d & 1) == 0) return bond_value(fb[a * T + sl]);
+        const int owner = nbj / T;
+        B b;
+        ld_dsm(cluster_addr(base + fb_off + (unsigned)((a * T + nbj - owner * T) * (int)sizeof(B)), owner), b);
+        R2 h = bond_value(b);
         h.y = -h.y;
         return h;
     };
@@ -858,62 +1030,76 @@ __device__ bool cluster_steps2(const Params& p, int rank, typename Cx<R>::T* vs,
                     if (nb[d] == s_loc[k + 1]) c_fma(r1v, h, cv6[k]);
             }
         }
-        vs[sl] = r0o;
-        vs[T + sl] = r0v;
-        vs[2 * T + sl] = r1o;
-        vs[3 * T + sl] = r1v;
+        Q q0, q1;
+        q0.re = c_make<R2>(r0o.x, r0v.x);
+        q0.im = c_make<R2>(r0o.y, r0v.y);
+        q1.re = c_make<R2>(r1o.x, r1v.x);
+        q1.im = c_make<R2>(r1o.y, r1v.y);
+        vq[sl] = q0;
+        vq[T + sl] = q1;
     }
     cl.sync();
 
     for (int m = 1; m <= p.nsteps; ++m) {
-        R2* rd = vs + (size_t)((m & 1) ? 2 : 0) * T;  // [vector][T] of r_m
-        R2* wr = vs + (size_t)((m & 1) ? 0 : 2) * T;  // r_{m-1}, overwritten by r_{m+1}
-        double* prow = p.partial + ((size_t)(m - 1) * C + rank) * kEntries;
+        const int b = m & 1;  // buffer of r_m; the other holds r_{m-1}, overwritten by r_{m+1}
+        const Q* rd = vq + (size_t)b * T;
+        Q* wr = vq + (size_t)(b ^ 1) * T;
+        const unsigned rd_off = (unsigned)b * (unsigned)T * (unsigned)sizeof(Q);
+        GramAcc<R> g;
+        for (int sl0 = tid; sl0 < T; sl0 += U * kThreads) {
+            Q nv[U][6], cur[U], prv[U];
+            B h[U][6];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int sl = sl0 + u * kThreads;
+                if (sl < T) {
+                    const int zl = (int)__umulhi((unsigned)sl, p.divLL);
+                    const int r = sl - zl * LL;
+                    const int y = (int)__umulhi((unsigned)r, p.divL);
+                    const int x = r - y * L;
+                    const int xp = x == L - 1 ? sl - (L - 1) : sl + 1;
+                    const int xm = x == 0 ? sl + (L - 1) : sl - 1;
+                    const int yp = y == L - 1 ? sl - (L - 1) * L : sl + L;
+                    const int ym = y == 0 ? sl + (L - 1) * L : sl - L;
+                    const bool up = zl == P - 1, dn = zl == 0;
+                    const int zp = up ? sl + LL - T : sl + LL;
+                    const int zm = dn ? sl - LL + T : sl - LL;
+                    nv[u][0] = rd[xp];
+                    nv[u][1] = rd[xm];
+                    nv[u][2] = rd[yp];
+                    nv[u][3] = rd[ym];
+                    ld_dsm((up ? base_up : base) + rd_off + (unsigned)zp * (unsigned)sizeof(Q), nv[u][4]);
+                    ld_dsm((dn ? base_dn : base) + rd_off + (unsigned)zm * (unsigned)sizeof(Q), nv[u][5]);
+                    h[u][0] = fb[sl];
+                    h[u][1] = fb[xm];
+                    h[u][2] = fb[T + sl];
+                    h[u][3] = fb[T + ym];
+                    h[u][4] = fb[2 * T + sl];
+                    ld_dsm((dn ? base_dn : base) + fb_off + (unsigned)(2 * T + zm) * (unsigned)sizeof(B), h[u][5]);
+                    cur[u] = rd[sl];
+                    prv[u] = wr[sl];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int sl = sl0 + u * kThreads;
+                if (sl < T) {
+                    Stencil<R> st;
+#pragma unroll
+                    for (int d = 0; d < 6; ++d) st.add(h[u][d], nv[u][d], (d & 1) == 0);
+                    const Q nx = st.next(prv[u]);
+                    wr[sl] = nx;
+                    g.add(cur[u], nx);
+                }
+            }
+        }
+        asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
         R acc[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) acc[e] = (R)0;
-        for (int sl = tid; sl < T; sl += kThreads) {
-            const int i = s0 + sl;
-            int nb[6];
-            site_nbrs(i, L, p.divL, p.divLL, nb);
-            R2 h[6], nv[2][6];
-#pragma unroll
-            for (int d = 0; d < 6; ++d) {
-                h[d] = bond(sl, d, nb[d]);
-                nv[0][d] = *at(rd, nb[d]);
-                nv[1][d] = *at(rd + T, nb[d]);
-            }
-            R2 cur[2], nxt[2];
-#pragma unroll
-            for (int v = 0; v < 2; ++v) {
-                cur[v] = rd[v * T + sl];
-                const R2 pv = wr[v * T + sl];
-                R2 a = c_make<R2>(0, 0);
-#pragma unroll
-                for (int d = 0; d < 6; ++d) c_fma(a, h[d], nv[v][d]);
-                nxt[v] = c_make<R2>(fma((R)2, a.x, -pv.x), fma((R)2, a.y, -pv.y));
-                wr[v * T + sl] = nxt[v];
-            }
-            const R2 a = cur[0], b = cur[1], na = nxt[0], nbv = nxt[1];
-            acc[0] = fma(a.x, a.x, fma(a.y, a.y, acc[0]));
-            acc[1] = fma(b.x, b.x, fma(b.y, b.y, acc[1]));
-            acc[2] = fma(a.x, b.x, fma(a.y, b.y, acc[2]));
-            acc[3] = fma(a.x, b.y, fma(-a.y, b.x, acc[3]));
-            acc[4] = fma(a.x, na.x, fma(a.y, na.y, acc[4]));
-            acc[5] = fma(b.x, nbv.x, fma(b.y, nbv.y, acc[5]));
-            acc[6] = fma(a.x, nbv.x, fma(a.y, nbv.y, acc[6]));
-            acc[7] = fma(a.x, nbv.y, fma(-a.y, nbv.x, acc[7]));
-        }
+        g.out(acc);
         const R s8 = warp_reduce_scatter8(acc, lane);
-        if ((lane & 3) == 0) red[warp][lane >> 2] = (double)s8;
-        __syncthreads();
-        if (tid < 8) {
-            double sum = 0.0;
-#pragma unroll
-            for (int w = 0; w < kWarps; ++w) sum += red[w][tid];
-            prow[tid] = sum;
-        }
-        cl.sync();
+        if ((lane & 3) == 0)
+            ((R*)(p.partial + ((size_t)(m - 1) * C + rank) * kEntries))[warp * 8 + (lane >> 2)] = s8;
+        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
     }
     return true;
 }
@@ -1254,7 +1440,18 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                     X[1] = s_ov1;
                 } else {
                     const double* src = p.partial + (size_t)(item - 1) * p.ncta * kEntries;
-                    if (lane < 8) {
+                    if constexpr (VARIANT == 2) {
+                        // per CTA and warp 8 sums of type R; lane: entry lane & 7, every
+                        // fourth (CTA, warp) slot from lane >> 3
+                        double sum = 0.0;
+                        for (int cw = lane >> 3; cw < p.ncta * kWarps; cw += 4) {
+                            const R* row = (const R*)(src + (size_t)(cw / kWarps) * kEntries);
+                            sum += (double)__ldcg(row + (cw % kWarps) * 8 + (lane & 7));
+                        }
+                        sum += __shfl_xor_sync(0xffffffffu, sum, 8);
+                        sum += __shfl_xor_sync(0xffffffffu, sum, 16);
+                        if (lane < 8) red[warp][lane] = sum;
+                    } else if (lane < 8) {
                         double sum = 0.0;
                         for (int c = 0; c < p.ncta; ++c) sum += __ldcg(src + (size_t)c * kEntries + lane);
                         red[warp][lane] = sum;

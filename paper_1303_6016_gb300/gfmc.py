@@ -30,7 +30,8 @@ RECURSIONS = {"unit_vectors": 0, "proposal": 1}
 EXPORTS = ("gfmc_default_options", "gfmc_create", "gfmc_moments", "gfmc_delta_omega",
            "gfmc_updates", "gfmc_sweep", "gfmc_get_spins", "gfmc_set_state", "gfmc_get_counter",
            "gfmc_set_wait_budget", "gfmc_inject_stall", "gfmc_last_error", "gfmc_destroy",
-           "gfmc_delta_omega_noalloc", "gfmc_run_batch", "gfmc_run_clusters", "gfmc_server_create",
+           "gfmc_delta_omega_noalloc", "gfmc_run_batch", "gfmc_run_clusters", "gfmc_cluster_min_ctas",
+           "gfmc_server_create",
            "gfmc_server_submit",
            "gfmc_server_poll", "gfmc_server_last_error", "gfmc_server_destroy")
 
@@ -91,6 +92,8 @@ def load(path: str = LIB_PATH):
     L.gfmc_run_batch.restype = ctypes.c_int
     L.gfmc_run_clusters.argtypes = L.gfmc_run_batch.argtypes
     L.gfmc_run_clusters.restype = ctypes.c_int
+    L.gfmc_cluster_min_ctas.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.gfmc_cluster_min_ctas.restype = ctypes.c_int
     L.gfmc_server_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(vp)]
     L.gfmc_server_create.restype = ctypes.c_int
     L.gfmc_server_submit.argtypes = [vp, ctypes.c_int, vp, i64, ctypes.POINTER(ctypes.c_uint8), d]
@@ -248,6 +251,16 @@ def run_clusters(chains, n_updates, cluster_ctas, trace=True, stream=None) -> li
     """Chains on the proposal-vector recursion, each on one thread-block
     cluster holding its lattice in shared memory (gfmc_run_clusters)."""
     return run_batch(chains, n_updates, cluster_ctas, trace, stream, _fn="gfmc_run_clusters")
+
+
+def cluster_min_ctas(L: int, M: int, precision: str = "fp32_mixed") -> int:
+    """Smallest cluster size that holds an L^3 lattice with M moments."""
+    lib = load()
+    out = ctypes.c_int(0)
+    st = lib.gfmc_cluster_min_ctas(int(L), int(M), PRECISIONS[precision], ctypes.byref(out))
+    if st != GFMC_OK:
+        raise GfmcError(st, lib.gfmc_last_error(None).decode())
+    return out.value
 
 
 def run_batch(chains, n_updates, team_ctas=None, trace=True, stream=None, _fn="gfmc_run_batch") -> list:

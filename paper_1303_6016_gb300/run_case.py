@@ -26,13 +26,17 @@ def main(argv=None):
     ap.add_argument("--recursion", default="unit_vectors", choices=sorted(gfmc.RECURSIONS))
     ap.add_argument("--team", type=int, default=0,
                     help="run the updates as a one-chain batch on a team of this many CTAs")
+    ap.add_argument("--cluster", type=int, default=0,
+                    help="run the updates on a thread-block cluster of this many CTAs (proposal recursion)")
     a = ap.parse_args(argv)
     build.build()
     sp = inputs.make(a.spins, a.L, seed=0 if a.spins != "vmf" else 2)
     with gfmc.Chain(a.L, sp, M=a.M, beta=a.beta, mu=a.mu, precision=a.precision,
                     num_ctas=a.num_ctas, recursion=a.recursion) as ch:
         t0 = time.perf_counter()
-        if a.team > 0:
+        if a.cluster > 0:
+            out = gfmc.run_clusters([ch], [a.updates], [a.cluster])[0]
+        elif a.team > 0:
             out = gfmc.run_batch([ch], [a.updates], team_ctas=[a.team])[0]
         else:
             out = ch.updates(a.updates)

@@ -51,10 +51,10 @@ def agree_until_tie(a, b, tol, min_k):
 
 
 def test_fp64_clusters_match_oracle_at_every_cluster_size(G):
-    """Every cluster size, with sites split evenly (N = 64, 216, 512), several
-    groups in flight at once; each chain replayed by the oracle."""
-    specs = [(4, 1, 20.0), (4, 2, 10.0), (4, 4, 20.0), (4, 8, 15.0), (4, 16, 20.0),
-             (6, 2, 12.0), (6, 8, 20.0), (8, 16, 20.0), (8, 1, 9.0)]
+    """Every cluster size, slabs of 1 to 4 z-planes per CTA, several groups in
+    flight at once; each chain replayed by the oracle."""
+    specs = [(4, 1, 20.0), (4, 2, 10.0), (4, 4, 20.0), (8, 8, 15.0), (16, 16, 20.0),
+             (6, 2, 12.0), (12, 4, 20.0), (8, 1, 9.0), (16, 4, 12.0)]
     M, n = 64, 40
     chains, sps = [], []
     for c, (L, _, beta) in enumerate(specs):
@@ -96,7 +96,7 @@ def test_clusters_continue_a_chain_and_a_full_sweep_measures(G):
 def test_fp32_clusters_equal_the_chain_alone(G):
     """FP32-mixed chains on clusters of 1 to 16 CTAs against the same chains on
     the single-chain engine."""
-    specs = [(8, 1), (8, 4), (12, 16), (16, 8)]
+    specs = [(8, 1), (8, 4), (12, 4), (16, 8), (16, 16)]
     M, n = 128, 40
     mix, alone = [], []
     for c, (L, _) in enumerate(specs):
@@ -114,7 +114,7 @@ def test_fp32_clusters_equal_the_chain_alone(G):
 def test_full_size_lattice_on_a_cluster_of_16(G):
     """The L=32, M=1024 lattice held by a 16-CTA cluster (2048 sites per CTA),
     FP32-mixed, against the single-chain engine; FP64 L=24 against the oracle
-    for its first updates."""
+    for its first updates (8 CTAs of 3 planes)."""
     L, M, n = 32, 1024, 6
     sp = inputs.uniform_sphere(L, 0)
     with G.Chain(L, sp, M=M, precision="fp32_mixed", seed=1, recursion="proposal") as ch:
@@ -126,7 +126,7 @@ def test_full_size_lattice_on_a_cluster_of_16(G):
     L, M, n = 24, 512, 3
     sp = inputs.uniform_sphere(L, 5)
     with G.Chain(L, sp, M=M, seed=1, recursion="proposal") as ch:
-        out = G.run_clusters([ch], n, [16])[0]
+        out = G.run_clusters([ch], n, [8])[0]
     oracle_replay(L, sp, M, 20.0, 1, 0, out)
 
 
@@ -135,8 +135,10 @@ def test_clusters_reject_bad_requests(G):
     unit = G.Chain(4, inputs.uniform_sphere(4, 0), M=M)
     prop = G.Chain(6, inputs.uniform_sphere(6, 0), M=M, recursion="proposal")
     big = G.Chain(32, inputs.uniform_sphere(32, 0), M=M, recursion="proposal")
+    unit8 = G.Chain(8, inputs.uniform_sphere(8, 0), M=M, recursion="proposal")
     for chains, C in (([unit], [2]),      # unit-vector recursion
-                      ([prop], [16]),     # 16 does not divide 216
+                      ([prop], [16]),     # 16 does not divide L = 6
+                      ([unit8], [16]),    # divides N = 512 but not L = 8: no whole planes
                       ([prop], [3]),      # not a cluster size
                       ([big], [2]),       # FP64 L=32 does not fit in two CTAs' shared memory
                       ([prop, prop], [1, 1])):  # the same chain twice
@@ -144,5 +146,33 @@ def test_clusters_reject_bad_requests(G):
             G.run_clusters(chains, 1, C)
         assert e.value.status == G.GFMC_EINVAL
     assert prop.counter == 0 and big.counter == 0
-    for ch in (unit, prop, big):
+    for ch in (unit, prop, big, unit8):
+        ch.close()
+
+
+def test_smallest_cluster_and_cluster_runner(G):
+    """The smallest cluster that holds a lattice, and the runner that puts every
+    chain on its smallest cluster (FP64 chains replayed by the oracle)."""
+    from paper_1303_6016_gb300 import batch
+    assert G.cluster_min_ctas(8, 1024) == 1
+    assert G.cluster_min_ctas(32, 1024) == 16
+    c24 = G.cluster_min_ctas(24, 1024)
+    assert 24 % c24 == 0 and c24 > 1
+    for args in ((32, 1024, "fp64"), (8, 100), (2, 64)):
+        with pytest.raises(G.GfmcError) as e:
+            G.cluster_min_ctas(*args)
+        assert e.value.status == G.GFMC_EINVAL
+    specs = [(6, 12.0), (8, 20.0), (12, 9.0)]
+    M, n = 64, 30
+    chains, sps = [], []
+    for c, (L, beta) in enumerate(specs):
+        sp = inputs.uniform_sphere(L, 90 + c)
+        sps.append(sp)
+        chains.append(G.Chain(L, sp, M=M, beta=beta, mu=-2.0, seed=5, chain_id=c, recursion="proposal"))
+    runner = batch.ClusterRunner(chains)
+    assert runner.cluster_ctas == [1, 1, 1]
+    outs = runner.run(n, trace=True)
+    for c, (L, beta) in enumerate(specs):
+        oracle_replay(L, sps[c], M, beta, 5, c, outs[c])
+    for ch in chains:
         ch.close()
