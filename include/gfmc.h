@@ -189,7 +189,7 @@ gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_update
  * launches of different groups overlap, and clusters need not all be resident
  * at once.  Results as gfmc_updates would give them (up to the rounding order
  * of the sums); the outputs are as for gfmc_run_batch.  GFMC_EINVAL when a
- * chain's lattice does not fit in the shared memory of its cluster (80 bytes
+ * chain's lattice does not fit in the shared memory of its cluster (56 bytes
  * per site FP32, 112 FP64, N / C sites per CTA, plus a 16 x M byte work area
  * per CTA). */
 gfmc_status gfmc_run_clusters(gfmc_t* chains, int n_chains, const int64_t* n_updates, const int* cluster_ctas,

@@ -729,7 +729,7 @@ gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_update
 // (o, v) and three forward bonds per site) plus the work area of the tail.
 static size_t cluster_lattice_bytes(int L, int C, int precision)
 {
-    const size_t per_site = precision == GFMC_PREC_FP64 ? 2 * 32 + 3 * 16 : 2 * 16 + 3 * 16;
+    const size_t per_site = precision == GFMC_PREC_FP64 ? 2 * 32 + 3 * 16 : 2 * 16 + 3 * 8;
     const size_t T = (size_t)L * L * L / (size_t)C;
     return (per_site * T + 255) & ~(size_t)255;
 }

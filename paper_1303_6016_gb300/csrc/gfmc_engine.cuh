@@ -282,9 +282,11 @@ template <class R> __device__ __forceinline__ R warp_reduce_scatter8(R (&v)[8], 
 }
 
 // Deterministic CTA-wide sum (and max) of one double per thread.
+template <int NT = kThreads>
 __device__ __forceinline__ void block_sum_max(double s, double mx, double* out_s, double* out_m)
 {
-    __shared__ double sh_s[kWarps], sh_m[kWarps];
+    constexpr int NW = NT / 32;
+    __shared__ double sh_s[NW], sh_m[NW];
     for (int o = 16; o > 0; o >>= 1) {
         s += __shfl_xor_sync(0xffffffffu, s, o);
         mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -297,7 +299,7 @@ __device__ __forceinline__ void block_sum_max(double s, double mx, double* out_s
     __syncthreads();
     if (threadIdx.x == 0) {
         double a = 0.0, b = 0.0;
-        for (int w = 0; w < kWarps; ++w) {
+        for (int w = 0; w < NW; ++w) {
             a += sh_s[w];
             b = fmax(b, sh_m[w]);
         }
@@ -796,19 +798,17 @@ __device__ bool team_steps2(const Params& p, int cta, unsigned phase, typename C
 template <class R> struct alignas(4 * sizeof(R)) SOV {
     typename Cx<R>::T re, im;
 };
-// A stored forward bond Htilde_{i, i+e_alpha}: FP32 with each part
-// duplicated, (re, re) and (im, im), the operands of the packed FMAs.
-template <class R> struct BondSm;
-template <> struct alignas(16) BondSm<float> {
-    float2 re2, im2;
+// A stored forward bond Htilde_{i, i+e_alpha} (re, im); the packed FP32 FMAs
+// take each part duplicated in a register pair.
+template <class R> struct alignas(2 * sizeof(R)) BondSm {
+    R re, im;
 };
-template <> struct alignas(16) BondSm<double> {
-    double re, im;
-};
-__device__ __forceinline__ BondSm<float> make_bond(float2 h) { return {make_float2(h.x, h.x), make_float2(h.y, h.y)}; }
+__device__ __forceinline__ BondSm<float> make_bond(float2 h) { return {h.x, h.y}; }
 __device__ __forceinline__ BondSm<double> make_bond(double2 h) { return {h.x, h.y}; }
-__device__ __forceinline__ float2 bond_value(const BondSm<float>& b) { return make_float2(b.re2.x, b.im2.x); }
-__device__ __forceinline__ double2 bond_value(const BondSm<double>& b) { return make_double2(b.re, b.im); }
+template <class R> __device__ __forceinline__ typename Cx<R>::T bond_value(const BondSm<R>& b)
+{
+    return c_make<typename Cx<R>::T>(b.re, b.im);
+}
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -834,8 +834,7 @@ __device__ __forceinline__ void ld_dsm(unsigned a, SOV<double>& q)
 }
 __device__ __forceinline__ void ld_dsm(unsigned a, BondSm<float>& b)
 {
-    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(b.re2.x), "=f"(b.re2.y), "=f"(b.im2.x), "=f"(b.im2.y) : "r"(a));
+    asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(b.re), "=f"(b.im) : "r"(a));
 }
 __device__ __forceinline__ void ld_dsm(unsigned a, BondSm<double>& b)
 {
@@ -851,14 +850,15 @@ template <> struct Stencil<float> {
     float2 P = {0.f, 0.f}, Q = {0.f, 0.f}, Sf = {0.f, 0.f}, Sb = {0.f, 0.f}, Wf = {0.f, 0.f}, Wb = {0.f, 0.f};
     __device__ __forceinline__ void add(const BondSm<float>& b, const SOV<float>& r, bool fwd)
     {
-        P = __ffma2_rn(b.re2, r.re, P);
-        Q = __ffma2_rn(b.re2, r.im, Q);
+        const float2 re2 = make_float2(b.re, b.re), im2 = make_float2(b.im, b.im);
+        P = __ffma2_rn(re2, r.re, P);
+        Q = __ffma2_rn(re2, r.im, Q);
         if (fwd) {
-            Sf = __ffma2_rn(b.im2, r.im, Sf);
-            Wf = __ffma2_rn(b.im2, r.re, Wf);
+            Sf = __ffma2_rn(im2, r.im, Sf);
+            Wf = __ffma2_rn(im2, r.re, Wf);
         } else {
-            Sb = __ffma2_rn(b.im2, r.im, Sb);
-            Wb = __ffma2_rn(b.im2, r.re, Wb);
+            Sb = __ffma2_rn(im2, r.im, Sb);
+            Wb = __ffma2_rn(im2, r.re, Wb);
         }
     }
     // r_{m+1} = 2 Htilde r_m - r_{m-1}
@@ -953,21 +953,21 @@ template <> struct GramAcc<double> {
 // overwrites, writes of step m visible before step m+1 reads).
 // vs: [buffer][T] of SOV, then [3][T] stored forward bonds.
 // Per step each warp writes its 8 Gram sums (type R) to its own slot of the
-// step's partial row, [C][kWarps][8] in the rows of kEntries doubles; the
+// step's partial row, [C][NT / 32][8] in the rows of kEntries doubles; the
 // reduce phase adds them over warps and CTAs in FP64, so a step has no CTA
 // barrier and no FP64 arithmetic.  The cluster barrier is split: a CTA
 // arrives once its stores of r_{m+1} are issued, reduces its warps' sums,
 // then waits.  U sites per thread have all their loads issued before any
 // arithmetic.
-template <class R>
+template <class R, int NT>
 __device__ bool cluster_steps2(const Params& p, int rank, typename Cx<R>::T* vs, const int* s_loc,
-                               const double2* s_c, double (*red)[kEntries])
+                               const double2* s_c)
 {
     namespace cg = cooperative_groups;
     using R2 = typename Cx<R>::T;
     using Q = SOV<R>;
     using B = BondSm<R>;
-    constexpr int U = sizeof(R) == 4 ? 2 : 1;
+    constexpr int U = (sizeof(R) == 4 && NT <= NT) ? 2 : 1;
     cg::cluster_group cl = cg::this_cluster();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int N = p.N, L = p.L, C = p.ncta, LL = L * L, T = N / C, P = L / C;
@@ -980,7 +980,7 @@ __device__ bool cluster_steps2(const Params& p, int rank, typename Cx<R>::T* vs,
     const unsigned base_dn = cluster_addr(base, rank == 0 ? C - 1 : rank - 1);
     const R2* hop;
     if constexpr (sizeof(R) == 8) hop = (const R2*)p.hop64; else hop = (const R2*)p.hop32;
-    for (int sl = tid; sl < T; sl += kThreads)
+    for (int sl = tid; sl < T; sl += NT)
 #pragma unroll
         for (int a = 0; a < 3; ++a) fb[a * T + sl] = make_bond(ldcg2(hop + (size_t)a * N + s0 + sl));
     cl.sync();
@@ -1001,7 +1001,7 @@ __device__ bool cluster_steps2(const Params& p, int rank, typename Cx<R>::T* vs,
     for (int k = 0; k < 6; ++k) cv6[k] = c_make<R2>((R)s_c[k + 1].x, (R)s_c[k + 1].y);
     const int lo = s_loc[0];
 
-    for (int sl = tid; sl < T; sl += kThreads) {
+    for (int sl = tid; sl < T; sl += NT) {
         const int i = s0 + sl;
         int nb[6];
         site_nbrs(i, L, p.divL, p.divLL, nb);
@@ -1046,12 +1046,12 @@ __device__ bool cluster_steps2(const Params& p, int rank, typename Cx<R>::T* vs,
         Q* wr = vq + (size_t)(b ^ 1) * T;
         const unsigned rd_off = (unsigned)b * (unsigned)T * (unsigned)sizeof(Q);
         GramAcc<R> g;
-        for (int sl0 = tid; sl0 < T; sl0 += U * kThreads) {
+        for (int sl0 = tid; sl0 < T; sl0 += U * NT) {
             Q nv[U][6], cur[U], prv[U];
             B h[U][6];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int sl = sl0 + u * kThreads;
+                const int sl = sl0 + u * NT;
                 if (sl < T) {
                     const int zl = (int)__umulhi((unsigned)sl, p.divLL);
                     const int r = sl - zl * LL;
@@ -1082,7 +1082,7 @@ __device__ bool cluster_steps2(const Params& p, int rank, typename Cx<R>::T* vs,
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int sl = sl0 + u * kThreads;
+                const int sl = sl0 + u * NT;
                 if (sl < T) {
                     Stencil<R> st;
 #pragma unroll
@@ -1132,15 +1132,20 @@ template <int VARIANT> __device__ __forceinline__ bool chain_barrier(const Param
 // vectors |o> and |v> = Delta~|o> only: the paper's recursion on the
 // combined vectors o, v, o+v, o+iv (Algorithm 1) reduced by linearity to two
 // recursions and the cross product <o|T_n|v>; single-chain variant only.
-template <class R, int VARIANT, int NV = kVec>
+template <class R, int VARIANT, int NV = kVec, int NT = kThreads>
 __device__ __forceinline__ void run_chain(const Params& p, const int cta, double2* dyn,
                                           typename Cx<R>::T* vec_smem)
 {
     static_assert(NV == kVec || NV == 2, "recursion on 7 unit vectors or on o and v");
     static_assert(VARIANT != 2 || NV == 2, "cluster variant: recursion on o and v");
+    static_assert(NT == kThreads || VARIANT == 2, "only the cluster variant runs other block sizes");
+    static_assert(NT % 32 == 0 && NT >= kThreads, "whole warps, at least the default block");
+    constexpr int NW = NT / 32;
+    // per warp: room for 112 Gram entries; the cluster variant only reduces 8 here
+    constexpr int kRed = VARIANT == 2 ? 8 : kEntries;
     using R2 = typename Cx<R>::T;
-    __shared__ double red[kWarps][kEntries];
-    __shared__ double2 s_mu2[kWarps][2][kPairs];
+    __shared__ double red[NW][kRed];
+    __shared__ double2 s_mu2[NW][2][kPairs];
     __shared__ double2 s_mu1[kPairs];
     __shared__ double2 s_c[kVec];
     __shared__ int s_loc[kVec];
@@ -1283,7 +1288,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 if (tid < 8) {
                     double sum = 0.0;
 #pragma unroll
-                    for (int w = 0; w < kWarps; ++w) sum += red[w][tid];
+                    for (int w = 0; w < NW; ++w) sum += red[w][tid];
                     prow[tid] = sum;
                 }
 #pragma unroll
@@ -1373,7 +1378,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                     if (tid < kEntries) {
                         double sum = 0.0;
     #pragma unroll
-                        for (int w = 0; w < kWarps; ++w) sum += red[w][tid];
+                        for (int w = 0; w < NW; ++w) sum += red[w][tid];
                         prow[tid] = sum;
                     }
                 }
@@ -1384,7 +1389,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 }
             }
         } else if constexpr (VARIANT == 2) {
-            cluster_steps2<R>(p, cta, vec_smem, s_loc, s_c, red);
+            cluster_steps2<R, NT>(p, cta, vec_smem, s_loc, s_c);
         } else if constexpr (NV == 2) {
             if (vec_smem) {
                 if (!team_steps2<R>(p, cta, phase, buf0, buf1, s_loc, s_c, red, SmemVec{})) return;
@@ -1427,7 +1432,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 s_ov1 = o1;
             }
             __syncthreads();
-            const int gw = cta * kWarps + warp, TW = p.ncta * kWarps;
+            const int gw = cta * NW + warp, TW = p.ncta * NW;
             for (int item = gw; item <= p.nsteps; item += TW) {
                 double oo[2], vv[2];
                 double2 X[2];
@@ -1444,9 +1449,9 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                         // per CTA and warp 8 sums of type R; lane: entry lane & 7, every
                         // fourth (CTA, warp) slot from lane >> 3
                         double sum = 0.0;
-                        for (int cw = lane >> 3; cw < p.ncta * kWarps; cw += 4) {
-                            const R* row = (const R*)(src + (size_t)(cw / kWarps) * kEntries);
-                            sum += (double)__ldcg(row + (cw % kWarps) * 8 + (lane & 7));
+                        for (int cw = lane >> 3; cw < p.ncta * NW; cw += 4) {
+                            const R* row = (const R*)(src + (size_t)(cw / NW) * kEntries);
+                            sum += (double)__ldcg(row + (cw % NW) * 8 + (lane & 7));
                         }
                         sum += __shfl_xor_sync(0xffffffffu, sum, 8);
                         sum += __shfl_xor_sync(0xffffffffu, sum, 16);
@@ -1477,7 +1482,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
             }
         } else
         {
-            const int gw = cta * kWarps + warp, TW = p.ncta * kWarps;
+            const int gw = cta * NW + warp, TW = p.ncta * NW;
             for (int item = gw; item <= p.nsteps; item += TW) {
                 if (item == 0) {
                     if (lane < kPairs) {
@@ -1527,12 +1532,12 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
             while ((1 << lg) < M) ++lg;
             for (int V = cta; V < 4; V += p.ncta) {
                 double2* x = dyn;
-                for (int n = tid; n < M; n += kThreads)
+                for (int n = tid; n < M; n += NT)
                     x[__brev((unsigned)n) >> (32 - lg)] = __ldcg(p.fftin + (size_t)V * M + n);
                 __syncthreads();
                 for (int half = 1, lh = 0; half < M; half <<= 1, ++lh) {
                     const int tstride = M >> (lh + 1);
-                    for (int b = tid; b < (M >> 1); b += kThreads) {
+                    for (int b = tid; b < (M >> 1); b += NT) {
                         const int grp = b >> lh, pos = b & (half - 1);
                         const int i0 = (grp << (lh + 1)) + pos, i1 = i0 + half;
                         const double2 w = __ldcg(p.fftw + (size_t)pos * tstride);
@@ -1542,7 +1547,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                     }
                     __syncthreads();
                 }
-                for (int k = tid; k < M; k += kThreads) {
+                for (int k = tid; k < M; k += NT) {
                     const double2 chi = (k & 1) ? dconj(x[M - 1 - (k >> 1)]) : x[k >> 1];
                     const double sc = 2.0 / __ldcg(p.sinth + k);
                     p.gnode[(size_t)V * M + k] = make_double2(-sc * chi.y, sc * chi.x);
@@ -1558,7 +1563,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
             const int k1 = (int)(((long long)(cta + 1) * M) / p.ncta);
             const int kend = min(k1 + 1, M);
             double* sarg = (double*)dyn;
-            for (int k = k0 + tid; k < kend; k += kThreads) {
+            for (int k = k0 + tid; k < kend; k += NT) {
                 const double2 Goo = __ldcg(p.gnode + k), Gvv = __ldcg(p.gnode + (size_t)M + k);
                 const double2 Gp = __ldcg(p.gnode + 2 * (size_t)M + k), Gq = __ldcg(p.gnode + 3 * (size_t)M + k);
                 const double2 Am = dsub(dsub(Gp, Goo), Gvv);  // G_ov + G_vo
@@ -1573,7 +1578,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
             }
             __syncthreads();
             double part = 0.0, mx = 0.0;
-            for (int k = k0 + tid; k < k1; k += kThreads) {
+            for (int k = k0 + tid; k < k1; k += NT) {
                 double inc;
                 if (k == M - 1) {
                     inc = sarg[k - k0];
@@ -1586,7 +1591,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 mx = fmax(mx, fabs(inc));
             }
             double ps, pm;
-            block_sum_max(part, mx, &ps, &pm);
+            block_sum_max<NT>(part, mx, &ps, &pm);
             if (tid == 0) {
                 p.qpart[2 * cta] = ps;
                 p.qpart[2 * cta + 1] = pm;
@@ -1645,7 +1650,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
         // ---- magnetisation after each completed sweep ----
         if ((upd + 1ull) % (unsigned long long)N == 0ull) {
             double sx = 0.0, sy = 0.0, sz = 0.0;
-            for (int si = s0 + tid; si < s1; si += kThreads) {
+            for (int si = s0 + tid; si < s1; si += NT) {
                 const double th = __ldcg(p.spins + 2 * si), ph = __ldcg(p.spins + 2 * si + 1);
                 double st, ct, sp, cp;
                 sincos(th, &st, &ct);
@@ -1655,11 +1660,11 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 sz += ct;
             }
             double a0, b0;
-            block_sum_max(sx, 0.0, &a0, &b0);
+            block_sum_max<NT>(sx, 0.0, &a0, &b0);
             if (tid == 0) p.magpart[3 * cta] = a0;
-            block_sum_max(sy, 0.0, &a0, &b0);
+            block_sum_max<NT>(sy, 0.0, &a0, &b0);
             if (tid == 0) p.magpart[3 * cta + 1] = a0;
-            block_sum_max(sz, 0.0, &a0, &b0);
+            block_sum_max<NT>(sz, 0.0, &a0, &b0);
             if (tid == 0) p.magpart[3 * cta + 2] = a0;
             if (!chain_barrier<VARIANT>(p, 6)) return;
             if (cta == 0 && tid == 0) {
@@ -1715,8 +1720,14 @@ __global__ void __launch_bounds__(kThreads, 1) gfmc_team_engine(const TeamJob* _
 // A batch of chains, one thread-block cluster per chain (cluster size C = the
 // chains' p.ncta), all on the recursion of the proposal's vectors; the
 // dynamic shared memory holds [vector area of vec_bytes][work area].
+// Threads per CTA of the cluster engine: FP32 512 (one site per thread per
+// pass, twice the warps of the other engines to hide shared-memory latency),
+// FP64 256.
+template <class R> constexpr int cluster_threads() { return sizeof(R) == 4 ? 2 * kThreads : kThreads; }
+
 template <class R>
-__global__ void __launch_bounds__(kThreads, 1) gfmc_cluster_engine(const TeamJob* __restrict__ jobs, int vec_bytes)
+__global__ void __launch_bounds__(cluster_threads<R>(), 1) gfmc_cluster_engine(const TeamJob* __restrict__ jobs,
+                                                                                int vec_bytes)
 {
     extern __shared__ double2 dyn_all[];
     __shared__ Params sp;
@@ -1727,7 +1738,7 @@ __global__ void __launch_bounds__(kThreads, 1) gfmc_cluster_engine(const TeamJob
     if (threadIdx.x == 0) sp = jobs[job].p;
     __syncthreads();
     using R2 = typename Cx<R>::T;
-    run_chain<R, 2, 2>(sp, rank, dyn_all + vec_bytes / (int)sizeof(double2), (R2*)dyn_all);
+    run_chain<R, 2, 2, cluster_threads<R>()>(sp, rank, dyn_all + vec_bytes / (int)sizeof(double2), (R2*)dyn_all);
 }
 
 }  // namespace gfmc

@@ -73,7 +73,7 @@ cudaError_t launch_cluster_f32(const TeamJob* d_jobs, int njobs, int C, int vec_
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(C * njobs));
-    cfg.blockDim = dim3(kThreads);
+    cfg.blockDim = dim3(cluster_threads<float>());
     cfg.dynamicSmemBytes = (size_t)smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -92,7 +92,7 @@ cudaError_t cluster_max_active_f32(int C, int smem, int* out)
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)C);
-    cfg.blockDim = dim3(kThreads);
+    cfg.blockDim = dim3(cluster_threads<float>());
     cfg.dynamicSmemBytes = (size_t)smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
