@@ -439,6 +439,19 @@ __device__ __forceinline__ void gram_chunk_reduce(const R2 (&rc)[kVec], const R2
     if (lane < 28) dst[28 * C + lane] = (double)s;
 }
 
+// As gram_chunk_reduce, with the chunk's warp sums left in type R (no
+// conversion on the step's critical path).
+template <class R, class R2, int C>
+__device__ __forceinline__ void gram_chunk_reduce_raw(const R2 (&rc)[kVec], const R2 (&rn)[kVec], int lane, R* dst)
+{
+    R vals[32];
+    gram_fill<R, R2, C, 0>(rc, rn, vals);
+#pragma unroll
+    for (int qq = 28; qq < 32; ++qq) vals[qq] = (R)0;
+    const R s = warp_reduce_scatter32(vals, lane);
+    if (lane < 28) dst[28 * C + lane] = s;
+}
+
 // As gram_chunk_reduce, but adding the chunk's warp sums to dst.
 template <class R, class R2, int C>
 __device__ __forceinline__ void gram_chunk_accumulate(const R2 (&rc)[kVec], const R2 (&rn)[kVec], int lane,
@@ -1250,18 +1263,37 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
             publish(p, cta, phase + 1);
 
             // ---- steps: two recursions and the 8 real products of the doubling ----
+            // Each warp leaves its 8 sums of step m (type R) in w8[m & 1]; they are added
+            // over the warps in FP64 during step m+1, while its neighbour loads are in
+            // flight (the wait at the top of each step orders the two).
+            __shared__ R w8[2][NW][8];
+            auto flush8 = [&](int m) {
+                if (tid < 8) {
+                    double sum = 0.0;
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) sum += (double)w8[m & 1][w][tid];
+                    p.partial[((size_t)(m - 1) * p.ncta + cta) * kEntries + tid] = sum;
+                }
+            };
             for (int m = 1; m <= p.nsteps; ++m) {
                 if (!wait_neighbours(p, cta, phase + (unsigned)m, 100 + m)) return;
                 const R2* rd = (m & 1) ? buf1 : buf0;
                 R2* wr = (m & 1) ? buf0 : buf1;
+                R2 nv[2][6];
+                if (active) {
+#pragma unroll
+                    for (int v = 0; v < 2; ++v)
+#pragma unroll
+                        for (int d = 0; d < 6; ++d) nv[v][d] = ldcg2(rd + (size_t)v * N + nb[d]);
+                }
+                if (m >= 2) flush8(m - 1);
                 R2 nxt[2];
                 if (active) {
 #pragma unroll
                     for (int v = 0; v < 2; ++v) {
-                        const R2* cv = rd + (size_t)v * N;
                         R2 acc = c_make<R2>(0, 0);
 #pragma unroll
-                        for (int d = 0; d < 6; ++d) c_fma(acc, h[d], ldcg2(cv + nb[d]));
+                        for (int d = 0; d < 6; ++d) c_fma(acc, h[d], nv[v][d]);
                         nxt[v] = c_make<R2>(fma((R)2, acc.x, -prv[v].x), fma((R)2, acc.y, -prv[v].y));
                         if (m < p.nsteps) stcg2(wr + (size_t)v * N + i, nxt[v]);
                     }
@@ -1269,7 +1301,6 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                     nxt[0] = c_make<R2>(0, 0);
                     nxt[1] = c_make<R2>(0, 0);
                 }
-                double* prow = p.partial + ((size_t)(m - 1) * p.ncta + cta) * kEntries;
                 publish(p, cta, phase + (unsigned)m + 1u);
                 // |r_m^o|^2, |r_m^v|^2, <r_m^o|r_m^v>, Re<r_m^o|r_m+1^o>, Re<r_m^v|r_m+1^v>, <r_m^o|r_m+1^v>
                 const R2 a = cur[0], b = cur[1], na = nxt[0], nbv = nxt[1];
@@ -1283,20 +1314,15 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 v8[6] = fma(a.x, nbv.x, a.y * nbv.y);
                 v8[7] = fma(a.x, nbv.y, -(a.y * nbv.x));
                 const R s8 = warp_reduce_scatter8(v8, lane);
-                if ((lane & 3) == 0) red[warp][lane >> 2] = (double)s8;
-                __syncthreads();
-                if (tid < 8) {
-                    double sum = 0.0;
-#pragma unroll
-                    for (int w = 0; w < NW; ++w) sum += red[w][tid];
-                    prow[tid] = sum;
-                }
+                if ((lane & 3) == 0) w8[m & 1][warp][lane >> 2] = s8;
 #pragma unroll
                 for (int v = 0; v < 2; ++v) {
                     prv[v] = cur[v];
                     cur[v] = nxt[v];
                 }
             }
+            __syncthreads();
+            flush8(p.nsteps);
         } else if constexpr (VARIANT == 0) {
             // ---- phase 0: r_0 = e_{l_v} and r_1 = Htilde e_{l_v} of the own site, kept in registers;
             //      only r_1 is published (no CTA ever reads another CTA's r_0) ----
@@ -1318,19 +1344,33 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
             publish(p, cta, phase + 1);
 
             // ---- steps m = 1 .. M/2-1: r_{m+1} = 2 Htilde r_m - r_{m-1} and the Gram sums ----
+            // FP32: each warp leaves its 112 Gram sums of step m in g32[m & 1]; they are added
+            // over the warps in FP64 during step m+1 while its neighbour loads are in flight.
+            __shared__ float g32[sizeof(R) == 4 ? 2 : 1][sizeof(R) == 4 ? NW : 1][kEntries];
+            auto flush112 = [&](int m) {
+                if (tid < kEntries) {
+                    double sum = 0.0;
+    #pragma unroll
+                    for (int w = 0; w < NW; ++w) sum += (double)g32[m & 1][w][tid];
+                    p.partial[((size_t)(m - 1) * p.ncta + cta) * kEntries + tid] = sum;
+                }
+            };
             for (int m = 1; m <= p.nsteps; ++m) {
                 if (!wait_neighbours(p, cta, phase + (unsigned)m, 100 + m)) return;
                 const R2* rd = (m & 1) ? buf1 : buf0;  // r_m of every site
                 R2* wr = (m & 1) ? buf0 : buf1;        // receives r_{m+1}; held r_{m-1}
                 R2 nxt[kVec];
-                if (active) {
-                    if constexpr (sizeof(R) == 4) {
-                        // issue all 42 neighbour loads before the first use (latency-bound path)
-                        R2 nv[kVec][6];
+                if constexpr (sizeof(R) == 4) {
+                    // issue all 42 neighbour loads before the first use (latency-bound path)
+                    R2 nv[kVec][6];
+                    if (active) {
     #pragma unroll
                         for (int v = 0; v < kVec; ++v)
     #pragma unroll
                             for (int d = 0; d < 6; ++d) nv[v][d] = ldcg2(rd + (size_t)v * N + nb[d]);
+                    }
+                    if (m >= 2) flush112(m - 1);
+                    if (active) {
     #pragma unroll
                         for (int v = 0; v < kVec; ++v) {
                             R2 acc = c_make<R2>(0, 0);
@@ -1341,14 +1381,17 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                         }
                     } else {
     #pragma unroll
-                        for (int v = 0; v < kVec; ++v) {
-                            const R2* cv = rd + (size_t)v * N;
-                            R2 acc = c_make<R2>(0, 0);
+                        for (int v = 0; v < kVec; ++v) nxt[v] = c_make<R2>(0, 0);
+                    }
+                } else if (active) {
     #pragma unroll
-                            for (int d = 0; d < 6; ++d) c_fma(acc, h[d], ldcg2(cv + nb[d]));
-                            nxt[v] = c_make<R2>(fma((R)2, acc.x, -prv[v].x), fma((R)2, acc.y, -prv[v].y));
-                            if (m < p.nsteps) stcg2(wr + (size_t)v * N + i, nxt[v]);
-                        }
+                    for (int v = 0; v < kVec; ++v) {
+                        const R2* cv = rd + (size_t)v * N;
+                        R2 acc = c_make<R2>(0, 0);
+    #pragma unroll
+                        for (int d = 0; d < 6; ++d) c_fma(acc, h[d], ldcg2(cv + nb[d]));
+                        nxt[v] = c_make<R2>(fma((R)2, acc.x, -prv[v].x), fma((R)2, acc.y, -prv[v].y));
+                        if (m < p.nsteps) stcg2(wr + (size_t)v * N + i, nxt[v]);
                     }
                 } else {
     #pragma unroll
@@ -1370,23 +1413,20 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 } else {
                     // Gram entries e = 0..55: e < 28 -> conj(r_m^j) r_m^k, else conj(r_m^j) r_{m+1}^k,
                     // (j, k) the upper pair e mod 28; 4 chunks of 14 complex values, warp butterfly.
-                    gram_chunk_reduce<R, R2, 0>(cur, nxt, lane, red[warp]);
-                    gram_chunk_reduce<R, R2, 1>(cur, nxt, lane, red[warp]);
-                    gram_chunk_reduce<R, R2, 2>(cur, nxt, lane, red[warp]);
-                    gram_chunk_reduce<R, R2, 3>(cur, nxt, lane, red[warp]);
-                    __syncthreads();
-                    if (tid < kEntries) {
-                        double sum = 0.0;
-    #pragma unroll
-                        for (int w = 0; w < NW; ++w) sum += red[w][tid];
-                        prow[tid] = sum;
-                    }
+                    gram_chunk_reduce_raw<R, R2, 0>(cur, nxt, lane, g32[m & 1][warp]);
+                    gram_chunk_reduce_raw<R, R2, 1>(cur, nxt, lane, g32[m & 1][warp]);
+                    gram_chunk_reduce_raw<R, R2, 2>(cur, nxt, lane, g32[m & 1][warp]);
+                    gram_chunk_reduce_raw<R, R2, 3>(cur, nxt, lane, g32[m & 1][warp]);
                 }
     #pragma unroll
                 for (int v = 0; v < kVec; ++v) {
                     prv[v] = cur[v];
                     cur[v] = nxt[v];
                 }
+            }
+            if constexpr (sizeof(R) == 4) {
+                __syncthreads();
+                flush112(p.nsteps);
             }
         } else if constexpr (VARIANT == 2) {
             cluster_steps2<R, NT>(p, cta, vec_smem, s_loc, s_c);
