@@ -190,8 +190,8 @@ gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_update
  * at once.  Results as gfmc_updates would give them (up to the rounding order
  * of the sums); the outputs are as for gfmc_run_batch.  GFMC_EINVAL when a
  * chain's lattice does not fit in the shared memory of its cluster (56 bytes
- * per site FP32, 112 FP64, N / C sites per CTA, plus a 16 x M byte work area
- * per CTA). */
+ * per site FP32, 112 FP64, N / C sites per CTA; the tail reuses that space as
+ * its 16 x M byte work area). */
 gfmc_status gfmc_run_clusters(gfmc_t* chains, int n_chains, const int64_t* n_updates, const int* cluster_ctas,
                               uint64_t* n_accepted, uint8_t** decisions, double** d_omega_trace,
                               double** magnetization, int64_t* n_mag, void* stream);

@@ -733,12 +733,17 @@ static size_t cluster_lattice_bytes(int L, int C, int precision)
     const size_t T = (size_t)L * L * L / (size_t)C;
     return (per_site * T + 255) & ~(size_t)255;
 }
-static constexpr int kClusterStaticReserve = 12 * 1024;  // the engine's static shared memory, rounded up
-
-static bool cluster_fits(int L, int M, int C, int precision, int dev_smem)
+// Dynamic shared memory of a CTA: the slab during the recursion, reused as the
+// tail's work area (16 M bytes) afterwards.
+static size_t cluster_dyn_bytes(int L, int M, int C, int precision)
 {
-    return L % C == 0 && cluster_lattice_bytes(L, C, precision) + (size_t)M * sizeof(double2) + kClusterStaticReserve <=
-                             (size_t)dev_smem;
+    return std::max(cluster_lattice_bytes(L, C, precision), (size_t)M * sizeof(double2));
+}
+
+// dev_smem: the device's opt-in shared memory per block; static: the engine's own
+static bool cluster_fits(int L, int M, int C, int precision, int dev_smem, int static_smem)
+{
+    return L % C == 0 && cluster_dyn_bytes(L, M, C, precision) + (size_t)static_smem <= (size_t)dev_smem;
 }
 
 gfmc_status gfmc_cluster_min_ctas(int L, int M, int precision, int* cluster_ctas)
@@ -747,13 +752,14 @@ gfmc_status gfmc_cluster_min_ctas(int L, int M, int precision, int* cluster_ctas
         (precision != GFMC_PREC_FP64 && precision != GFMC_PREC_FP32_MIXED))
         return fail(nullptr, GFMC_EINVAL, "need 3 <= L <= %d, M a power of two >= 16, a precision and an output",
                     gfmc::kMaxL);
-    int dev = 0, dev_smem = 0;
+    int dev = 0, dev_smem = 0, static_smem = 0;
     cudaError_t e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
-        (e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+        (e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess ||
+        (e = gfmc::cluster_static_smem(precision, &static_smem)) != cudaSuccess)
         return cuda_fail(nullptr, e, "querying shared memory");
     for (int C = 1; C <= 16; C *= 2)
-        if (cluster_fits(L, M, C, precision, dev_smem)) {
+        if (cluster_fits(L, M, C, precision, dev_smem, static_smem)) {
             *cluster_ctas = C;
             return GFMC_OK;
         }
@@ -788,6 +794,10 @@ gfmc_status gfmc_run_clusters(gfmc_t* chains, int n_chains, const int64_t* n_upd
     if ((e = cudaSetDevice(dev)) != cudaSuccess) return cuda_fail(nullptr, e, "cudaSetDevice");
     if ((e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
         return cuda_fail(nullptr, e, "querying shared memory");
+    int static_smem[2] = {0, 0};
+    if ((e = gfmc::cluster_static_smem(GFMC_PREC_FP64, &static_smem[0])) != cudaSuccess ||
+        (e = gfmc::cluster_static_smem(GFMC_PREC_FP32_MIXED, &static_smem[1])) != cudaSuccess)
+        return cuda_fail(nullptr, e, "querying shared memory");
     cudaStream_t s = (cudaStream_t)stream;
     // groups of chains with the same precision and cluster size: one launch each
     struct Group {
@@ -804,11 +814,12 @@ gfmc_status gfmc_run_clusters(gfmc_t* chains, int n_chains, const int64_t* n_upd
         const int T = h->N / C;
         if ((unsigned long long)h->N * (unsigned long long)T >= (1ull << 32))
             return fail(nullptr, GFMC_EINVAL, "chain %d: %d sites per CTA are too many for a cluster", c, T);
-        const size_t vb = cluster_lattice_bytes(h->L, C, h->precision);
-        const int work = h->M * (int)sizeof(double2);
-        if (!cluster_fits(h->L, h->M, C, h->precision, dev_smem))
-            return fail(nullptr, GFMC_EINVAL, "chain %d: %zu B of lattice and %d B of work area per CTA exceed the "
-                        "%d B of shared memory; use a larger cluster", c, vb, work, dev_smem);
+        const size_t vb = cluster_dyn_bytes(h->L, h->M, C, h->precision);
+        const int work = 0;
+        const int st_smem = static_smem[h->precision == GFMC_PREC_FP64 ? 0 : 1];
+        if (!cluster_fits(h->L, h->M, C, h->precision, dev_smem, st_smem))
+            return fail(nullptr, GFMC_EINVAL, "chain %d: %zu B of lattice per CTA (and %d B of the engine's own) exceed "
+                        "the %d B of shared memory; use a larger cluster", c, vb, st_smem, dev_smem);
         Group* g = nullptr;
         for (auto& x : groups)
             if (x.prec == h->precision && x.C == C) g = &x;
@@ -845,6 +856,8 @@ gfmc_status gfmc_run_clusters(gfmc_t* chains, int n_chains, const int64_t* n_upd
             (e = cudaMemsetAsync(P.n_mag, 0, sizeof(long long), s)) != cudaSuccess)
             return cuda_fail(nullptr, e, "clearing control words");
     }
+    // largest clusters first: they are the hardest to place and, per chain, the longest
+    std::stable_sort(groups.begin(), groups.end(), [](const Group& a, const Group& b) { return a.C > b.C; });
     for (const auto& g : groups) {
         int active = 0;
         const int smem = (int)g.vec_bytes + g.work;

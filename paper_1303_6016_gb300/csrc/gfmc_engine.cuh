@@ -1758,8 +1758,11 @@ __global__ void __launch_bounds__(kThreads, 1) gfmc_team_engine(const TeamJob* _
 }
 
 // A batch of chains, one thread-block cluster per chain (cluster size C = the
-// chains' p.ncta), all on the recursion of the proposal's vectors; the
-// dynamic shared memory holds [vector area of vec_bytes][work area].
+// chains' p.ncta), all on the recursion of the proposal's vectors.  The
+// dynamic shared memory holds the CTA's slab of the lattice during the
+// recursion and is the work area of the tail (FFT, phases) afterwards: each
+// update sets up its vectors and reloads its bonds before its first step, and
+// the last cluster barrier of the steps ends every read of another CTA's slab.
 // Threads per CTA of the cluster engine: FP32 512 (one site per thread per
 // pass, twice the warps of the other engines to hide shared-memory latency),
 // FP64 256.
@@ -1778,7 +1781,7 @@ __global__ void __launch_bounds__(cluster_threads<R>(), 1) gfmc_cluster_engine(c
     if (threadIdx.x == 0) sp = jobs[job].p;
     __syncthreads();
     using R2 = typename Cx<R>::T;
-    run_chain<R, 2, 2, cluster_threads<R>()>(sp, rank, dyn_all + vec_bytes / (int)sizeof(double2), (R2*)dyn_all);
+    run_chain<R, 2, 2, cluster_threads<R>()>(sp, rank, dyn_all, (R2*)dyn_all);
 }
 
 }  // namespace gfmc

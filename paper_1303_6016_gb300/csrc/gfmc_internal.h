@@ -122,6 +122,8 @@ cudaError_t launch_server(const ServerArgs& a, int grid, int smem, cudaStream_t 
 cudaError_t launch_cluster_f64(const TeamJob* d_jobs, int njobs, int C, int vec_bytes, int smem, cudaStream_t s);
 cudaError_t launch_cluster_f32(const TeamJob* d_jobs, int njobs, int C, int vec_bytes, int smem, cudaStream_t s);
 cudaError_t cluster_max_active(int precision, int C, int smem, int* out);
+// static shared memory of the cluster engine of a precision (bytes)
+cudaError_t cluster_static_smem(int precision, int* out);
 cudaError_t server_max_ctas(int smem, int* out);
 int engine_smem_bytes(int M);
 cudaError_t engine_max_ctas(int precision, int M, int* out);

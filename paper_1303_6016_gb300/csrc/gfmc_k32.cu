@@ -86,6 +86,14 @@ cudaError_t launch_cluster_f32(const TeamJob* d_jobs, int njobs, int C, int vec_
     return cudaLaunchKernelEx(&cfg, gfmc_cluster_engine<float>, d_jobs, vec_bytes);
 }
 
+cudaError_t cluster_static_smem_f32(int* out)
+{
+    cudaFuncAttributes a;
+    const cudaError_t e = cudaFuncGetAttributes(&a, gfmc_cluster_engine<float>);
+    if (e == cudaSuccess) *out = (int)a.sharedSizeBytes;
+    return e;
+}
+
 cudaError_t cluster_max_active_f32(int C, int smem, int* out)
 {
     cudaError_t e = cluster_config_f32(C, smem);

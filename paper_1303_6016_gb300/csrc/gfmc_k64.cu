@@ -85,6 +85,14 @@ cudaError_t launch_cluster_f64(const TeamJob* d_jobs, int njobs, int C, int vec_
     return cudaLaunchKernelEx(&cfg, gfmc_cluster_engine<double>, d_jobs, vec_bytes);
 }
 
+cudaError_t cluster_static_smem_f64(int* out)
+{
+    cudaFuncAttributes a;
+    const cudaError_t e = cudaFuncGetAttributes(&a, gfmc_cluster_engine<double>);
+    if (e == cudaSuccess) *out = (int)a.sharedSizeBytes;
+    return e;
+}
+
 cudaError_t cluster_max_active_f64(int C, int smem, int* out)
 {
     cudaError_t e = cluster_config_f64(C, smem);

@@ -41,6 +41,12 @@ cudaError_t cluster_max_active(int precision, int C, int smem, int* out)
 {
     return precision == 0 ? cluster_max_active_f64(C, smem, out) : cluster_max_active_f32(C, smem, out);
 }
+cudaError_t cluster_static_smem_f64(int* out);
+cudaError_t cluster_static_smem_f32(int* out);
+cudaError_t cluster_static_smem(int precision, int* out)
+{
+    return precision == 0 ? cluster_static_smem_f64(out) : cluster_static_smem_f32(out);
+}
 
 cudaError_t engine_max_ctas(int precision, int M, int* out)
 {

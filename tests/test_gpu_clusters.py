@@ -111,17 +111,19 @@ def test_fp32_clusters_equal_the_chain_alone(G):
         ch.close()
 
 
-def test_full_size_lattice_on_a_cluster_of_16(G):
-    """The L=32, M=1024 lattice held by a 16-CTA cluster (2048 sites per CTA),
+def test_full_size_lattice_on_clusters_of_8_and_16(G):
+    """The L=32, M=1024 lattice held by a 16-CTA cluster (2048 sites per CTA)
+    and by an 8-CTA cluster (4096 sites, the shared memory nearly full),
     FP32-mixed, against the single-chain engine; FP64 L=24 against the oracle
     for its first updates (8 CTAs of 3 planes)."""
     L, M, n = 32, 1024, 6
     sp = inputs.uniform_sphere(L, 0)
     with G.Chain(L, sp, M=M, precision="fp32_mixed", seed=1, recursion="proposal") as ch:
         alone = ch.updates(n)
-    with G.Chain(L, sp, M=M, precision="fp32_mixed", seed=1, recursion="proposal") as ch:
-        out = G.run_clusters([ch], n, [16])[0]
-    agree_until_tie(out, alone, 1e-4, 3)
+    for C in (16, 8):
+        with G.Chain(L, sp, M=M, precision="fp32_mixed", seed=1, recursion="proposal") as ch:
+            out = G.run_clusters([ch], n, [C])[0]
+        agree_until_tie(out, alone, 1e-4, 3)
 
     L, M, n = 24, 512, 3
     sp = inputs.uniform_sphere(L, 5)
@@ -155,10 +157,11 @@ def test_smallest_cluster_and_cluster_runner(G):
     chain on its smallest cluster (FP64 chains replayed by the oracle)."""
     from paper_1303_6016_gb300 import batch
     assert G.cluster_min_ctas(8, 1024) == 1
-    assert G.cluster_min_ctas(32, 1024) == 16
+    assert G.cluster_min_ctas(32, 1024) == 8   # 4096 sites x 56 B per CTA
     c24 = G.cluster_min_ctas(24, 1024)
     assert 24 % c24 == 0 and c24 > 1
-    for args in ((32, 1024, "fp64"), (8, 100), (2, 64)):
+    assert G.cluster_min_ctas(32, 1024, "fp64") == 16  # 2048 sites x 112 B per CTA
+    for args in ((64, 1024), (8, 100), (2, 64)):
         with pytest.raises(G.GfmcError) as e:
             G.cluster_min_ctas(*args)
         assert e.value.status == G.GFMC_EINVAL
