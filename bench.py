@@ -36,22 +36,29 @@ if ROOT not in sys.path:
 METRIC = "spin updates/s at L=32,M=1024 (FP64 vs FP32-mixed); stencil GB/s; p99 sweep latency"
 UNIT = "spin updates/s"
 
-# Algorithmic work of one site in one fused stencil step (7 vectors):
+# Algorithmic work of one site in one fused stencil step, recursion on the 7
+# unit vectors:
 #   stencil  7 x (6 complex MACs + 2r - r_prev)      = 7 x (6 x 8 + 4)   = 364 flop
 #   Gram     28 <r_m|r_m> (7 real diagonal) + 28 <r_m|r_m+1>
 #            = 7 x 3 + 21 x 6 + 28 x 6                                     = 315 flop
 #   sums     112 real partial products added once                           = 112 flop
+# and on the proposal's two vectors o, v: 2 x 52 stencil + 8 real products of
+# 3 flop + 8 sums = 136 flop.
 FLOP_PER_SITE_STEP = 364 + 315 + 112
-# Bytes of one site in one step: read r_m and r_{m-1}, write r_{m+1} for 7
-# vectors (21 complex values) plus the site's bond row (3 complex values).
-def bytes_per_site_step(real_bytes: int) -> int:
-    return 21 * 2 * real_bytes + 3 * 2 * real_bytes
+FLOP_PER_SITE_STEP_PROPOSAL = 2 * 52 + 8 * 3 + 8
 
 
-def update_work(L: int, M: int, real_bytes: int):
+# Bytes of one site in one step: read r_m and r_{m-1}, write r_{m+1} for each
+# of the nv vectors (3 nv complex values) plus the site's bond row (3 complex).
+def bytes_per_site_step(real_bytes: int, nv: int = 7) -> int:
+    return 3 * nv * 2 * real_bytes + 3 * 2 * real_bytes
+
+
+def update_work(L: int, M: int, real_bytes: int, nv: int = 7):
     N = L ** 3
     steps = M // 2 - 1
-    return steps * N * FLOP_PER_SITE_STEP, steps * N * bytes_per_site_step(real_bytes)
+    flop = FLOP_PER_SITE_STEP if nv == 7 else FLOP_PER_SITE_STEP_PROPOSAL
+    return steps * N * flop, steps * N * bytes_per_site_step(real_bytes, nv)
 
 
 # DRAM bytes per update of the engine kernels from one ncu capture each
@@ -266,7 +273,8 @@ def run_batching(stream, steps, warmup, updates, flush, recursion="unit_vectors"
         for i, t in zip(w, tc):
             teams.setdefault(int(Ls[i]), set()).add(int(t))
     n = len(chains)
-    _, bytes_u = zip(*[update_work(int(L), 1024, 4) for L in Ls])
+    nv = 2 if recursion == "proposal" else 7
+    _, bytes_u = zip(*[update_work(int(L), 1024, 4, nv) for L in Ls])
     for ch in chains:
         ch.close()
     return {"value": n * updates * steps / (total / 1000.0), "unit": UNIT, "chains": n,

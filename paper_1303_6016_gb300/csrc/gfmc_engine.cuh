@@ -466,33 +466,83 @@ __device__ __forceinline__ void gram_chunk_accumulate(const R2 (&rc)[kVec], cons
 }
 
 
-// FP64 Gram sums of one CTA from shared memory: thread (entry e, group g)
-// accumulates conj(x_j) y_k over the sites s = g, g+4, ... of the tile with
-// fused multiply-adds only; the four groups are added in order.  sr holds
-// r_m of vector v at sr[v*kStage + s] and r_{m+1} at sr[(7+v)*kStage + s].
+// FP64 Gram sums of one CTA from shared memory in kGramUnits = 49 work units
+// of four fused multiply-adds per site: units 0..20 are the off-diagonal pairs
+// j < k of <r_m|r_m>, 21..41 those of <r_m|r_{m+1}>, 42..48 the diagonal j = k
+// of both blocks (real parts only: the diagonal sums are real).  Every unit
+// forms two real inner products Re<x|y> and Re<x|y'> over its rows (for an
+// off-diagonal pair y' = -i y, since Im conj(x) y = Re conj(x) (-i y); for a
+// diagonal unit y = x and y' = r_{m+1}^j), so all 49 units run one
+// instruction stream.  kGramGroups groups of 49 threads split the sites
+// (s = g, g + kGramGroups, ...) and the groups are added in order.  sr rows
+// (stride kStage): v -> r_m^v, 7+v -> r_{m+1}^v, 14+v -> -i r_m^v,
+// 21+v -> -i r_{m+1}^v.  out[kEntries] as the per-CTA partial row: entry e <
+// 28 at 2e, 2e+1 = conj(r_m^j) r_m^k summed; e >= 28 the same for r_{m+1}^k.
+constexpr int kGramUnits = 49;
+constexpr int kGramGroups = 5;
+
+__device__ __forceinline__ double2 minus_i(double2 z)
+{
+    // -i z = (Im z, -Re z); the sign flip is a bit operation
+    return make_double2(z.y, __hiloint2double(__double2hiint(z.x) ^ 0x80000000, __double2loint(z.x)));
+}
+
 __device__ __forceinline__ void gram_smem_f64(const double2* sr, int T, double* gsum, double* out)
 {
     const int tid = threadIdx.x;
-    if (tid < 4 * 56) {
-        const int e = tid % 56, g = tid / 56;
-        const int pp = e % kPairs;
-        const int j = pair_j(pp), k = pair_k(pp);
-        const double2* xs = sr + j * kStage;
-        const double2* ys = sr + (e < kPairs ? k : kVec + k) * kStage;
+    if (tid < kGramUnits * kGramGroups) {
+        const int u = tid % kGramUnits, g = tid / kGramUnits;
+        int rx, ry, ry2, ere, eim;
+        bool diag = false;
+        if (u < 42) {
+            // off-diagonal pair q of block b, row-major over j < k
+            const int b = u / 21;
+            int q = u % 21, j = 0;
+            while (q >= 6 - j) {
+                q -= 6 - j;
+                ++j;
+            }
+            const int k = j + 1 + q;
+            rx = j;
+            ry = b * kVec + k;
+            ry2 = 2 * kVec + b * kVec + k;
+            ere = 56 * b + 2 * pair_of(j, k);
+            eim = ere + 1;
+        } else {
+            const int j = u - 42;
+            diag = true;
+            rx = j;
+            ry = j;
+            ry2 = kVec + j;
+            ere = 2 * pair_of(j, j);
+            eim = 56 + ere;
+        }
+        const double2* xs = sr + rx * kStage;
+        const double2* ys = sr + ry * kStage;
+        const double2* zs = sr + ry2 * kStage;
         double re = 0.0, im = 0.0;
-        for (int s = g; s < T; s += 4) {
-            const double2 x = xs[s], y = ys[s];
+        for (int s = g; s < T; s += kGramGroups) {
+            const double2 x = xs[s], y = ys[s], z = zs[s];
             re = fma(x.x, y.x, re);
             re = fma(x.y, y.y, re);
-            im = fma(x.x, y.y, im);
-            im = fma(-x.y, y.x, im);
+            im = fma(x.x, z.x, im);
+            im = fma(x.y, z.y, im);
         }
-        if (e < kPairs && j == k) im = 0.0;
-        gsum[g * kEntries + 2 * e] = re;
-        gsum[g * kEntries + 2 * e + 1] = im;
+        double* gs = gsum + g * kEntries;
+        gs[ere] = re;
+        gs[eim] = im;
+        if (diag) {
+            gs[ere + 1] = 0.0;
+            gs[eim + 1] = 0.0;
+        }
     }
     __syncthreads();
-    if (tid < kEntries) out[tid] = ((gsum[tid] + gsum[kEntries + tid]) + gsum[2 * kEntries + tid]) + gsum[3 * kEntries + tid];
+    if (tid < kEntries) {
+        double s = gsum[tid];
+#pragma unroll
+        for (int g = 1; g < kGramGroups; ++g) s += gsum[g * kEntries + tid];
+        out[tid] = s;
+    }
 }
 
 // FP64 Gram sums accumulated over one staged chunk of up to kThreads sites
@@ -1342,6 +1392,11 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 if (active) stcg2(buf1 + (size_t)v * N + i, r1);
             }
             publish(p, cta, phase + 1);
+            if constexpr (sizeof(R) == 8) {
+                // the FP64 steps use 2 Htilde (exact scaling) so each step is FMAs only
+    #pragma unroll
+                for (int d = 0; d < 6; ++d) h[d] = c_make<R2>(2 * h[d].x, 2 * h[d].y);
+            }
 
             // ---- steps m = 1 .. M/2-1: r_{m+1} = 2 Htilde r_m - r_{m-1} and the Gram sums ----
             // FP32: each warp leaves its 112 Gram sums of step m in g32[m & 1]; they are added
@@ -1384,13 +1439,14 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                         for (int v = 0; v < kVec; ++v) nxt[v] = c_make<R2>(0, 0);
                     }
                 } else if (active) {
+                    // h holds 2 Htilde here: r_{m+1} = -r_{m-1} + sum_d (2 h_d) r_m(nb_d), FMAs only
     #pragma unroll
                     for (int v = 0; v < kVec; ++v) {
                         const R2* cv = rd + (size_t)v * N;
-                        R2 acc = c_make<R2>(0, 0);
+                        R2 acc = c_make<R2>(-prv[v].x, -prv[v].y);
     #pragma unroll
                         for (int d = 0; d < 6; ++d) c_fma(acc, h[d], ldcg2(cv + nb[d]));
-                        nxt[v] = c_make<R2>(fma((R)2, acc.x, -prv[v].x), fma((R)2, acc.y, -prv[v].y));
+                        nxt[v] = acc;
                         if (m < p.nsteps) stcg2(wr + (size_t)v * N + i, nxt[v]);
                     }
                 } else {
@@ -1399,11 +1455,13 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 }
                 double* prow = p.partial + ((size_t)(m - 1) * p.ncta + cta) * kEntries;
                 if constexpr (sizeof(R) == 8) {
-                    // stage r_m, r_{m+1} of the own site for the shared-memory Gram sums
+                    // stage r_m, r_{m+1} and -i times each of the own site for the Gram sums
     #pragma unroll
                     for (int v = 0; v < kVec; ++v) {
                         dyn[v * kStage + tid] = cur[v];
                         dyn[(kVec + v) * kStage + tid] = nxt[v];
+                        dyn[(2 * kVec + v) * kStage + tid] = minus_i(cur[v]);
+                        dyn[(3 * kVec + v) * kStage + tid] = minus_i(nxt[v]);
                     }
                 }
                 // r_{m+1} is stored: neighbours may start step m+1 while this CTA forms its dots

@@ -126,6 +126,7 @@ cudaError_t cluster_max_active(int precision, int C, int smem, int* out);
 cudaError_t cluster_static_smem(int precision, int* out);
 cudaError_t server_max_ctas(int smem, int* out);
 int engine_smem_bytes(int M);
+int single_smem_bytes(int M, int precision);
 cudaError_t engine_max_ctas(int precision, int M, int* out);
 cudaError_t launch_build_hoppings(const Params& p, cudaStream_t s);
 cudaError_t launch_setup_tables(const Params& p, int kernel_kind, double lambda, cudaStream_t s);

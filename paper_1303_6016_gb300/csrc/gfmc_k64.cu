@@ -6,7 +6,7 @@ namespace gfmc {
 template <int NV>
 static cudaError_t launch_nv_f64(const Params& p, cudaStream_t s)
 {
-    const int smem = engine_smem_bytes(p.M);
+    const int smem = single_smem_bytes(p.M, 0);
     cudaError_t e = cudaFuncSetAttribute(gfmc_engine<double, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     Params q = p;
@@ -24,7 +24,7 @@ cudaError_t launch_engine_f64(const Params& p, int nv, cudaStream_t s)
 
 cudaError_t engine_max_ctas_f64(int M, int* out)
 {
-    const int smem = engine_smem_bytes(M);
+    const int smem = single_smem_bytes(M, 0);
     cudaError_t e = cudaFuncSetAttribute(gfmc_engine<double>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;

@@ -34,6 +34,16 @@ int engine_smem_bytes(int M)
     return fft > stage ? fft : stage;
 }
 
+// Dynamic shared memory of the one-site-per-thread engine: the FFT buffer or,
+// for FP64, the 28 staged rows of its Gram sums (r_m, r_{m+1} and -i times each).
+int single_smem_bytes(int M, int precision)
+{
+    if (precision != 0) return engine_smem_bytes(M);
+    const int fft = M * (int)sizeof(double2);
+    const int stage = 4 * kVec * kStage * (int)sizeof(double2);
+    return fft > stage ? fft : stage;
+}
+
 cudaError_t cluster_max_active_f64(int C, int smem, int* out);
 cudaError_t cluster_max_active_f32(int C, int smem, int* out);
 
