@@ -207,6 +207,45 @@ __device__ __forceinline__ void publish(const Params& p, int cta, unsigned value
     }
 }
 
+// Named CTA barriers (ids 1..15; 0 is __syncthreads).  bar.arrive does not
+// wait; it synchronises with the bar.sync of the same barrier, so writes made
+// before an arrive are visible to the threads released by that sync.
+__device__ __forceinline__ void nbar_sync(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void nbar_arrive(int id, int n)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+// wait_neighbours for one warp: the lanes poll the neighbour CTAs' flags
+// (acquire) in parallel; true in every lane when all reached `target`, false
+// when an error was recorded or this warp's wait ran out of its budget.
+__device__ inline bool warp_wait_neighbours(const Params& p, int cta, unsigned target, int where, int lane)
+{
+    bool ok = true;
+    if (p.ncta > 1) {
+        const int b = p.nbr_ptr[cta], e = p.nbr_ptr[cta + 1];
+        for (int q = b + lane; q < e && ok; q += 32) {
+            const unsigned* f = &p.flags[p.nbr_idx[q]];
+            const long long t0 = clock64();
+            while ((int)(ld_acquire_u32(f) - target) < 0) {
+                if (ld_relaxed_s32(p.err) != 0) {
+                    ok = false;
+                    break;
+                }
+                if (clock64() - t0 > p.budget) {
+                    set_error(p, ERR_TIMEOUT, where, (int)target);
+                    ok = false;
+                    break;
+                }
+            }
+        }
+    }
+    return __all_sync(0xffffffffu, ok) != 0;
+}
+
 // ---------------------------------------------------------------------------
 // reductions
 // ---------------------------------------------------------------------------
@@ -487,6 +526,9 @@ __device__ __forceinline__ double2 minus_i(double2 z)
     return make_double2(z.y, __hiloint2double(__double2hiint(z.x) ^ 0x80000000, __double2loint(z.x)));
 }
 
+// NAMED: the CTA's compute warps (threads 0..kThreads-1) meet at named barrier
+// 1 instead of __syncthreads (a helper warp runs elsewhere meanwhile).
+template <bool NAMED = false>
 __device__ __forceinline__ void gram_smem_f64(const double2* sr, int T, double* gsum, double* out)
 {
     const int tid = threadIdx.x;
@@ -536,7 +578,7 @@ __device__ __forceinline__ void gram_smem_f64(const double2* sr, int T, double* 
             gs[eim + 1] = 0.0;
         }
     }
-    __syncthreads();
+    if constexpr (NAMED) nbar_sync(1, kThreads); else __syncthreads();
     if (tid < kEntries) {
         double s = gsum[tid];
 #pragma unroll
@@ -1201,7 +1243,8 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
 {
     static_assert(NV == kVec || NV == 2, "recursion on 7 unit vectors or on o and v");
     static_assert(VARIANT != 2 || NV == 2, "cluster variant: recursion on o and v");
-    static_assert(NT == kThreads || VARIANT == 2, "only the cluster variant runs other block sizes");
+    static_assert(NT == kThreads || VARIANT == 2 || (VARIANT == 0 && sizeof(R) == 8 && NV == kVec),
+                  "other block sizes: the cluster variant, and the FP64 single-chain engine's helper warp");
     static_assert(NT % 32 == 0 && NT >= kThreads, "whole warps, at least the default block");
     constexpr int NW = NT / 32;
     // per warp: room for 112 Gram entries; the cluster variant only reduces 8 here
@@ -1410,6 +1453,71 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                     p.partial[((size_t)(m - 1) * p.ncta + cta) * kEntries + tid] = sum;
                 }
             };
+            if constexpr (sizeof(R) == 8 && NT > kThreads) {
+                // FP64 with a helper warp (warp kWarps): after the compute warps' stencil of
+                // step m (named barrier 2) it publishes the CTA's flag and waits for the
+                // neighbours' flags of step m+1 (named barrier 3) while the compute warps form
+                // the Gram sums of step m, so neither the release nor the poll is on the
+                // FP64 pipe's critical path.
+                __shared__ int s_go;
+                if (warp == kWarps) {
+                    bool ok = true;
+                    for (int m = 1; m <= p.nsteps + 1 && ok; ++m) {
+                        if (m > 1) {
+                            nbar_sync(2, NT);
+                            if (lane == 0 && p.ncta > 1 && !(p.stall && cta == 0))
+                                st_release_u32(&p.flags[cta], phase + (unsigned)m);
+                        }
+                        if (m <= p.nsteps) {
+                            ok = warp_wait_neighbours(p, cta, phase + (unsigned)m, 100 + m, lane);
+                            if (lane == 0) s_go = ok ? 1 : 0;
+                            nbar_arrive(3, NT);
+                        }
+                    }
+                    if (!ok) return;
+                } else {
+                    for (int m = 1; m <= p.nsteps; ++m) {
+                        nbar_sync(3, NT);
+                        if (!s_go) return;
+                        const R2* rd = (m & 1) ? buf1 : buf0;  // r_m of every site
+                        R2* wr = (m & 1) ? buf0 : buf1;        // receives r_{m+1}; held r_{m-1}
+                        R2 nxt[kVec];
+                        if (active) {
+                            // h holds 2 Htilde: r_{m+1} = -r_{m-1} + sum_d (2 h_d) r_m(nb_d), FMAs only
+    #pragma unroll
+                            for (int v = 0; v < kVec; ++v) {
+                                const R2* cv = rd + (size_t)v * N;
+                                R2 acc = c_make<R2>(-prv[v].x, -prv[v].y);
+    #pragma unroll
+                                for (int d = 0; d < 6; ++d) c_fma(acc, h[d], ldcg2(cv + nb[d]));
+                                nxt[v] = acc;
+                                if (m < p.nsteps) stcg2(wr + (size_t)v * N + i, nxt[v]);
+                            }
+                        } else {
+    #pragma unroll
+                            for (int v = 0; v < kVec; ++v) nxt[v] = c_make<R2>(0, 0);
+                        }
+    #pragma unroll
+                        for (int v = 0; v < kVec; ++v) {
+                            dyn[v * kStage + tid] = cur[v];
+                            dyn[(kVec + v) * kStage + tid] = nxt[v];
+                            dyn[(2 * kVec + v) * kStage + tid] = minus_i(cur[v]);
+                            dyn[(3 * kVec + v) * kStage + tid] = minus_i(nxt[v]);
+                        }
+                        // r_{m+1} stored: the helper may publish it; the staged rows are
+                        // complete for the Gram sums once the compute warps meet at barrier 1
+                        nbar_arrive(2, NT);
+                        nbar_sync(1, kThreads);
+                        gram_smem_f64<true>(dyn, s1 - s0, &red[0][0],
+                                            p.partial + ((size_t)(m - 1) * p.ncta + cta) * kEntries);
+    #pragma unroll
+                        for (int v = 0; v < kVec; ++v) {
+                            prv[v] = cur[v];
+                            cur[v] = nxt[v];
+                        }
+                    }
+                }
+            } else
             for (int m = 1; m <= p.nsteps; ++m) {
                 if (!wait_neighbours(p, cta, phase + (unsigned)m, 100 + m)) return;
                 const R2* rd = (m & 1) ? buf1 : buf0;  // r_m of every site
@@ -1783,12 +1891,19 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
     }
 }
 
+// Threads per CTA of the single-chain engine: the FP64 unit-vector engine
+// adds a helper warp to the kThreads compute threads.
+template <class R, int NV> constexpr int engine_threads()
+{
+    return (sizeof(R) == 8 && NV == kVec) ? kThreads + 32 : kThreads;
+}
+
 // A single chain spread over the whole GPU.
 template <class R, int NV = kVec>
-__global__ void __launch_bounds__(kThreads, 1) gfmc_engine(const Params p)
+__global__ void __launch_bounds__(engine_threads<R, NV>()) gfmc_engine(const Params p)
 {
     extern __shared__ double2 dyn[];
-    run_chain<R, 0, NV>(p, blockIdx.x, dyn, nullptr);
+    run_chain<R, 0, NV, engine_threads<R, NV>()>(p, blockIdx.x, dyn, nullptr);
 }
 
 // A batch of chains, each on its own team of CTAs (jobs sorted by cta0).

@@ -11,8 +11,8 @@ static cudaError_t launch_nv_f64(const Params& p, cudaStream_t s)
     if (e != cudaSuccess) return e;
     Params q = p;
     void* args[] = {(void*)&q};
-    return cudaLaunchCooperativeKernel((void*)gfmc_engine<double, NV>, dim3(p.ncta), dim3(kThreads), args,
-                                       (size_t)smem, s);
+    return cudaLaunchCooperativeKernel((void*)gfmc_engine<double, NV>, dim3(p.ncta),
+                                       dim3(engine_threads<double, NV>()), args, (size_t)smem, s);
 }
 
 cudaError_t launch_engine_f64(const Params& p, cudaStream_t s) { return launch_nv_f64<kVec>(p, s); }
@@ -29,7 +29,8 @@ cudaError_t engine_max_ctas_f64(int M, int* out)
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gfmc_engine<double>, kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gfmc_engine<double>, engine_threads<double, kVec>(),
+                                                      smem);
     if (e != cudaSuccess) return e;
     *out = per_sm;
     return cudaSuccess;
