@@ -232,17 +232,19 @@ int orc_kernel(int kind, int M, double lambda, double* g)
 /* Green's function at the Chebyshev nodes by a direct sum (Eq. green)      */
 /* ------------------------------------------------------------------------ */
 
-/* Node k: w_k = cos(theta_k), theta_k = pi (k + 1/2) / M  (Sec. 2.2, the FFT
- * nodes).  G^{jl}(w_k + i0) = (i / sin theta_k) [g_0 mu_0^{jl}
- *                              + 2 sum_{n=1}^{M-1} g_n mu_n^{jl} e^{-i n theta_k}]
+/* Node k of K: w_k = cos(theta_k), theta_k = pi (k + 1/2) / K (Sec. 2.2, the
+ * FFT nodes; the paper takes K = M nodes, K > M samples the same M-moment
+ * expansion on a finer grid).
+ * G^{jl}(w_k + i0) = (i / sin theta_k) [g_0 mu_0^{jl}
+ *                    + 2 sum_{n=1}^{M-1} g_n mu_n^{jl} e^{-i n theta_k}]
  * for G = (Htilde - w)^{-1} (Eq. green, second line; the exponential form).
  * G_out is 7x7 complex, row-major. */
-int orc_green7(int M, const double* mu_in, const double* g, int k, double* G_out)
+int orc_green7(int M, int K, const double* mu_in, const double* g, int k, double* G_out)
 {
-    if (M < 2 || k < 0 || k >= M) return ORC_EINVAL;
+    if (M < 2 || K < 2 || k < 0 || k >= K) return ORC_EINVAL;
     const cx* mu = (const cx*)mu_in;
     cx* G = (cx*)G_out;
-    double th = ORC_PI * (k + 0.5) / M;
+    double th = ORC_PI * (k + 0.5) / K;
     cx pref = I / sin(th);
     cx* ph = (cx*)malloc(sizeof(cx) * M);
     if (!ph) return ORC_ENOMEM;
@@ -379,60 +381,62 @@ static double wrap_pi(double d)
  *      branch that vanishes below the spectrum is the one for which
  *      (1/pi) Im d log d/dE = rho - rho' of Eq. dos_diff holds).
  *   4. Delta Omega = (1/pi) int f(E) phi(E) dE  (Eq. d_seff2 divided by beta),
- *      with E = a w and the M-node Chebyshev-Gauss rule
- *      int_{-1}^{1} h(w) dw ~ (pi/M) sum_k sin(theta_k) h(w_k)
- *      (reading: the paper does not say how the integral is discretised).
+ *      with E = a w and the K-node Chebyshev-Gauss rule
+ *      int_{-1}^{1} h(w) dw ~ (pi/K) sum_k sin(theta_k) h(w_k)
+ *      (reading: the paper does not say how the integral is discretised; it
+ *      evaluates G on K = M nodes, which is the default).
  * Also returns the largest |phase increment| in *max_inc (may be NULL). */
 int orc_delta_omega_from_moments(int L, const double* spins, double t, double chem,
-                                 double beta, double a, int M, const double* mu,
+                                 double beta, double a, int M, int K, const double* mu,
                                  const double* g, long o, double theta_new,
                                  double phi_new, double* d_omega, double* max_inc)
 {
-    if (M < 2 || !(beta > 0)) return ORC_EINVAL;
+    if (M < 2 || K < 2 || !(beta > 0)) return ORC_EINVAL;
     cx D[49];
     int st = orc_delta7(L, spins, t, a, o, theta_new, phi_new, (double*)D);
     if (st) return st;
-    double* arg = (double*)malloc(sizeof(double) * M);
-    for (int k = 0; k < M; ++k) {
+    double* arg = (double*)malloc(sizeof(double) * K);
+    if (!arg) return ORC_ENOMEM;
+    for (int k = 0; k < K; ++k) {
         cx G[49];
         double dk[2];
-        orc_green7(M, mu, g, k, (double*)G);
+        orc_green7(M, K, mu, g, k, (double*)G);
         orc_det_one_plus_gd((const double*)G, (const double*)D, dk);
         if (!isfinite(dk[0]) || !isfinite(dk[1])) { free(arg); return ORC_ENUMERIC; }
         arg[k] = atan2(dk[1], dk[0]);
     }
-    double phase = arg[M - 1];
+    double phase = arg[K - 1];
     double worst = fabs(phase);
     double sum = 0.0;
-    for (int k = M - 1; k >= 0; --k) {
-        if (k < M - 1) {
+    for (int k = K - 1; k >= 0; --k) {
+        if (k < K - 1) {
             double inc = wrap_pi(arg[k] - arg[k + 1]);
             if (fabs(inc) > worst) worst = fabs(inc);
             phase += inc;
         }
-        double th = ORC_PI * (k + 0.5) / M;
+        double th = ORC_PI * (k + 0.5) / K;
         double E = a * cos(th);
         sum += sin(th) * fermi(E, beta, chem) * phase;
     }
     free(arg);
-    *d_omega = a / M * sum;
+    *d_omega = a / K * sum;
     if (max_inc) *max_inc = worst;
     return ORC_OK;
 }
 
-/* Moments + Delta Omega in one call, for a chosen kernel. */
+/* Moments + Delta Omega in one call, for a chosen kernel and K nodes. */
 int orc_delta_omega(int L, const double* spins, double t, double chem, double beta,
-                    double a, int M, int kernel, double lambda, long o,
+                    double a, int M, int K, int kernel, double lambda, long o,
                     double theta_new, double phi_new, double* d_omega)
 {
     long N = (long)L * L * L;
-    if (L < 3 || o < 0 || o >= N || M < 2) return ORC_EINVAL;
+    if (L < 3 || o < 0 || o >= N || M < 2 || K < 2) return ORC_EINVAL;
     double* mu = (double*)malloc(sizeof(double) * 2 * 49 * (size_t)M);
     double* g = (double*)malloc(sizeof(double) * M);
     int st = orc_moments(L, spins, t, a, o, M, mu);
     if (!st) st = orc_kernel(kernel, M, lambda, g);
     if (!st)
-        st = orc_delta_omega_from_moments(L, spins, t, chem, beta, a, M, mu, g, o,
+        st = orc_delta_omega_from_moments(L, spins, t, chem, beta, a, M, K, mu, g, o,
                                           theta_new, phi_new, d_omega, NULL);
     free(mu);
     free(g);
@@ -534,13 +538,13 @@ double orc_magnetization(int L, const double* spins)
  * NULL): -1 = decide, 0/1 = take this decision instead (used to follow another
  * implementation through a near tie). */
 int orc_updates(int L, double* spins, double t, double chem, double beta, double a,
-                int M, int kernel, double lambda, uint64_t seed, uint32_t chain_id,
+                int M, int K, int kernel, double lambda, uint64_t seed, uint32_t chain_id,
                 uint64_t upd0, long n_updates, const int8_t* forced_in,
                 uint8_t* decisions_out, double* d_omega_out, double* ratio_u_out,
                 double* mag_out, long* n_mag)
 {
     long N = (long)L * L * L;
-    if (L < 3 || M < 2 || !(beta > 0) || n_updates < 0) return ORC_EINVAL;
+    if (L < 3 || M < 2 || K < 2 || !(beta > 0) || n_updates < 0) return ORC_EINVAL;
     double* mu = (double*)malloc(sizeof(double) * 2 * 49 * (size_t)M);
     double* g = (double*)malloc(sizeof(double) * M);
     if (!mu || !g) { free(mu); free(g); return ORC_ENOMEM; }
@@ -553,7 +557,7 @@ int orc_updates(int L, double* spins, double t, double chem, double beta, double
         orc_draw(seed, chain_id, upd, &th, &ph, &u);
         st = orc_moments(L, spins, t, a, o, M, mu);
         if (st) break;
-        st = orc_delta_omega_from_moments(L, spins, t, chem, beta, a, M, mu, g, o, th, ph,
+        st = orc_delta_omega_from_moments(L, spins, t, chem, beta, a, M, K, mu, g, o, th, ph,
                                           &dO, NULL);
         if (st) break;
         double ratio = exp(-beta * dO);

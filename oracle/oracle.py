@@ -52,15 +52,15 @@ def lib():
         L.orc_apply_htilde.argtypes = [c_int, d, c_double, c_double, d, d]
         L.orc_moments.argtypes = [c_int, d, c_double, c_double, c_long, c_int, d]
         L.orc_kernel.argtypes = [c_int, c_int, c_double, d]
-        L.orc_green7.argtypes = [c_int, d, d, c_int, d]
+        L.orc_green7.argtypes = [c_int, c_int, d, d, c_int, d]
         L.orc_delta7.argtypes = [c_int, d, c_double, c_double, c_long, c_double, c_double, d]
         L.orc_det_one_plus_gd.argtypes = [d, d, d]
         L.orc_det7.argtypes = [d, d]
         L.orc_delta_omega_from_moments.argtypes = [c_int, d, c_double, c_double, c_double,
-                                                   c_double, c_int, d, d, c_long, c_double,
+                                                   c_double, c_int, c_int, d, d, c_long, c_double,
                                                    c_double, d, d]
         L.orc_delta_omega.argtypes = [c_int, d, c_double, c_double, c_double, c_double, c_int,
-                                      c_int, c_double, c_long, c_double, c_double, d]
+                                      c_int, c_int, c_double, c_long, c_double, c_double, d]
         L.orc_grand_potential.argtypes = [c_long, d, c_double, c_double]
         L.orc_grand_potential.restype = c_double
         L.orc_philox4x32_10.argtypes = [u32, u32, u32]
@@ -70,7 +70,7 @@ def lib():
         L.orc_magnetization.argtypes = [c_int, d]
         L.orc_magnetization.restype = c_double
         L.orc_updates.argtypes = [c_int, d, c_double, c_double, c_double, c_double, c_int, c_int,
-                                  c_double, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
+                                  c_int, c_double, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64,
                                   c_long, i8, u8, d, d, d, lp]
         _lib = L
     return _lib
@@ -132,12 +132,14 @@ def kernel(M, kind=0, lam=4.0):
     return g
 
 
-def green7(mu, g, k):
+def green7(mu, g, k, nodes=None):
+    """7x7 Green's matrix at node k of `nodes` (default M) Chebyshev nodes."""
     mu = np.ascontiguousarray(mu, dtype=np.complex128)
     g = np.ascontiguousarray(g, dtype=np.float64)
     M = mu.shape[-1]
+    K = M if nodes is None else int(nodes)
     G = np.zeros((7, 7), dtype=np.complex128)
-    _check(lib().orc_green7(M, _dp(mu.view(np.float64)), _dp(g), k, _dp(G.view(np.float64))),
+    _check(lib().orc_green7(M, K, _dp(mu.view(np.float64)), _dp(g), k, _dp(G.view(np.float64))),
            "green7")
     return G
 
@@ -167,14 +169,15 @@ def det7(A):
 
 
 def delta_omega_from_moments(L, spins, mu, g, site, theta_new, phi_new, t=1.0, chem=-2.0,
-                             beta=20.0, a=None):
+                             beta=20.0, a=None, nodes=None):
     a = DEFAULT_SCALE * abs(t) if a is None else a
     s = _spins(spins)
     mu = np.ascontiguousarray(mu, dtype=np.complex128)
     g = np.ascontiguousarray(g, dtype=np.float64)
     out = np.zeros(1)
     inc = np.zeros(1)
-    _check(lib().orc_delta_omega_from_moments(L, _dp(s), t, chem, beta, a, mu.shape[-1],
+    K = mu.shape[-1] if nodes is None else int(nodes)
+    _check(lib().orc_delta_omega_from_moments(L, _dp(s), t, chem, beta, a, mu.shape[-1], K,
                                               _dp(mu.view(np.float64)), _dp(g), site,
                                               theta_new, phi_new, _dp(out), _dp(inc)),
            "delta_omega_from_moments")
@@ -182,11 +185,12 @@ def delta_omega_from_moments(L, spins, mu, g, site, theta_new, phi_new, t=1.0, c
 
 
 def delta_omega(L, spins, site, theta_new, phi_new, M, t=1.0, chem=-2.0, beta=20.0, a=None,
-                kernel_kind=0, lam=4.0):
+                kernel_kind=0, lam=4.0, nodes=None):
     a = DEFAULT_SCALE * abs(t) if a is None else a
     s = _spins(spins)
     out = np.zeros(1)
-    _check(lib().orc_delta_omega(L, _dp(s), t, chem, beta, a, M, kernel_kind, lam, site,
+    K = M if nodes is None else int(nodes)
+    _check(lib().orc_delta_omega(L, _dp(s), t, chem, beta, a, M, K, kernel_kind, lam, site,
                                  theta_new, phi_new, _dp(out)), "delta_omega")
     return float(out[0])
 
@@ -216,8 +220,10 @@ def magnetization(L, spins):
 
 
 def updates(L, spins, n_updates, M, t=1.0, chem=-2.0, beta=20.0, a=None, kernel_kind=0,
-            lam=4.0, seed=1, chain_id=0, upd0=0, forced=None):
-    """Run n_updates sequential updates; returns a dict with the new spins and traces."""
+            lam=4.0, seed=1, chain_id=0, upd0=0, forced=None, nodes=None):
+    """Run n_updates sequential updates (Green's function and quadrature on
+    `nodes` Chebyshev nodes, default M); returns a dict with the new spins and
+    traces."""
     a = DEFAULT_SCALE * abs(t) if a is None else a
     s = _spins(spins).copy()
     n = int(n_updates)
@@ -231,7 +237,8 @@ def updates(L, spins, n_updates, M, t=1.0, chem=-2.0, beta=20.0, a=None, kernel_
     if forced is not None:
         f = np.ascontiguousarray(forced, dtype=np.int8)
         fp = f.ctypes.data_as(ctypes.POINTER(ctypes.c_int8))
-    _check(lib().orc_updates(L, _dp(s), t, chem, beta, a, M, kernel_kind, lam, seed, chain_id,
+    K = M if nodes is None else int(nodes)
+    _check(lib().orc_updates(L, _dp(s), t, chem, beta, a, M, K, kernel_kind, lam, seed, chain_id,
                              upd0, n, fp, dec.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
                              _dp(dom), _dp(ru), _dp(mag), ctypes.byref(nmag)), "updates")
     return {"spins": s, "decisions": dec, "d_omega": dom, "ratio": ru[:, 0], "u": ru[:, 1],

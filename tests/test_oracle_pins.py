@@ -360,6 +360,58 @@ def test_delta_omega_converges_to_exact_diagonalisation(beta):
     assert total[512] < total[128]
 
 
+@pytest.mark.parametrize("factor", [1, 2, 4])
+def test_green_sum_rule_on_finer_node_grids(factor):
+    """K >= M nodes theta_k = pi (k + 1/2)/K (the FFT nodes of Sec. 2.2 on a
+    finer grid): sin(theta) Im G(w) is a polynomial of degree M - 1 in w, so the
+    K-node Chebyshev-Gauss rule gives the sum rule pi g_0 mu_0 exactly for every
+    K >= M / 2."""
+    M, eps = 256, -0.47
+    K = factor * M
+    g = O.kernel(M, 0)
+    mu = np.zeros((7, 7, M), dtype=np.complex128)
+    mu[0, 0, :] = cheb_T(np.arange(M), eps)
+    th = np.pi * (np.arange(K) + 0.5) / K
+    s = sum(math.sin(th[k]) * O.green7(mu, g, k, nodes=K)[0, 0].imag for k in range(K))
+    assert s * math.pi / K == pytest.approx(math.pi * g[0], abs=1e-12)
+    # and the far field 1/(eps - w) is sampled at the K-grid's own nodes
+    ks = np.arange(3, K, 97)
+    w = np.cos(th[ks])
+    G = np.array([O.green7(mu, g, int(k), nodes=K)[0, 0] for k in ks])
+    far = np.abs(w - eps) > 0.3
+    np.testing.assert_allclose(G[far].real, 1.0 / (eps - w[far]), rtol=5e-3, atol=5e-3)
+
+
+def test_identity_proposal_gives_zero_on_2m_nodes():
+    L, M = 4, 64
+    sp = inputs.uniform_sphere(L, 0)
+    for o in (0, 13):
+        assert O.delta_omega(L, sp, o, sp[o, 0], sp[o, 1], M, nodes=2 * M) == 0.0
+
+
+@pytest.mark.parametrize("beta", [1.0, 5.0, 20.0])
+def test_2m_nodes_converge_to_exact_diagonalisation(beta):
+    """Delta Omega with the Green's function and the quadrature on K = 2M nodes
+    against Omega(S') - Omega(S) from the eigenvalues (Sec. 2.1) on a 6^3
+    lattice, and against the same expansion on 8M nodes: doubling the nodes
+    takes out most of the quadrature error of the M-node rule."""
+    L, chem = 6, -2.0
+    sp = inputs.uniform_sphere(L, 0)
+    q_m = q_2m = 0.0
+    for o, th, ph in ((0, 1.0, 2.0), (5, 2.5, 0.3), (17, 0.2, 4.0)):
+        exact = exact_delta_omega(L, sp, o, th, ph, beta, chem)
+        for M in (256, 512):
+            mu = O.moments(L, sp, o, M)
+            g = O.kernel(M)
+            d = {K: O.delta_omega_from_moments(L, sp, mu, g, o, th, ph, beta=beta, chem=chem, nodes=K)[0]
+                 for K in (M, 2 * M, 8 * M)}
+            tol = 5e-4 if beta < 20 else 3.5e-3  # site 17 at beta = 20 sits on a sharp feature
+            assert abs(d[2 * M] - exact) < tol, (o, M, d[2 * M], exact)
+            q_m += abs(d[M] - d[8 * M])
+            q_2m += abs(d[2 * M] - d[8 * M])
+    assert q_2m < 0.05 * q_m, (q_2m, q_m)
+
+
 # --------------------------------------------------------------------------
 # Philox4x32-10 and the Metropolis sweep (Algorithm 1)
 # --------------------------------------------------------------------------
