@@ -83,10 +83,17 @@ typedef struct {
      * chains on at most 256 sites per CTA; gfmc_moments, batches and servers
      * always use the unit vectors. */
     int recursion;
+    /* Chebyshev nodes K of the Green's function and of the Delta Omega
+     * quadrature, w_k = cos(pi (k + 1/2) / K): 0 or M selects K = M, the nodes
+     * of the paper's FFT (Sec. 2.2, Eq. green_short); 2 M samples the same
+     * M-moment expansion on twice as many nodes (an FFT of the zero-padded
+     * moments), which takes out most of the quadrature error of Eq. d_seff2.
+     * Any other value is GFMC_EINVAL. */
+    int nodes;
 } gfmc_options;
 
 /* Fill *opt with the defaults (FP64, Jackson, a = 6.05|t|, seed 1, chain 0,
- * default stream, automatic CTA count, unit-vector recursion). */
+ * default stream, automatic CTA count, unit-vector recursion, K = M nodes). */
 void gfmc_default_options(gfmc_options* opt);
 
 /* Create a chain (Sec. 2.1: the spin configuration and H({S}); Sec. 3.3.2:
@@ -198,8 +205,10 @@ gfmc_status gfmc_run_clusters(gfmc_t* chains, int n_chains, const int64_t* n_upd
 
 /* The smallest cluster size (1, 2, 4, 8 or 16 CTAs, dividing L) whose shared
  * memory holds a chain of side L with M moments in the given precision on the
- * current device, for gfmc_run_clusters.  GFMC_EINVAL (and 0) when none does
- * or the arguments are out of range (L in [3, 64], M a power of two >= 16). */
+ * current device, for gfmc_run_clusters (for a chain on K = 2M nodes pass
+ * 2M: the tail's work area grows with the nodes).  GFMC_EINVAL (and 0) when
+ * none does or the arguments are out of range (L in [3, 64], M a power of
+ * two >= 16). */
 gfmc_status gfmc_cluster_min_ctas(int L, int M, int precision, int* cluster_ctas);
 
 /* ------------------------------------------------------------------------
@@ -218,7 +227,8 @@ gfmc_status gfmc_cluster_min_ctas(int L, int M, int precision, int* cluster_ctas
 typedef struct gfmc_server_ctx* gfmc_server_t;
 
 /* n_slots slots of slot_ctas[k] CTAs each (their sum must fit on the device
- * at once); max_M bounds the M of the chains the server will run. */
+ * at once); max_M bounds the M, and the Chebyshev nodes, of the chains the
+ * server will run. */
 gfmc_status gfmc_server_create(int n_slots, const int* slot_ctas, int max_M, gfmc_server_t* out);
 
 /* Post a job to an idle slot: n_updates >= 1 updates of chain h from its

@@ -142,7 +142,7 @@ class ClusterRunner:
 
     def __init__(self, chains):
         self.chains = list(chains)
-        self.cluster_ctas = [gfmc.cluster_min_ctas(c.L, c.M, c.precision) for c in self.chains]
+        self.cluster_ctas = [gfmc.cluster_min_ctas(c.L, max(c.M, c.K), c.precision) for c in self.chains]
 
     def run(self, updates_per_chain, trace: bool = False):
         n = len(self.chains)

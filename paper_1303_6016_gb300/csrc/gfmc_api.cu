@@ -19,7 +19,7 @@
 using gfmc::Params;
 
 struct gfmc_ctx {
-    int L = 0, N = 0, M = 0, precision = 0, kernel = 0, device = 0;
+    int L = 0, N = 0, M = 0, K = 0, precision = 0, kernel = 0, device = 0;
     double t = 0, chem = 0, beta = 0, a = 0, lambda = 4.0;
     uint64_t seed = 1;
     uint32_t chain_id = 0;
@@ -179,7 +179,7 @@ gfmc_status run_engine(gfmc_ctx* h, Params& P)
         job.vec_smem = 0;
         if ((e = cudaMemcpyAsync(h->d_job, &job, sizeof(job), cudaMemcpyHostToDevice, h->stream)) != cudaSuccess)
             return cuda_fail(h, e, "uploading the job");
-        const int smem = gfmc::engine_smem_bytes(P.M);
+        const int smem = gfmc::engine_smem_bytes(P.K);
         e = h->precision == GFMC_PREC_FP64 ? gfmc::launch_team_f64(h->d_job, 1, P.ncta, 0, smem, h->stream)
                                             : gfmc::launch_team_f32(h->d_job, 1, P.ncta, 0, smem, h->stream);
     } else {
@@ -292,6 +292,7 @@ void gfmc_default_options(gfmc_options* opt)
     opt->stream = nullptr;
     opt->num_ctas = 0;
     opt->recursion = GFMC_RECURSION_UNIT_VECTORS;
+    opt->nodes = 0;
 }
 
 gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double beta, int M,
@@ -319,12 +320,16 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
         return fail(nullptr, GFMC_EINVAL, "spectral scale a = %g must exceed 6|t| = %g", a, 6.0 * std::fabs(t));
     const double lam = opt.lorentz_lambda > 0 ? opt.lorentz_lambda : 4.0;
     if (!std::isfinite(lam)) return fail(nullptr, GFMC_EINVAL, "lorentz_lambda must be finite");
+    const int K = opt.nodes == 0 ? M : opt.nodes;
+    if (K != M && K != 2 * M)
+        return fail(nullptr, GFMC_EINVAL, "nodes = %d must be 0, M = %d or 2M = %d", opt.nodes, M, 2 * M);
 
     gfmc_ctx* h = new (std::nothrow) gfmc_ctx;
     if (!h) return fail(nullptr, GFMC_ENOMEM, "host allocation failed");
     h->L = L;
     h->N = L * L * L;
     h->M = M;
+    h->K = K;
     h->t = t;
     h->chem = mu;
     h->beta = beta;
@@ -352,10 +357,10 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
     if ((e = cudaGetDevice(&h->device)) != cudaSuccess) return bail(cuda_fail(h, e, "cudaGetDevice"));
 
     int maxc = 0;
-    if ((e = gfmc::engine_max_ctas(h->precision, M, &maxc)) != cudaSuccess)
+    if ((e = gfmc::engine_max_ctas(h->precision, K, &maxc)) != cudaSuccess)
         return bail(cuda_fail(h, e, "querying engine occupancy"));
     int maxt = 0;
-    if ((e = gfmc::team_max_ctas(h->precision, gfmc::engine_smem_bytes(M), &maxt)) != cudaSuccess)
+    if ((e = gfmc::team_max_ctas(h->precision, gfmc::engine_smem_bytes(K), &maxt)) != cudaSuccess)
         return bail(cuda_fail(h, e, "querying team occupancy"));
     maxc = std::min(maxc, maxt);
     const int N = h->N;
@@ -375,6 +380,7 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
     P.L = L;
     P.N = N;
     P.M = M;
+    P.K = K;
     P.nsteps = M / 2 - 1;
     P.ncta = ncta;
     P.divL = (unsigned)(((1ull << 32) + (unsigned long long)L - 1) / (unsigned long long)L);
@@ -394,11 +400,11 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
         (e = dalloc(h, &P.hop32, 3 * (size_t)N)) != cudaSuccess ||
         (e = dalloc(h, (char**)&rb, 2 * (size_t)gfmc::kVec * N * vbytes)) != cudaSuccess ||
         (e = dalloc(h, &P.gker, (size_t)M)) != cudaSuccess || (e = dalloc(h, &P.twc, (size_t)M)) != cudaSuccess ||
-        (e = dalloc(h, &P.fftw, (size_t)M / 2)) != cudaSuccess ||
-        (e = dalloc(h, &P.sinth, (size_t)M)) != cudaSuccess || (e = dalloc(h, &P.cumw, (size_t)M)) != cudaSuccess ||
+        (e = dalloc(h, &P.fftw, (size_t)K / 2)) != cudaSuccess ||
+        (e = dalloc(h, &P.sinth, (size_t)K)) != cudaSuccess || (e = dalloc(h, &P.cumw, (size_t)K)) != cudaSuccess ||
         (e = dalloc(h, &P.partial, (size_t)P.nsteps * ncta * gfmc::kEntries)) != cudaSuccess ||
         (e = dalloc(h, &P.fftin, 4 * (size_t)M)) != cudaSuccess ||
-        (e = dalloc(h, &P.gnode, 4 * (size_t)M)) != cudaSuccess ||
+        (e = dalloc(h, &P.gnode, 4 * (size_t)K)) != cudaSuccess ||
         (e = dalloc(h, &P.qpart, 2 * (size_t)ncta)) != cudaSuccess ||
         (e = dalloc(h, &P.magpart, 3 * (size_t)ncta)) != cudaSuccess ||
         (e = dalloc(h, &P.mom_out, 49 * (size_t)M)) != cudaSuccess ||
@@ -612,7 +618,7 @@ gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_update
     const size_t vsz = prec == GFMC_PREC_FP64 ? sizeof(double2) : sizeof(float2);
     // Shared memory: the largest resident lattice plus the work area of the largest M.
     int work = 0;
-    for (int c = 0; c < n_chains; ++c) work = std::max(work, gfmc::engine_smem_bytes(chains[c]->M));
+    for (int c = 0; c < n_chains; ++c) work = std::max(work, gfmc::engine_smem_bytes(chains[c]->K));
     int dev_smem = 0;
     if ((e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
         return cuda_fail(nullptr, e, "querying shared memory");
@@ -724,9 +730,9 @@ gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_update
     return result;
 }
 
-// Bytes of shared memory a CTA of a cluster of C CTAs needs for a chain of
-// side L with M moments: its slab of the lattice (two recursion buffers of
-// (o, v) and three forward bonds per site) plus the work area of the tail.
+// Bytes of shared memory a CTA of a cluster of C CTAs needs for the slab of a
+// chain of side L: two recursion buffers of (o, v) and three forward bonds per
+// site.
 static size_t cluster_lattice_bytes(int L, int C, int precision)
 {
     const size_t per_site = precision == GFMC_PREC_FP64 ? 2 * 32 + 3 * 16 : 2 * 16 + 3 * 8;
@@ -734,16 +740,16 @@ static size_t cluster_lattice_bytes(int L, int C, int precision)
     return (per_site * T + 255) & ~(size_t)255;
 }
 // Dynamic shared memory of a CTA: the slab during the recursion, reused as the
-// tail's work area (16 M bytes) afterwards.
-static size_t cluster_dyn_bytes(int L, int M, int C, int precision)
+// tail's work area (16 K bytes for K Chebyshev nodes) afterwards.
+static size_t cluster_dyn_bytes(int L, int K, int C, int precision)
 {
-    return std::max(cluster_lattice_bytes(L, C, precision), (size_t)M * sizeof(double2));
+    return std::max(cluster_lattice_bytes(L, C, precision), (size_t)K * sizeof(double2));
 }
 
 // dev_smem: the device's opt-in shared memory per block; static: the engine's own
-static bool cluster_fits(int L, int M, int C, int precision, int dev_smem, int static_smem)
+static bool cluster_fits(int L, int K, int C, int precision, int dev_smem, int static_smem)
 {
-    return L % C == 0 && cluster_dyn_bytes(L, M, C, precision) + (size_t)static_smem <= (size_t)dev_smem;
+    return L % C == 0 && cluster_dyn_bytes(L, K, C, precision) + (size_t)static_smem <= (size_t)dev_smem;
 }
 
 gfmc_status gfmc_cluster_min_ctas(int L, int M, int precision, int* cluster_ctas)
@@ -814,10 +820,10 @@ gfmc_status gfmc_run_clusters(gfmc_t* chains, int n_chains, const int64_t* n_upd
         const int T = h->N / C;
         if ((unsigned long long)h->N * (unsigned long long)T >= (1ull << 32))
             return fail(nullptr, GFMC_EINVAL, "chain %d: %d sites per CTA are too many for a cluster", c, T);
-        const size_t vb = cluster_dyn_bytes(h->L, h->M, C, h->precision);
+        const size_t vb = cluster_dyn_bytes(h->L, h->K, C, h->precision);
         const int work = 0;
         const int st_smem = static_smem[h->precision == GFMC_PREC_FP64 ? 0 : 1];
-        if (!cluster_fits(h->L, h->M, C, h->precision, dev_smem, st_smem))
+        if (!cluster_fits(h->L, h->K, C, h->precision, dev_smem, st_smem))
             return fail(nullptr, GFMC_EINVAL, "chain %d: %zu B of lattice per CTA (and %d B of the engine's own) exceed "
                         "the %d B of shared memory; use a larger cluster", c, vb, st_smem, dev_smem);
         Group* g = nullptr;
@@ -1081,7 +1087,8 @@ gfmc_status gfmc_server_submit(gfmc_server_t s, int slot, gfmc_t h, int64_t n_up
     if (s->chain[slot]) return sfail(s, GFMC_EINVAL, "slot %d is busy", slot);
     if (h->in_server) return sfail(s, GFMC_EINVAL, "the chain already has a job in a server");
     if (h->device != s->device) return sfail(s, GFMC_EINVAL, "the chain lives on another device");
-    if (h->M > s->maxM) return sfail(s, GFMC_EINVAL, "chain M = %d above the server's %d", h->M, s->maxM);
+    if (h->K > s->maxM)
+        return sfail(s, GFMC_EINVAL, "chain with M = %d on %d nodes above the server's %d", h->M, h->K, s->maxM);
     if (n_updates < 1) return sfail(s, GFMC_EINVAL, "n_updates = %lld < 1", (long long)n_updates);
     const int tc = s->slot_ctas[slot];
     if (tc > h->N) return sfail(s, GFMC_EINVAL, "slot of %d CTAs for a chain of %d sites", tc, h->N);

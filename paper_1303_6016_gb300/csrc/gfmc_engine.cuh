@@ -1732,18 +1732,20 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
         if (!chain_barrier<VARIANT>(p, 2)) return;
         if (p.mode == MODE_MOMENTS) return;
 
-        // ---- FFT of the four sequences and G_V at the nodes ----
+        // ---- K-point FFT of the four sequences (zero beyond M) and G_V at the K nodes ----
+        const int K = p.K;
         {
             int lg = 0;
-            while ((1 << lg) < M) ++lg;
+            while ((1 << lg) < K) ++lg;
             for (int V = cta; V < 4; V += p.ncta) {
                 double2* x = dyn;
-                for (int n = tid; n < M; n += NT)
-                    x[__brev((unsigned)n) >> (32 - lg)] = __ldcg(p.fftin + (size_t)V * M + n);
+                for (int n = tid; n < K; n += NT)
+                    x[__brev((unsigned)n) >> (32 - lg)] =
+                        n < M ? __ldcg(p.fftin + (size_t)V * M + n) : make_double2(0.0, 0.0);
                 __syncthreads();
-                for (int half = 1, lh = 0; half < M; half <<= 1, ++lh) {
-                    const int tstride = M >> (lh + 1);
-                    for (int b = tid; b < (M >> 1); b += NT) {
+                for (int half = 1, lh = 0; half < K; half <<= 1, ++lh) {
+                    const int tstride = K >> (lh + 1);
+                    for (int b = tid; b < (K >> 1); b += NT) {
                         const int grp = b >> lh, pos = b & (half - 1);
                         const int i0 = (grp << (lh + 1)) + pos, i1 = i0 + half;
                         const double2 w = __ldcg(p.fftw + (size_t)pos * tstride);
@@ -1753,10 +1755,10 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                     }
                     __syncthreads();
                 }
-                for (int k = tid; k < M; k += NT) {
-                    const double2 chi = (k & 1) ? dconj(x[M - 1 - (k >> 1)]) : x[k >> 1];
+                for (int k = tid; k < K; k += NT) {
+                    const double2 chi = (k & 1) ? dconj(x[K - 1 - (k >> 1)]) : x[k >> 1];
                     const double sc = 2.0 / __ldcg(p.sinth + k);
-                    p.gnode[(size_t)V * M + k] = make_double2(-sc * chi.y, sc * chi.x);
+                    p.gnode[(size_t)V * K + k] = make_double2(-sc * chi.y, sc * chi.x);
                 }
                 __syncthreads();
             }
@@ -1765,13 +1767,13 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
 
         // ---- d_k, continuous phase, Chebyshev-Gauss partial sums ----
         {
-            const int k0 = (int)(((long long)cta * M) / p.ncta);
-            const int k1 = (int)(((long long)(cta + 1) * M) / p.ncta);
-            const int kend = min(k1 + 1, M);
+            const int k0 = (int)(((long long)cta * K) / p.ncta);
+            const int k1 = (int)(((long long)(cta + 1) * K) / p.ncta);
+            const int kend = min(k1 + 1, K);
             double* sarg = (double*)dyn;
             for (int k = k0 + tid; k < kend; k += NT) {
-                const double2 Goo = __ldcg(p.gnode + k), Gvv = __ldcg(p.gnode + (size_t)M + k);
-                const double2 Gp = __ldcg(p.gnode + 2 * (size_t)M + k), Gq = __ldcg(p.gnode + 3 * (size_t)M + k);
+                const double2 Goo = __ldcg(p.gnode + k), Gvv = __ldcg(p.gnode + (size_t)K + k);
+                const double2 Gp = __ldcg(p.gnode + 2 * (size_t)K + k), Gq = __ldcg(p.gnode + 3 * (size_t)K + k);
                 const double2 Am = dsub(dsub(Gp, Goo), Gvv);  // G_ov + G_vo
                 const double2 Bm = dsub(dsub(Gq, Goo), Gvv);  // i (G_ov - G_vo)
                 // G_ov = (A - iB)/2, G_vo = (A + iB)/2
@@ -1786,7 +1788,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
             double part = 0.0, mx = 0.0;
             for (int k = k0 + tid; k < k1; k += NT) {
                 double inc;
-                if (k == M - 1) {
+                if (k == K - 1) {
                     inc = sarg[k - k0];
                 } else {
                     inc = sarg[k - k0] - sarg[k + 1 - k0];
@@ -1812,7 +1814,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 s += __ldcg(p.qpart + 2 * c);
                 mx = fmax(mx, __ldcg(p.qpart + 2 * c + 1));
             }
-            const double dom = p.a / M * s;
+            const double dom = p.a / K * s;
             s_dom = dom;
             int acc = 0;
             if (p.mode == MODE_SWEEP) {

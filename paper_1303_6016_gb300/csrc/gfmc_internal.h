@@ -25,6 +25,7 @@ enum ErrCode : int { ERR_NONE = 0, ERR_TIMEOUT = 4, ERR_NUMERIC = 5 };
 struct Params {
     // lattice and model
     int L, N, M, nsteps, ncta;
+    int K;                 // Chebyshev nodes of G and of the quadrature (M or 2M)
     unsigned divL, divLL;  // ceil(2^32 / L), ceil(2^32 / L^2): exact i / L, i / L^2 for i < N
     unsigned divT;         // cluster variant: ceil(2^32 / (N / ncta)), the owner of a site
     double t, chem, beta, a;
@@ -37,15 +38,15 @@ struct Params {
 
     // constant tables, filled by the set-up kernel
     double* gker;     // [M]     kernel g_n
-    double2* twc;     // [M]     e^{-i n pi / (2M)}
-    double2* fftw;    // [M/2]   e^{-2 pi i j / M}
-    double* sinth;    // [M]     sin theta_k, theta_k = pi (k + 1/2) / M
-    double* cumw;     // [M]     C_k = sum_{j<=k} sin theta_j f(a cos theta_j)
+    double2* twc;     // [M]     e^{-i n pi / (2K)}
+    double2* fftw;    // [K/2]   e^{-2 pi i j / K}
+    double* sinth;    // [K]     sin theta_k, theta_k = pi (k + 1/2) / K
+    double* cumw;     // [K]     C_k = sum_{j<=k} sin theta_j f(a cos theta_j)
 
     // per-update scratch
     double* partial;  // [nsteps][ncta][kEntries]  per-CTA Gram partial sums
-    double2* fftin;   // [4][M]  damped, twisted combined moments
-    double2* gnode;   // [4][M]  G_V(w_k) for V = o, v, o+v, o+iv
+    double2* fftin;   // [4][M]  damped, twisted combined moments (zero beyond M)
+    double2* gnode;   // [4][K]  G_V(w_k) for V = o, v, o+v, o+iv
     double* qpart;    // [ncta][2]  (phase-sum partial, max |increment|)
     double* magpart;  // [ncta][3]
     double2* mom_out; // [7][7][M] full moment matrix (moments mode)
@@ -125,9 +126,10 @@ cudaError_t cluster_max_active(int precision, int C, int smem, int* out);
 // static shared memory of the cluster engine of a precision (bytes)
 cudaError_t cluster_static_smem(int precision, int* out);
 cudaError_t server_max_ctas(int smem, int* out);
-int engine_smem_bytes(int M);
-int single_smem_bytes(int M, int precision);
-cudaError_t engine_max_ctas(int precision, int M, int* out);
+// K: the number of Chebyshev nodes (the FFT buffer of the tail holds K double2)
+int engine_smem_bytes(int K);
+int single_smem_bytes(int K, int precision);
+cudaError_t engine_max_ctas(int precision, int K, int* out);
 cudaError_t launch_build_hoppings(const Params& p, cudaStream_t s);
 cudaError_t launch_setup_tables(const Params& p, int kernel_kind, double lambda, cudaStream_t s);
 

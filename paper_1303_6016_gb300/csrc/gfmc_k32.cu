@@ -7,7 +7,7 @@ namespace gfmc {
 template <int NV>
 static cudaError_t launch_nv_f32(const Params& p, cudaStream_t s)
 {
-    const int smem = engine_smem_bytes(p.M);
+    const int smem = engine_smem_bytes(p.K);
     cudaError_t e = cudaFuncSetAttribute(gfmc_engine<float, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     Params q = p;
@@ -23,9 +23,9 @@ cudaError_t launch_engine_f32(const Params& p, int nv, cudaStream_t s)
     return nv == 2 ? launch_nv_f32<2>(p, s) : launch_nv_f32<kVec>(p, s);
 }
 
-cudaError_t engine_max_ctas_f32(int M, int* out)
+cudaError_t engine_max_ctas_f32(int K, int* out)
 {
-    const int smem = engine_smem_bytes(M);
+    const int smem = engine_smem_bytes(K);
     cudaError_t e = cudaFuncSetAttribute(gfmc_engine<float>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;

@@ -6,7 +6,7 @@ namespace gfmc {
 template <int NV>
 static cudaError_t launch_nv_f64(const Params& p, cudaStream_t s)
 {
-    const int smem = single_smem_bytes(p.M, 0);
+    const int smem = single_smem_bytes(p.K, 0);
     cudaError_t e = cudaFuncSetAttribute(gfmc_engine<double, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     Params q = p;
@@ -22,9 +22,9 @@ cudaError_t launch_engine_f64(const Params& p, int nv, cudaStream_t s)
     return nv == 2 ? launch_nv_f64<2>(p, s) : launch_nv_f64<kVec>(p, s);
 }
 
-cudaError_t engine_max_ctas_f64(int M, int* out)
+cudaError_t engine_max_ctas_f64(int K, int* out)
 {
-    const int smem = single_smem_bytes(M, 0);
+    const int smem = single_smem_bytes(K, 0);
     cudaError_t e = cudaFuncSetAttribute(gfmc_engine<double>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;

@@ -8,8 +8,8 @@
 
 namespace gfmc {
 
-cudaError_t engine_max_ctas_f64(int M, int* out);
-cudaError_t engine_max_ctas_f32(int M, int* out);
+cudaError_t engine_max_ctas_f64(int K, int* out);
+cudaError_t engine_max_ctas_f32(int K, int* out);
 cudaError_t team_max_ctas_f64(int smem, int* out);
 cudaError_t team_max_ctas_f32(int smem, int* out);
 
@@ -25,21 +25,22 @@ cudaError_t team_max_ctas(int precision, int smem, int* out)
     return cudaSuccess;
 }
 
-// Dynamic shared memory of the engine: the FFT buffer (M double2) or the
-// staged own-site vectors of the FP64 Gram sums (14 x kStage double2).
-int engine_smem_bytes(int M)
+// Dynamic shared memory of the engine: the FFT buffer (K double2, K the
+// number of nodes) or the staged own-site vectors of the FP64 Gram sums
+// (14 x kStage double2).
+int engine_smem_bytes(int K)
 {
-    const int fft = M * (int)sizeof(double2);
+    const int fft = K * (int)sizeof(double2);
     const int stage = 2 * kVec * kStage * (int)sizeof(double2);
     return fft > stage ? fft : stage;
 }
 
 // Dynamic shared memory of the one-site-per-thread engine: the FFT buffer or,
 // for FP64, the 28 staged rows of its Gram sums (r_m, r_{m+1} and -i times each).
-int single_smem_bytes(int M, int precision)
+int single_smem_bytes(int K, int precision)
 {
-    if (precision != 0) return engine_smem_bytes(M);
-    const int fft = M * (int)sizeof(double2);
+    if (precision != 0) return engine_smem_bytes(K);
+    const int fft = K * (int)sizeof(double2);
     const int stage = 4 * kVec * kStage * (int)sizeof(double2);
     return fft > stage ? fft : stage;
 }
@@ -58,10 +59,10 @@ cudaError_t cluster_static_smem(int precision, int* out)
     return precision == 0 ? cluster_static_smem_f64(out) : cluster_static_smem_f32(out);
 }
 
-cudaError_t engine_max_ctas(int precision, int M, int* out)
+cudaError_t engine_max_ctas(int precision, int K, int* out)
 {
     int per_sm = 0;
-    cudaError_t e = precision == 0 ? engine_max_ctas_f64(M, &per_sm) : engine_max_ctas_f32(M, &per_sm);
+    cudaError_t e = precision == 0 ? engine_max_ctas_f64(K, &per_sm) : engine_max_ctas_f32(K, &per_sm);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0;
     e = cudaGetDevice(&dev);
@@ -110,27 +111,30 @@ __global__ void build_hoppings_kernel(Params p)
 // g_n: kind 0 Jackson [(M-n+1) cos(pi n/(M+1)) + sin(pi n/(M+1)) cot(pi/(M+1))]/(M+1)
 // (Weisse et al., Rev. Mod. Phys. 78, 275, the KPM review the paper cites);
 // kind 1 Lorentz sinh(lambda (1 - n/M)) / sinh(lambda) (Sec. 2.2).
-// twc_n = e^{-i n pi/(2M)} (Eq. mu_to_mu_tilde); fftw_j = e^{-2 pi i j/M}
-// (Eq. green_fft); sin theta_k with theta_k = pi (k + 1/2)/M (the FFT nodes).
+// With K nodes (K = M in the paper; the zero-padded moments make a K-point
+// FFT for K > M): twc_n = e^{-i n pi/(2K)} (Eq. mu_to_mu_tilde, n < M);
+// fftw_j = e^{-2 pi i j/K} (Eq. green_fft, j < K/2); sin theta_k with
+// theta_k = pi (k + 1/2)/K (the FFT nodes, k < K).
 __global__ void setup_tables_kernel(Params p, int kind, double lambda)
 {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    const int M = p.M;
-    if (n >= M) return;
-    double g;
-    if (kind == 0) {
-        const double q = CUDART_PI / (M + 1);
-        g = ((M - n + 1) * cos(q * n) + sin(q * n) * cos(q) / sin(q)) / (M + 1);
-    } else {
-        g = sinh(lambda * (1.0 - (double)n / M)) / sinh(lambda);
-    }
-    p.gker[n] = g;
+    const int M = p.M, K = p.K;
     double s, c;
-    sincospi((double)n / (2.0 * M), &s, &c);
-    p.twc[n] = make_double2(c, -s);
-    p.sinth[n] = sinpi((n + 0.5) / M);
-    if (n < M / 2) {
-        sincospi(2.0 * n / M, &s, &c);
+    if (n < M) {
+        double g;
+        if (kind == 0) {
+            const double q = CUDART_PI / (M + 1);
+            g = ((M - n + 1) * cos(q * n) + sin(q * n) * cos(q) / sin(q)) / (M + 1);
+        } else {
+            g = sinh(lambda * (1.0 - (double)n / M)) / sinh(lambda);
+        }
+        p.gker[n] = g;
+        sincospi((double)n / (2.0 * K), &s, &c);
+        p.twc[n] = make_double2(c, -s);
+    }
+    if (n < K) p.sinth[n] = sinpi((n + 0.5) / K);
+    if (n < K / 2) {
+        sincospi(2.0 * n / K, &s, &c);
         p.fftw[n] = make_double2(c, -s);
     }
 }
@@ -147,14 +151,14 @@ __device__ __forceinline__ double fermi(double E, double beta, double chem)
 
 // C_k = sum_{j <= k} sin(theta_j) f(a cos theta_j): the Chebyshev-Gauss weights
 // of Eq. d_seff2 summed from k = 0, so that the quadrature of the continuous
-// phase phi_k = phi_{M-1} + sum_{j >= k} inc_j becomes
-// phi_{M-1} C_{M-1} + sum_j inc_j C_j.  One thread: a plain running sum.
+// phase phi_k = phi_{K-1} + sum_{j >= k} inc_j becomes
+// phi_{K-1} C_{K-1} + sum_j inc_j C_j.  One thread: a plain running sum.
 __global__ void cumw_kernel(Params p)
 {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     double s = 0.0;
-    for (int k = 0; k < p.M; ++k) {
-        const double x = (k + 0.5) / p.M;
+    for (int k = 0; k < p.K; ++k) {
+        const double x = (k + 0.5) / p.K;
         s += sinpi(x) * fermi(p.a * cospi(x), p.beta, p.chem);
         p.cumw[k] = s;
     }
@@ -170,7 +174,8 @@ cudaError_t launch_build_hoppings(const Params& p, cudaStream_t s)
 
 cudaError_t launch_setup_tables(const Params& p, int kernel_kind, double lambda, cudaStream_t s)
 {
-    setup_tables_kernel<<<(p.M + 255) / 256, 256, 0, s>>>(p, kernel_kind, lambda);
+    const int n = p.K > p.M ? p.K : p.M;
+    setup_tables_kernel<<<(n + 255) / 256, 256, 0, s>>>(p, kernel_kind, lambda);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     cumw_kernel<<<1, 32, 0, s>>>(p);

@@ -166,6 +166,7 @@ extern "C" gfmc_status gfmc_delta_omega_noalloc(int L, const double* d_spins, do
     P.L = L;
     P.N = N;
     P.M = M;
+    P.K = M;  // the nodes of the paper's FFT
     P.nsteps = nsteps;
     P.ncta = ncta;
     P.t = t;

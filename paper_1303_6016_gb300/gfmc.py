@@ -46,7 +46,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("kernel", ctypes.c_int),
                 ("lorentz_lambda", ctypes.c_double), ("spectral_scale", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("chain_id", ctypes.c_uint32),
-                ("stream", ctypes.c_void_p), ("num_ctas", ctypes.c_int), ("recursion", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("num_ctas", ctypes.c_int), ("recursion", ctypes.c_int),
+                ("nodes", ctypes.c_int)]
 
 
 _lib = None
@@ -133,9 +134,11 @@ class Chain:
     def __init__(self, L: int, spins, t: float = 1.0, mu: float = -2.0, beta: float = 20.0,
                  M: int = 256, precision: str = "fp64", kernel: str = "jackson",
                  lorentz_lambda: float = 4.0, spectral_scale: float = 0.0, seed: int = 1,
-                 chain_id: int = 0, stream=None, num_ctas: int = 0, recursion: str = "unit_vectors"):
+                 chain_id: int = 0, stream=None, num_ctas: int = 0, recursion: str = "unit_vectors",
+                 nodes: int = 0):
         lib = load()
         self.L, self.N, self.M = int(L), int(L) ** 3, int(M)
+        self.K = int(nodes) if nodes else self.M  # Chebyshev nodes of G and of the quadrature
         self.t, self.mu, self.beta = float(t), float(mu), float(beta)
         self.precision = precision
         opt = Options()
@@ -150,6 +153,7 @@ class Chain:
         opt.stream = s if s else None
         opt.num_ctas = int(num_ctas)
         opt.recursion = RECURSIONS[recursion]
+        opt.nodes = int(nodes)
         sp = np.ascontiguousarray(spins, dtype=np.float64).reshape(-1, 2)
         if sp.shape[0] != self.N:
             raise ValueError(f"spins has {sp.shape[0]} rows, expected N = {self.N}")

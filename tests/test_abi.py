@@ -86,6 +86,22 @@ def test_create_rejects_bad_spins_and_scale(lib):
 
 
 @needs_nvcc
+@pytest.mark.parametrize("nodes", [3 * 64, 64 // 2, 4 * 64, -1])
+def test_create_rejects_bad_node_counts(lib, nodes):
+    """gfmc_options.nodes: 0, M or 2M; anything else is rejected before any device work."""
+    sp = inputs.uniform_sphere(4, 0)
+    opt = gfmc.Options()
+    lib.gfmc_default_options(ctypes.byref(opt))
+    assert opt.nodes == 0
+    opt.nodes = nodes
+    h = ctypes.c_void_p()
+    st = lib.gfmc_create(4, sp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 1.0, -2.0, 20.0, 64,
+                         ctypes.byref(opt), ctypes.byref(h))
+    assert st == gfmc.GFMC_EINVAL and "nodes" in lib.gfmc_last_error(None).decode()
+    assert not h.value
+
+
+@needs_nvcc
 def test_null_handle_is_rejected(lib):
     out = np.zeros(2)
     assert lib.gfmc_delta_omega(None, 0, 0.0, 0.0, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) \
