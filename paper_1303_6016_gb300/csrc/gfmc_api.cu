@@ -140,6 +140,40 @@ gfmc_status plan_tiles(gfmc_ctx* h, int ncta, std::vector<int>& start, std::vect
     return GFMC_OK;
 }
 
+// The sites the stencil of CTA c reads -- its tile and every neighbour of a
+// tile site -- as runs of consecutive site indices (first, length) in
+// increasing order: wins[ptr[c] .. ptr[c+1]).  max_len receives the largest
+// number of sites of one CTA.
+void plan_windows(int L, int ncta, const std::vector<int>& start, std::vector<int>& ptr, std::vector<int2>& wins,
+                  int& max_len)
+{
+    ptr.assign(1, 0);
+    wins.clear();
+    max_len = 0;
+    std::vector<int> sites;
+    for (int c = 0; c < ncta; ++c) {
+        sites.clear();
+        for (int i = start[c]; i < start[c + 1]; ++i) {
+            const int x = i % L, y = (i / L) % L, z = i / (L * L);
+            sites.push_back(i);
+            sites.push_back((x + 1) % L + L * (y + L * z));
+            sites.push_back((x + L - 1) % L + L * (y + L * z));
+            sites.push_back(x + L * ((y + 1) % L + L * z));
+            sites.push_back(x + L * ((y + L - 1) % L + L * z));
+            sites.push_back(x + L * (y + L * ((z + 1) % L)));
+            sites.push_back(x + L * (y + L * ((z + L - 1) % L)));
+        }
+        std::sort(sites.begin(), sites.end());
+        sites.erase(std::unique(sites.begin(), sites.end()), sites.end());
+        for (size_t q = 0; q < sites.size(); ++q) {
+            if (q > 0 && sites[q] == sites[q - 1] + 1) ++wins.back().y;
+            else wins.push_back(make_int2(sites[q], 1));
+        }
+        ptr.push_back((int)wins.size());
+        max_len = std::max(max_len, (int)sites.size());
+    }
+}
+
 gfmc_status ensure_trace(gfmc_ctx* h, long long n)
 {
     if (n <= h->trace_cap) return GFMC_OK;
@@ -375,6 +409,20 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
     h->multi_site = (long long)ncta * gfmc::kThreads < N;
     std::vector<int> tstart, nptr, nidx;
     if ((st = plan_tiles(h, ncta, tstart, nptr, nidx)) != GFMC_OK) return bail(st);
+    // FP64 single-chain engine: prefetch the sites each CTA reads into shared
+    // memory when its runs fit beside the staged Gram rows
+    std::vector<int> wptr;
+    std::vector<int2> wins;
+    int win_max = 0;
+    bool prefetch = false;
+    if (h->precision == GFMC_PREC_FP64 && !h->multi_site) {
+        plan_windows(L, ncta, tstart, wptr, wins, win_max);
+        int dev_smem = 0, static_smem = 0;
+        if ((e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device)) != cudaSuccess ||
+            (e = gfmc::engine_static_smem_f64(&static_smem)) != cudaSuccess)
+            return bail(cuda_fail(h, e, "querying shared memory"));
+        prefetch = gfmc::single_smem_bytes(K, GFMC_PREC_FP64, win_max) + static_smem <= dev_smem;
+    }
 
     Params& P = h->P;
     P.L = L;
@@ -414,6 +462,20 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
         (e = dalloc(h, &P.err, 4)) != cudaSuccess || (e = dalloc(h, &h->d_nacc, 1)) != cudaSuccess ||
         (e = dalloc(h, &h->d_nmag, 1)) != cudaSuccess)
         return bail(cuda_fail(h, e, "allocating chain state"));
+    if (prefetch) {
+        int* d_wp = nullptr;
+        int2* d_w = nullptr;
+        if ((e = dalloc(h, &d_wp, wptr.size())) != cudaSuccess || (e = dalloc(h, &d_w, wins.size())) != cudaSuccess ||
+            (e = cudaMemcpyAsync(d_wp, wptr.data(), sizeof(int) * wptr.size(), cudaMemcpyHostToDevice, h->stream)) !=
+                cudaSuccess ||
+            (e = cudaMemcpyAsync(d_w, wins.data(), sizeof(int2) * wins.size(), cudaMemcpyHostToDevice, h->stream)) !=
+                cudaSuccess)
+            return bail(cuda_fail(h, e, "uploading the prefetch plan"));
+        P.win_ptr = d_wp;
+        P.win = d_w;
+        P.win_max = win_max;
+        P.prefetch = 1;
+    }
     P.rbuf = rb;
     h->cap_ncta = ncta;
     P.tile_start = d_ts;

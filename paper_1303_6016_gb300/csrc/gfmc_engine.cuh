@@ -219,6 +219,18 @@ __device__ __forceinline__ void nbar_arrive(int id, int n)
     asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared (L2 only), and the wait for all
+// of this thread's copies.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 // wait_neighbours for one warp: the lanes poll the neighbour CTAs' flags
 // (acquire) in parallel; true in every lane when all reached `target`, false
 // when an error was recorded or this warp's wait ran out of its budget.
@@ -1273,6 +1285,24 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
     int nb[6];
 #pragma unroll
     for (int d = 0; d < 6; ++d) nb[d] = active ? nbr_site(i, d, L) : 0;
+    // FP64 engine with prefetch: where each neighbour sits in the CTA's runs
+    // of prefetched sites (the host plans the runs to hold every neighbour)
+    [[maybe_unused]] int nbo[6] = {0, 0, 0, 0, 0, 0};
+    if constexpr (VARIANT == 0 && sizeof(R) == 8 && NT > kThreads) {
+        if (p.prefetch && active) {
+            const int wb = p.win_ptr[cta], we = p.win_ptr[cta + 1];
+#pragma unroll
+            for (int d = 0; d < 6; ++d) {
+                int off = 0, at = 0;
+                for (int w = wb; w < we; ++w) {
+                    const int2 r = p.win[w];
+                    if (nb[d] >= r.x && nb[d] < r.x + r.y) at = off + nb[d] - r.x;
+                    off += r.y;
+                }
+                nbo[d] = at;
+            }
+        }
+    }
 
     R2* buf0 = vec_smem ? vec_smem : (R2*)p.rbuf;
     R2* buf1 = buf0 + (size_t)NV * N;
@@ -1470,6 +1500,25 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                         }
                         if (m <= p.nsteps) {
                             ok = warp_wait_neighbours(p, cta, phase + (unsigned)m, 100 + m, lane);
+                            if (ok && p.prefetch) {
+                                // r_m of every site the stencil of step m reads, into shared memory
+                                __syncwarp();
+                                const R2* src = (m & 1) ? buf1 : buf0;
+                                double2* wsm = dyn + 4 * kVec * kStage;
+                                const int wb = p.win_ptr[cta], we = p.win_ptr[cta + 1], W = p.win_max;
+                                int off = 0;
+                                for (int w = wb; w < we; ++w) {
+                                    const int2 r = p.win[w];
+                                    for (int v = 0; v < kVec; ++v) {
+                                        const R2* sv = src + (size_t)v * N + r.x;
+                                        double2* dv = wsm + v * W + off;
+                                        for (int c = lane; c < r.y; c += 32) cp_async16(dv + c, sv + c);
+                                    }
+                                    off += r.y;
+                                }
+                                cp_async_wait_all();
+                                __syncwarp();
+                            }
                             if (lane == 0) s_go = ok ? 1 : 0;
                             nbar_arrive(3, NT);
                         }
@@ -1482,7 +1531,20 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                         const R2* rd = (m & 1) ? buf1 : buf0;  // r_m of every site
                         R2* wr = (m & 1) ? buf0 : buf1;        // receives r_{m+1}; held r_{m-1}
                         R2 nxt[kVec];
-                        if (active) {
+                        if (active && p.prefetch) {
+                            // h holds 2 Htilde: r_{m+1} = -r_{m-1} + sum_d (2 h_d) r_m(nb_d), FMAs only;
+                            // r_m of the neighbours from the prefetched runs in shared memory
+                            const double2* wsm = dyn + 4 * kVec * kStage;
+                            const int W = p.win_max;
+    #pragma unroll
+                            for (int v = 0; v < kVec; ++v) {
+                                R2 acc = c_make<R2>(-prv[v].x, -prv[v].y);
+    #pragma unroll
+                                for (int d = 0; d < 6; ++d) c_fma(acc, h[d], wsm[v * W + nbo[d]]);
+                                nxt[v] = acc;
+                                if (m < p.nsteps) stcg2(wr + (size_t)v * N + i, nxt[v]);
+                            }
+                        } else if (active) {
                             // h holds 2 Htilde: r_{m+1} = -r_{m-1} + sum_d (2 h_d) r_m(nb_d), FMAs only
     #pragma unroll
                             for (int v = 0; v < kVec; ++v) {

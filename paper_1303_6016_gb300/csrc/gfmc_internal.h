@@ -55,6 +55,15 @@ struct Params {
     const int* tile_start;  // [ncta + 1]
     const int* nbr_ptr;     // [ncta + 1]
     const int* nbr_idx;     // [nbr_ptr[ncta]]
+    // FP64 single-chain engine: the sites a CTA's stencil reads (its tile and
+    // the tile's neighbours) as runs of consecutive sites, win[win_ptr[c] ..
+    // win_ptr[c+1]) = (first site, length); win_max = the largest total.  With
+    // prefetch set, the helper warp copies these runs of r_m into shared
+    // memory while the compute warps form the Gram sums of the step before.
+    const int* win_ptr;     // [ncta + 1]
+    const int2* win;        // [win_ptr[ncta]]
+    int win_max;
+    int prefetch;
 
     // synchronisation
     unsigned* flags;  // [ncta]  completed stencil phases of each CTA
@@ -128,7 +137,9 @@ cudaError_t cluster_static_smem(int precision, int* out);
 cudaError_t server_max_ctas(int smem, int* out);
 // K: the number of Chebyshev nodes (the FFT buffer of the tail holds K double2)
 int engine_smem_bytes(int K);
-int single_smem_bytes(int K, int precision);
+int single_smem_bytes(int K, int precision, int win_max = 0);
+// static shared memory of the FP64 single-chain engine (bytes)
+cudaError_t engine_static_smem_f64(int* out);
 cudaError_t engine_max_ctas(int precision, int K, int* out);
 cudaError_t launch_build_hoppings(const Params& p, cudaStream_t s);
 cudaError_t launch_setup_tables(const Params& p, int kernel_kind, double lambda, cudaStream_t s);

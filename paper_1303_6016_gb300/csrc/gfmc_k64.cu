@@ -6,7 +6,7 @@ namespace gfmc {
 template <int NV>
 static cudaError_t launch_nv_f64(const Params& p, cudaStream_t s)
 {
-    const int smem = single_smem_bytes(p.K, 0);
+    const int smem = single_smem_bytes(p.K, 0, p.prefetch ? p.win_max : 0);
     cudaError_t e = cudaFuncSetAttribute(gfmc_engine<double, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     Params q = p;
@@ -20,6 +20,14 @@ cudaError_t launch_engine_f64(const Params& p, cudaStream_t s) { return launch_n
 cudaError_t launch_engine_f64(const Params& p, int nv, cudaStream_t s)
 {
     return nv == 2 ? launch_nv_f64<2>(p, s) : launch_nv_f64<kVec>(p, s);
+}
+
+cudaError_t engine_static_smem_f64(int* out)
+{
+    cudaFuncAttributes a;
+    const cudaError_t e = cudaFuncGetAttributes(&a, gfmc_engine<double, kVec>);
+    if (e == cudaSuccess) *out = (int)a.sharedSizeBytes;
+    return e;
 }
 
 cudaError_t engine_max_ctas_f64(int K, int* out)

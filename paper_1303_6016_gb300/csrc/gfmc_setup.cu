@@ -36,12 +36,13 @@ int engine_smem_bytes(int K)
 }
 
 // Dynamic shared memory of the one-site-per-thread engine: the FFT buffer or,
-// for FP64, the 28 staged rows of its Gram sums (r_m, r_{m+1} and -i times each).
-int single_smem_bytes(int K, int precision)
+// for FP64, the 28 staged rows of its Gram sums (r_m, r_{m+1} and -i times
+// each) followed by the prefetched runs of r_m (7 vectors x win_max sites).
+int single_smem_bytes(int K, int precision, int win_max)
 {
     if (precision != 0) return engine_smem_bytes(K);
     const int fft = K * (int)sizeof(double2);
-    const int stage = 4 * kVec * kStage * (int)sizeof(double2);
+    const int stage = (4 * kVec * kStage + kVec * win_max) * (int)sizeof(double2);
     return fft > stage ? fft : stage;
 }
 
@@ -152,16 +153,37 @@ __device__ __forceinline__ double fermi(double E, double beta, double chem)
 // C_k = sum_{j <= k} sin(theta_j) f(a cos theta_j): the Chebyshev-Gauss weights
 // of Eq. d_seff2 summed from k = 0, so that the quadrature of the continuous
 // phase phi_k = phi_{K-1} + sum_{j >= k} inc_j becomes
-// phi_{K-1} C_{K-1} + sum_j inc_j C_j.  One thread: a plain running sum.
-__global__ void cumw_kernel(Params p)
+// phi_{K-1} C_{K-1} + sum_j inc_j C_j.  One block of kScanThreads threads:
+// thread t sums its contiguous chunk of nodes in order, thread 0 adds the
+// chunk totals in order, and each thread adds its offset (a fixed order, so
+// the table is the same on every run).
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads) cumw_kernel(Params p)
 {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    __shared__ double tot[kScanThreads];
+    const int t = threadIdx.x, K = p.K;
+    const int chunk = (K + kScanThreads - 1) / kScanThreads;
+    const int k0 = min(K, t * chunk), k1 = min(K, k0 + chunk);
     double s = 0.0;
-    for (int k = 0; k < p.K; ++k) {
-        const double x = (k + 0.5) / p.K;
+    for (int k = k0; k < k1; ++k) {
+        const double x = (k + 0.5) / K;
         s += sinpi(x) * fermi(p.a * cospi(x), p.beta, p.chem);
         p.cumw[k] = s;
     }
+    tot[t] = s;
+    __syncthreads();
+    if (t == 0) {
+        double run = 0.0;
+        for (int q = 0; q < kScanThreads; ++q) {
+            const double v = tot[q];
+            tot[q] = run;
+            run += v;
+        }
+    }
+    __syncthreads();
+    const double off = tot[t];
+    for (int k = k0; k < k1; ++k) p.cumw[k] += off;
 }
 
 }  // namespace
@@ -178,7 +200,7 @@ cudaError_t launch_setup_tables(const Params& p, int kernel_kind, double lambda,
     setup_tables_kernel<<<(n + 255) / 256, 256, 0, s>>>(p, kernel_kind, lambda);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    cumw_kernel<<<1, 32, 0, s>>>(p);
+    cumw_kernel<<<1, kScanThreads, 0, s>>>(p);
     return cudaGetLastError();
 }
 
