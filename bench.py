@@ -275,9 +275,31 @@ def run_batching(stream, steps, warmup, updates, flush, recursion="unit_vectors"
     n = len(chains)
     nv = 2 if recursion == "proposal" else 7
     _, bytes_u = zip(*[update_work(int(L), 1024, 4, nv) for L in Ls])
+    graph = None
+    if len(plan) == 1:
+        # the same step captured once in a CUDA graph (gfmc_plan_*) and replayed
+        from paper_1303_6016_gb300 import gfmc
+        w, tc = plan[0]
+        order = list(w)
+        with gfmc.Plan([chains[i] for i in order], [updates] * n, list(tc), schedule="teams") as gp:
+            gp.launch(warmup)
+            gp.sync(trace=False)
+            perg = []
+            for k in range(steps):
+                flush.fill_(k)
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.record()
+                gp.launch(1)
+                e.record()
+                e.synchronize()
+                perg.append(s.elapsed_time(e))
+            gp.sync(trace=False)
+        graph = {"value": n * updates * steps / (sum(perg) / 1000.0), "unit": UNIT,
+                 "ms_per_step": sum(perg) / steps,
+                 "note": "one CUDA graph launch per step (gfmc_plan_launch), no host work between steps"}
     for ch in chains:
         ch.close()
-    return {"value": n * updates * steps / (total / 1000.0), "unit": UNIT, "chains": n,
+    return {"value": n * updates * steps / (total / 1000.0), "unit": UNIT, "chains": n, "graph": graph,
             "updates_per_chain_per_step": updates, "ms_per_step": total / steps,
             "launches_per_step": len(plan), "team_ctas_by_L": {str(k): sorted(v) for k, v in sorted(teams.items())},
             "lattice_counts": {str(int(L)): int((Ls == L).sum()) for L in sorted(set(Ls.tolist()))},
@@ -310,10 +332,30 @@ def run_batching_clusters(stream, steps, warmup, updates, flush):
     total = sum(per)
     n = len(chains)
     by_L = {str(int(L)): c for L, c in sorted(zip(Ls, runner.cluster_ctas))}
+    # the same steps captured once in a CUDA graph (gfmc_plan_*) and replayed
+    from paper_1303_6016_gb300 import gfmc
+    with gfmc.Plan(chains, [updates] * n, runner.cluster_ctas, schedule="clusters") as plan:
+        plan.launch(warmup)
+        plan.sync(trace=False)
+        perg = []
+        for k in range(steps):
+            flush.fill_(k)
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            plan.launch(1)
+            e.record()
+            e.synchronize()
+            perg.append(s.elapsed_time(e))
+        plan.sync(trace=False)
+    totg = sum(perg)
     for ch in chains:
         ch.close()
+    _, bytes_u = zip(*[update_work(int(L), 1024, 4, 2) for L in Ls])
     return {"value": n * updates * steps / (total / 1000.0), "unit": UNIT, "chains": n,
             "updates_per_chain_per_step": updates, "ms_per_step": total / steps,
+            "stencil_gbs": sum(bytes_u) * updates / (total / steps / 1000.0) / 1e9,
+            "graph": {"value": n * updates * steps / (totg / 1000.0), "unit": UNIT, "ms_per_step": totg / steps,
+                      "note": "one CUDA graph launch per step (gfmc_plan_launch), no host work between steps"},
             "cluster_ctas_by_L": by_L, "recursion": "proposal",
             "config": "the batching workload (64 chains, L from {8,12,16,24,32}, M = 1024, FP32-mixed), "
                       "each chain on one thread-block cluster holding its lattice in shared memory"}

@@ -212,6 +212,47 @@ gfmc_status gfmc_run_clusters(gfmc_t* chains, int n_chains, const int64_t* n_upd
 gfmc_status gfmc_cluster_min_ctas(int L, int M, int precision, int* cluster_ctas);
 
 /* ------------------------------------------------------------------------
+ * Batch plans: one step of a batch of independent chains (Algorithm 1's
+ * sampling on many chains, Sec. 3.2), captured once in a CUDA graph and
+ * replayed step after step with no host work per step.
+ * ------------------------------------------------------------------------ */
+typedef struct gfmc_plan_ctx* gfmc_plan_t;
+
+/* How a plan places its chains: GFMC_SCHEDULE_TEAMS -- one cooperative launch,
+ * chain c on a team of ctas[c] CTAs, as gfmc_run_batch (every precision and
+ * recursion, the chains of one precision); GFMC_SCHEDULE_CLUSTERS -- chain c on
+ * a thread-block cluster of ctas[c] CTAs holding its lattice, as
+ * gfmc_run_clusters (chains on the proposal's vectors). */
+enum { GFMC_SCHEDULE_TEAMS = 0, GFMC_SCHEDULE_CLUSTERS = 1 };
+
+/* Capture one step -- n_updates[c] >= 1 sequential updates of every chain c
+ * from where its previous step ended -- in a CUDA graph: a set-up node that
+ * hands each chain its next block of update numbers, then the launches (the
+ * cluster groups as parallel branches).  The arguments are checked as by
+ * gfmc_run_batch / gfmc_run_clusters.  The chains' counters are taken now; from
+ * here until gfmc_plan_destroy the chains belong to the plan and must not be
+ * used by any other call (a chain in a plan is refused by gfmc_server_submit
+ * and by another plan).  GFMC_ECUDA if the device cannot capture the launches. */
+gfmc_status gfmc_plan_create(gfmc_t* chains, int n_chains, const int64_t* n_updates, const int* ctas, int schedule,
+                             gfmc_plan_t* out);
+
+/* Enqueue n_steps >= 0 steps (graph launches) on stream (cudaStream_t, NULL:
+ * the legacy default stream) and return at once.  Steps pending from an
+ * earlier call must be on the same stream (GFMC_EINVAL otherwise). */
+gfmc_status gfmc_plan_launch(gfmc_plan_t plan, int n_steps, void* stream);
+
+/* Wait for the pending steps, advance each chain's counter by the updates
+ * they ran, and copy out the last step's results as gfmc_run_batch does
+ * (arrays indexed by the chain's position in gfmc_plan_create; any pointer
+ * may be NULL).  A device error of a chain (GFMC_ETIMEOUT, GFMC_ENUMERIC) is
+ * returned here and stays recorded: later steps of that chain end at once. */
+gfmc_status gfmc_plan_sync(gfmc_plan_t plan, uint64_t* n_accepted, uint8_t** decisions, double** d_omega_trace,
+                           double** magnetization, int64_t* n_mag);
+
+/* Wait for pending steps, free the plan and release its chains.  NULL is ignored. */
+void gfmc_plan_destroy(gfmc_plan_t plan);
+
+/* ------------------------------------------------------------------------
  * Serving loop: a device-resident request loop over many chains.
  * A server is one persistent launch whose CTAs are split into slots.  Each
  * slot runs the jobs posted to it -- "continue this chain by n updates",

@@ -44,6 +44,7 @@ struct gfmc_ctx {
     // team variant of the engine (several sites per thread) as a one-job launch
     bool multi_site = false;
     bool in_server = false;  // submitted to a server slot and not yet polled done
+    bool in_plan = false;    // part of a batch plan (gfmc_plan_create .. gfmc_plan_destroy)
     gfmc::TeamJob* d_job = nullptr;
     // tile plan of this chain for a team of team_tc CTAs (batch launches)
     int team_tc = 0;
@@ -1019,6 +1020,369 @@ gfmc_status gfmc_run_clusters(gfmc_t* chains, int n_chains, const int64_t* n_upd
 }
 
 // ---------------------------------------------------------------------------
+// batch plans: one step of a batch captured once in a CUDA graph
+// ---------------------------------------------------------------------------
+
+namespace gfmc {
+namespace {
+
+// The first node of a captured step: job j takes the next block of updates of
+// its chain (upd0 = the chain's device counter, which then advances by the
+// job's n_updates) and clears the words a launch starts from (the team's
+// neighbour flags and grid barrier).  Error words are not cleared: a recorded
+// error stays, and every later step of the plan ends at its first wait.
+__global__ void plan_prepare_kernel(TeamJob* jobs, int njobs, unsigned long long* counters, const long long* n_upd)
+{
+    const int j = blockIdx.x;
+    if (j >= njobs) return;
+    Params& P = jobs[j].p;
+    for (int c = threadIdx.x; c < P.ncta; c += blockDim.x) P.flags[c] = 0u;
+    if (threadIdx.x == 0) {
+        P.bar[0] = 0u;
+        P.bar[1] = 0u;
+        P.upd0 = counters[j];
+        counters[j] += (unsigned long long)n_upd[j];
+    }
+}
+
+}  // namespace
+}  // namespace gfmc
+
+struct gfmc_plan_ctx {
+    int device = 0, schedule = 0;
+    std::vector<gfmc_ctx*> chains;  // in job-table order
+    std::vector<int> caller;        // job-table position -> the caller's chain index
+    std::vector<int64_t> n_upd;     // per job-table position
+    gfmc::TeamJob* d_jobs = nullptr;
+    unsigned long long* d_counters = nullptr;
+    long long* d_nupd = nullptr;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t last = nullptr;
+    long long pending = 0;  // steps launched since the last gfmc_plan_sync
+};
+
+void gfmc_plan_destroy(gfmc_plan_t p)
+{
+    if (!p) return;
+    cudaSetDevice(p->device);
+    if (p->last) cudaStreamSynchronize(p->last);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    for (auto s : p->streams)
+        if (s) cudaStreamDestroy(s);
+    for (auto e : p->events)
+        if (e) cudaEventDestroy(e);
+    cudaFree(p->d_jobs);
+    cudaFree(p->d_counters);
+    cudaFree(p->d_nupd);
+    for (auto h : p->chains) h->in_plan = false;
+    delete p;
+}
+
+gfmc_status gfmc_plan_create(gfmc_t* chains, int n_chains, const int64_t* n_updates, const int* ctas, int schedule,
+                             gfmc_plan_t* out)
+{
+    if (!out) return fail(nullptr, GFMC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!chains || n_chains < 1 || !n_updates || !ctas)
+        return fail(nullptr, GFMC_EINVAL, "need chains, n_chains >= 1, n_updates and ctas");
+    if (schedule != GFMC_SCHEDULE_TEAMS && schedule != GFMC_SCHEDULE_CLUSTERS)
+        return fail(nullptr, GFMC_EINVAL, "unknown schedule %d", schedule);
+    const bool clusters = schedule == GFMC_SCHEDULE_CLUSTERS;
+    const int prec = chains[0] ? chains[0]->precision : -1;
+    const int dev = chains[0] ? chains[0]->device : -1;
+    for (int c = 0; c < n_chains; ++c) {
+        gfmc_ctx* h = chains[c];
+        if (!h) return fail(nullptr, GFMC_EINVAL, "chain %d is NULL", c);
+        for (int d = 0; d < c; ++d)
+            if (chains[d] == h) return fail(nullptr, GFMC_EINVAL, "chain %d appears twice", c);
+        if (h->in_plan || h->in_server)
+            return fail(nullptr, GFMC_EINVAL, "chain %d already belongs to a plan or has a server job", c);
+        if (h->device != dev) return fail(nullptr, GFMC_EINVAL, "chain %d lives on another device", c);
+        if (n_updates[c] < 1) return fail(nullptr, GFMC_EINVAL, "n_updates[%d] < 1", c);
+        const int C = ctas[c];
+        if (clusters) {
+            if (h->recursion != GFMC_RECURSION_PROPOSAL)
+                return fail(nullptr, GFMC_EINVAL, "chain %d: clusters run the recursion on the proposal's vectors", c);
+            if (C != 1 && C != 2 && C != 4 && C != 8 && C != 16)
+                return fail(nullptr, GFMC_EINVAL, "ctas[%d] = %d not in {1, 2, 4, 8, 16}", c, C);
+            if (h->L % C != 0)
+                return fail(nullptr, GFMC_EINVAL, "chain %d: %d z-planes do not split over %d CTAs", c, h->L, C);
+        } else {
+            if (h->precision != prec) return fail(nullptr, GFMC_EINVAL, "chain %d has another precision", c);
+            if (C < 1 || C > std::min(h->N, 1024))
+                return fail(nullptr, GFMC_EINVAL, "ctas[%d] = %d outside [1, %d]", c, C, std::min(h->N, 1024));
+        }
+    }
+    cudaError_t e;
+    if ((e = cudaSetDevice(dev)) != cudaSuccess) return cuda_fail(nullptr, e, "cudaSetDevice");
+    int dev_smem = 0;
+    if ((e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess)
+        return cuda_fail(nullptr, e, "querying shared memory");
+
+    gfmc_plan_ctx* p = new (std::nothrow) gfmc_plan_ctx;
+    if (!p) return fail(nullptr, GFMC_ENOMEM, "host allocation failed");
+    p->device = dev;
+    p->schedule = schedule;
+    auto bail = [&](gfmc_status st) {
+        gfmc_plan_destroy(p);
+        return st;
+    };
+
+    // the jobs, in launch order, with their launch groups
+    struct Group {
+        int prec, C, first, count;
+        size_t vec_bytes;
+    };
+    std::vector<Group> groups;
+    std::vector<gfmc::TeamJob> jobs;
+    auto make_params = [&](gfmc_ctx* h, int c, int C) {
+        Params P = h->P;
+        P.ncta = C;
+        P.mode = gfmc::MODE_SWEEP;
+        P.upd0 = h->counter;
+        P.n_updates = n_updates[c];
+        P.dec_out = h->d_dec;
+        P.domega_out = h->d_dom;
+        P.maxinc_out = h->d_maxinc;
+        P.mag_out = h->d_mag;
+        P.n_acc = h->d_nacc;
+        P.n_mag = h->d_nmag;
+        P.budget = h->budget;
+        P.stall = 0;
+        return P;
+    };
+    int team_grid = 0, team_smem = 0, team_vec = 0;
+    if (clusters) {
+        int static_smem[2] = {0, 0};
+        if ((e = gfmc::cluster_static_smem(GFMC_PREC_FP64, &static_smem[0])) != cudaSuccess ||
+            (e = gfmc::cluster_static_smem(GFMC_PREC_FP32_MIXED, &static_smem[1])) != cudaSuccess)
+            return bail(cuda_fail(nullptr, e, "querying shared memory"));
+        std::vector<std::pair<int, int>> keys;  // (precision, C) in order of first appearance
+        for (int c = 0; c < n_chains; ++c) {
+            const std::pair<int, int> k(chains[c]->precision, ctas[c]);
+            if (std::find(keys.begin(), keys.end(), k) == keys.end()) keys.push_back(k);
+        }
+        // largest clusters first: they are the hardest to place and, per chain, the longest
+        std::stable_sort(keys.begin(), keys.end(), [](auto a, auto b) { return a.second > b.second; });
+        for (const auto& k : keys) {
+            Group g{k.first, k.second, (int)jobs.size(), 0, 0};
+            for (int c = 0; c < n_chains; ++c) {
+                gfmc_ctx* h = chains[c];
+                if (h->precision != k.first || ctas[c] != k.second) continue;
+                const int C = ctas[c], T = h->N / C;
+                if ((unsigned long long)h->N * (unsigned long long)T >= (1ull << 32))
+                    return bail(fail(nullptr, GFMC_EINVAL, "chain %d: %d sites per CTA are too many", c, T));
+                const int st_smem = static_smem[h->precision == GFMC_PREC_FP64 ? 0 : 1];
+                if (!cluster_fits(h->L, h->K, C, h->precision, dev_smem, st_smem))
+                    return bail(fail(nullptr, GFMC_EINVAL, "chain %d does not fit a cluster of %d CTAs", c, C));
+                g.vec_bytes = std::max(g.vec_bytes, cluster_dyn_bytes(h->L, h->K, C, h->precision));
+                gfmc_status st = ensure_trace(h, n_updates[c]);
+                if (st == GFMC_OK) st = ensure_team_capacity(h, C);
+                if (st != GFMC_OK) return bail(fail(nullptr, st, "chain %d: %s", c, h->err.c_str()));
+                Params P = make_params(h, c, C);
+                P.divT = (unsigned)(((1ull << 32) + (unsigned long long)T - 1) / (unsigned long long)T);
+                P.nv = 2;
+                gfmc::TeamJob j{};
+                j.p = P;
+                j.cta0 = 0;
+                j.vec_smem = 1;
+                jobs.push_back(j);
+                p->chains.push_back(h);
+                p->caller.push_back(c);
+                p->n_upd.push_back(n_updates[c]);
+                ++g.count;
+            }
+            int active = 0;
+            if ((e = gfmc::cluster_max_active(g.prec, g.C, (int)g.vec_bytes, &active)) != cudaSuccess)
+                return bail(cuda_fail(nullptr, e, "cluster occupancy"));
+            if (active < 1)
+                return bail(fail(nullptr, GFMC_EINVAL, "a cluster of %d CTAs with %zu B each cannot be scheduled", g.C,
+                                 g.vec_bytes));
+            groups.push_back(g);
+        }
+    } else {
+        const size_t vsz = prec == GFMC_PREC_FP64 ? sizeof(double2) : sizeof(float2);
+        int work = 0;
+        for (int c = 0; c < n_chains; ++c) work = std::max(work, gfmc::engine_smem_bytes(chains[c]->K));
+        const int reserve = 20 * 1024;
+        size_t vec_bytes = 0;
+        std::vector<int> resident(n_chains, 0);
+        for (int c = 0; c < n_chains; ++c) {
+            const int nvc = chains[c]->recursion == GFMC_RECURSION_PROPOSAL ? 2 : gfmc::kVec;
+            const size_t vb = 2 * (size_t)nvc * chains[c]->N * vsz;
+            if (ctas[c] == 1 && vb + work + reserve <= (size_t)dev_smem) {
+                resident[c] = 1;
+                vec_bytes = std::max(vec_bytes, (vb + 255) & ~(size_t)255);
+            }
+        }
+        team_vec = (int)vec_bytes;
+        team_smem = (int)vec_bytes + work;
+        for (int c = 0; c < n_chains; ++c) team_grid += ctas[c];
+        int maxc = 0;
+        if ((e = gfmc::team_max_ctas(prec, team_smem, &maxc)) != cudaSuccess)
+            return bail(cuda_fail(nullptr, e, "team occupancy"));
+        if (team_grid > maxc)
+            return bail(fail(nullptr, GFMC_EINVAL, "the batch needs %d co-resident CTAs, the device holds %d", team_grid,
+                             maxc));
+        int cta0 = 0;
+        for (int c = 0; c < n_chains; ++c) {
+            gfmc_ctx* h = chains[c];
+            const int tc = ctas[c];
+            gfmc_status st = ensure_trace(h, n_updates[c]);
+            if (st == GFMC_OK) st = ensure_team_capacity(h, tc);
+            if (st == GFMC_OK) st = use_team_plan(h, tc);
+            if (st != GFMC_OK) return bail(fail(nullptr, st, "chain %d: %s", c, h->err.c_str()));
+            Params P = make_params(h, c, tc);
+            P.tile_start = h->d_team_tiles;
+            P.nbr_ptr = h->d_team_nptr;
+            P.nbr_idx = h->d_team_nidx;
+            P.nv = h->recursion == GFMC_RECURSION_PROPOSAL ? 2 : gfmc::kVec;
+            gfmc::TeamJob j{};
+            j.p = P;
+            j.cta0 = cta0;
+            j.vec_smem = resident[c];
+            jobs.push_back(j);
+            cta0 += tc;
+            p->chains.push_back(h);
+            p->caller.push_back(c);
+            p->n_upd.push_back(n_updates[c]);
+        }
+    }
+    const int nj = (int)jobs.size();
+    for (auto h : p->chains) h->in_plan = true;
+
+    // device tables and cleared status words
+    std::vector<unsigned long long> ctr(nj);
+    std::vector<long long> nu(nj);
+    for (int j = 0; j < nj; ++j) {
+        ctr[j] = p->chains[j]->counter;
+        nu[j] = p->n_upd[j];
+    }
+    if ((e = cudaMalloc(&p->d_jobs, sizeof(gfmc::TeamJob) * nj)) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_counters, sizeof(unsigned long long) * nj)) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_nupd, sizeof(long long) * nj)) != cudaSuccess ||
+        (e = cudaMemcpy(p->d_jobs, jobs.data(), sizeof(gfmc::TeamJob) * nj, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(p->d_counters, ctr.data(), sizeof(unsigned long long) * nj, cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = cudaMemcpy(p->d_nupd, nu.data(), sizeof(long long) * nj, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(cuda_fail(nullptr, e, "allocating the plan's tables"));
+    for (auto h : p->chains)
+        if ((e = cudaMemset(h->P.err, 0, sizeof(int) * 4)) != cudaSuccess)
+            return bail(cuda_fail(nullptr, e, "clearing status words"));
+
+    // capture one step: prepare node, then the launches (cluster groups as parallel branches)
+    cudaStream_t cs = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(cuda_fail(nullptr, e, "creating a capture stream"));
+    p->streams.push_back(cs);
+    if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+        return bail(cuda_fail(nullptr, e, "starting the capture"));
+    cudaError_t ce = cudaSuccess;
+    gfmc::plan_prepare_kernel<<<nj, 128, 0, cs>>>(p->d_jobs, nj, p->d_counters, p->d_nupd);
+    ce = cudaGetLastError();
+    if (ce == cudaSuccess && !clusters) {
+        ce = prec == GFMC_PREC_FP64 ? gfmc::launch_team_ex_f64(p->d_jobs, nj, team_grid, team_vec, team_smem, cs)
+                                    : gfmc::launch_team_ex_f32(p->d_jobs, nj, team_grid, team_vec, team_smem, cs);
+    } else if (ce == cudaSuccess) {
+        cudaEvent_t fork = nullptr;
+        ce = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        if (ce == cudaSuccess) {
+            p->events.push_back(fork);
+            ce = cudaEventRecord(fork, cs);
+        }
+        for (size_t k = 0; k < groups.size() && ce == cudaSuccess; ++k) {
+            const Group& g = groups[k];
+            cudaStream_t gs = nullptr;
+            cudaEvent_t join = nullptr;
+            if ((ce = cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking)) != cudaSuccess) break;
+            p->streams.push_back(gs);
+            if ((ce = cudaStreamWaitEvent(gs, fork, 0)) != cudaSuccess) break;
+            ce = g.prec == GFMC_PREC_FP64
+                     ? gfmc::launch_cluster_f64(p->d_jobs + g.first, g.count, g.C, (int)g.vec_bytes, (int)g.vec_bytes, gs)
+                     : gfmc::launch_cluster_f32(p->d_jobs + g.first, g.count, g.C, (int)g.vec_bytes, (int)g.vec_bytes, gs);
+            if (ce != cudaSuccess) break;
+            if ((ce = cudaEventCreateWithFlags(&join, cudaEventDisableTiming)) != cudaSuccess) break;
+            p->events.push_back(join);
+            if ((ce = cudaEventRecord(join, gs)) != cudaSuccess) break;
+            ce = cudaStreamWaitEvent(cs, join, 0);
+        }
+    }
+    e = cudaStreamEndCapture(cs, &p->graph);
+    if (ce != cudaSuccess) return bail(cuda_fail(nullptr, ce, "capturing the step"));
+    if (e != cudaSuccess) return bail(cuda_fail(nullptr, e, "ending the capture"));
+    if ((e = cudaGraphInstantiate(&p->exec, p->graph, 0)) != cudaSuccess)
+        return bail(cuda_fail(nullptr, e, "instantiating the step graph"));
+    *out = p;
+    return GFMC_OK;
+}
+
+gfmc_status gfmc_plan_launch(gfmc_plan_t p, int n_steps, void* stream)
+{
+    if (!p) return fail(nullptr, GFMC_EINVAL, "invalid plan");
+    if (n_steps < 0) return fail(nullptr, GFMC_EINVAL, "n_steps = %d < 0", n_steps);
+    cudaError_t e;
+    if ((e = cudaSetDevice(p->device)) != cudaSuccess) return cuda_fail(nullptr, e, "cudaSetDevice");
+    const cudaStream_t s = (cudaStream_t)stream;
+    if (p->pending > 0 && s != p->last)
+        return fail(nullptr, GFMC_EINVAL, "steps of this plan are pending on another stream; sync first");
+    for (int k = 0; k < n_steps; ++k)
+        if ((e = cudaGraphLaunch(p->exec, s)) != cudaSuccess) return cuda_fail(nullptr, e, "launching a step");
+    p->last = s;
+    p->pending += n_steps;
+    return GFMC_OK;
+}
+
+gfmc_status gfmc_plan_sync(gfmc_plan_t p, uint64_t* n_accepted, uint8_t** decisions, double** d_omega_trace,
+                           double** magnetization, int64_t* n_mag)
+{
+    if (!p) return fail(nullptr, GFMC_EINVAL, "invalid plan");
+    cudaError_t e;
+    if ((e = cudaSetDevice(p->device)) != cudaSuccess) return cuda_fail(nullptr, e, "cudaSetDevice");
+    if ((e = cudaStreamSynchronize(p->last)) != cudaSuccess) return cuda_fail(nullptr, e, "plan execution");
+    const long long steps = p->pending;
+    p->pending = 0;
+    gfmc_status result = GFMC_OK;
+    for (size_t j = 0; j < p->chains.size(); ++j) {
+        gfmc_ctx* h = p->chains[j];
+        const int c = p->caller[j];
+        const int64_t n = p->n_upd[j];
+        h->counter += (uint64_t)(steps * n);
+        int err[4];
+        unsigned long long nacc = 0;
+        long long nm = 0;
+        if ((e = cudaMemcpy(err, h->P.err, sizeof(err), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+            (e = cudaMemcpy(&nacc, h->d_nacc, sizeof(nacc), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+            (e = cudaMemcpy(&nm, h->d_nmag, sizeof(nm), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(nullptr, e, "reading plan status");
+        if (err[0] != 0) {
+            if (result == GFMC_OK) {
+                result = err[0] == gfmc::ERR_TIMEOUT ? GFMC_ETIMEOUT
+                         : err[0] == gfmc::ERR_NUMERIC ? GFMC_ENUMERIC : GFMC_ECUDA;
+                fail(nullptr, result, "chain %d: device error %d at stage %d", c, err[0], err[1]);
+            }
+            continue;
+        }
+        if (steps == 0) continue;
+        if (n_accepted) n_accepted[c] = nacc;
+        if (n_mag) n_mag[c] = nm;
+        if (decisions && decisions[c] &&
+            (e = cudaMemcpy(decisions[c], h->d_dec, (size_t)n, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(nullptr, e, "copying decisions");
+        if (d_omega_trace && d_omega_trace[c] &&
+            (e = cudaMemcpy(d_omega_trace[c], h->d_dom, sizeof(double) * n, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(nullptr, e, "copying Delta Omega traces");
+        if (magnetization && magnetization[c] && nm > 0 &&
+            (e = cudaMemcpy(magnetization[c], h->d_mag, sizeof(double) * nm, cudaMemcpyDeviceToHost)) != cudaSuccess)
+            return cuda_fail(nullptr, e, "copying magnetisations");
+    }
+    return result;
+}
+
+// ---------------------------------------------------------------------------
 // serving loop
 // ---------------------------------------------------------------------------
 
@@ -1148,6 +1512,7 @@ gfmc_status gfmc_server_submit(gfmc_server_t s, int slot, gfmc_t h, int64_t n_up
     if (!h) return sfail(s, GFMC_EINVAL, "chain is NULL");
     if (s->chain[slot]) return sfail(s, GFMC_EINVAL, "slot %d is busy", slot);
     if (h->in_server) return sfail(s, GFMC_EINVAL, "the chain already has a job in a server");
+    if (h->in_plan) return sfail(s, GFMC_EINVAL, "the chain belongs to a batch plan");
     if (h->device != s->device) return sfail(s, GFMC_EINVAL, "the chain lives on another device");
     if (h->K > s->maxM)
         return sfail(s, GFMC_EINVAL, "chain with M = %d on %d nodes above the server's %d", h->M, h->K, s->maxM);

@@ -127,6 +127,9 @@ cudaError_t launch_engine_f32(const Params& p, int nv, cudaStream_t s);
 cudaError_t launch_team_f64(const TeamJob* d_jobs, int njobs, int grid, int vec_bytes, int smem, cudaStream_t s);
 cudaError_t launch_team_f32(const TeamJob* d_jobs, int njobs, int grid, int vec_bytes, int smem, cudaStream_t s);
 cudaError_t team_max_ctas(int precision, int smem, int* out);
+// launch_team_* through cudaLaunchKernelEx with the cooperative attribute (capturable in a CUDA graph)
+cudaError_t launch_team_ex_f64(const TeamJob* d_jobs, int njobs, int grid, int vec_bytes, int smem, cudaStream_t s);
+cudaError_t launch_team_ex_f32(const TeamJob* d_jobs, int njobs, int grid, int vec_bytes, int smem, cudaStream_t s);
 cudaError_t launch_server(const ServerArgs& a, int grid, int smem, cudaStream_t s);
 // one cluster of C CTAs per job (recursion on the proposal's vectors)
 cudaError_t launch_cluster_f64(const TeamJob* d_jobs, int njobs, int C, int vec_bytes, int smem, cudaStream_t s);

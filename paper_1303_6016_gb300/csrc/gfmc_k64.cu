@@ -56,6 +56,25 @@ cudaError_t launch_team_f64(const TeamJob* d_jobs, int njobs, int grid, int vec_
     return cudaLaunchCooperativeKernel((void*)gfmc_team_engine<double>, dim3(grid), dim3(kThreads), args, (size_t)smem, s);
 }
 
+// The same launch through cudaLaunchKernelEx with the cooperative attribute,
+// the form a CUDA graph captures as a cooperative kernel node.
+cudaError_t launch_team_ex_f64(const TeamJob* d_jobs, int njobs, int grid, int vec_bytes, int smem, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(gfmc_team_engine<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, gfmc_team_engine<double>, d_jobs, njobs, vec_bytes);
+}
+
 cudaError_t team_max_ctas_f64(int smem, int* out)
 {
     cudaError_t e = cudaFuncSetAttribute(gfmc_team_engine<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

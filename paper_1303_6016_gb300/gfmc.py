@@ -31,6 +31,7 @@ EXPORTS = ("gfmc_default_options", "gfmc_create", "gfmc_moments", "gfmc_delta_om
            "gfmc_updates", "gfmc_sweep", "gfmc_get_spins", "gfmc_set_state", "gfmc_get_counter",
            "gfmc_set_wait_budget", "gfmc_inject_stall", "gfmc_last_error", "gfmc_destroy",
            "gfmc_delta_omega_noalloc", "gfmc_run_batch", "gfmc_run_clusters", "gfmc_cluster_min_ctas",
+           "gfmc_plan_create", "gfmc_plan_launch", "gfmc_plan_sync", "gfmc_plan_destroy",
            "gfmc_server_create",
            "gfmc_server_submit",
            "gfmc_server_poll", "gfmc_server_last_error", "gfmc_server_destroy")
@@ -95,6 +96,17 @@ def load(path: str = LIB_PATH):
     L.gfmc_run_clusters.restype = ctypes.c_int
     L.gfmc_cluster_min_ctas.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     L.gfmc_cluster_min_ctas.restype = ctypes.c_int
+    L.gfmc_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_int),
+                                   ctypes.c_int, ctypes.POINTER(vp)]
+    L.gfmc_plan_create.restype = ctypes.c_int
+    L.gfmc_plan_launch.argtypes = [vp, ctypes.c_int, vp]
+    L.gfmc_plan_launch.restype = ctypes.c_int
+    L.gfmc_plan_sync.argtypes = [vp, ctypes.POINTER(u64), ctypes.POINTER(ctypes.POINTER(ctypes.c_uint8)),
+                                 ctypes.POINTER(ctypes.POINTER(ctypes.c_double)),
+                                 ctypes.POINTER(ctypes.POINTER(ctypes.c_double)), ctypes.POINTER(i64)]
+    L.gfmc_plan_sync.restype = ctypes.c_int
+    L.gfmc_plan_destroy.argtypes = [vp]
+    L.gfmc_plan_destroy.restype = None
     L.gfmc_server_create.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int, ctypes.POINTER(vp)]
     L.gfmc_server_create.restype = ctypes.c_int
     L.gfmc_server_submit.argtypes = [vp, ctypes.c_int, vp, i64, ctypes.POINTER(ctypes.c_uint8), d]
@@ -255,6 +267,71 @@ def run_clusters(chains, n_updates, cluster_ctas, trace=True, stream=None) -> li
     """Chains on the proposal-vector recursion, each on one thread-block
     cluster holding its lattice in shared memory (gfmc_run_clusters)."""
     return run_batch(chains, n_updates, cluster_ctas, trace, stream, _fn="gfmc_run_clusters")
+
+
+SCHEDULES = {"teams": 0, "clusters": 1}
+
+
+class Plan:
+    """One step of a batch captured in a CUDA graph (gfmc_plan_*): every chain
+    runs n_updates[c] updates per step; launch() enqueues steps, sync() waits
+    and returns the last step's results per chain.  While the plan exists its
+    chains belong to it."""
+
+    def __init__(self, chains, n_updates, ctas, schedule: str = "clusters"):
+        lib = load()
+        self._lib = lib
+        self.chains = list(chains)
+        n = len(self.chains)
+        self.n_updates = [int(u) for u in (n_updates if hasattr(n_updates, "__len__") else [n_updates] * n)]
+        H = (ctypes.c_void_p * n)(*[c._h.value for c in self.chains])
+        NU = (ctypes.c_int64 * n)(*self.n_updates)
+        TC = (ctypes.c_int * n)(*[int(t) for t in ctas])
+        h = ctypes.c_void_p()
+        st = lib.gfmc_plan_create(H, n, NU, TC, SCHEDULES[schedule], ctypes.byref(h))
+        if st != GFMC_OK:
+            raise GfmcError(st, lib.gfmc_last_error(None).decode())
+        self._h = h
+        self._stream = None
+        self._decs = [np.zeros(u, dtype=np.uint8) for u in self.n_updates]
+        self._doms = [np.zeros(u, dtype=np.float64) for u in self.n_updates]
+
+    def launch(self, n_steps: int = 1, stream=None):
+        if stream is None:
+            stream = current_stream_handle()
+        st = self._lib.gfmc_plan_launch(self._h, int(n_steps), stream)
+        if st != GFMC_OK:
+            raise GfmcError(st, self._lib.gfmc_last_error(None).decode())
+
+    def sync(self, trace: bool = True) -> list:
+        n = len(self.chains)
+        acc = (ctypes.c_uint64 * n)()
+        NM = (ctypes.c_int64 * n)()
+        DP = (ctypes.POINTER(ctypes.c_uint8) * n)(*[d.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+                                                      for d in self._decs]) if trace else None
+        OP = (ctypes.POINTER(ctypes.c_double) * n)(*[_dp(d) for d in self._doms]) if trace else None
+        st = self._lib.gfmc_plan_sync(self._h, acc, DP, OP, None, NM)
+        if st != GFMC_OK:
+            raise GfmcError(st, self._lib.gfmc_last_error(None).decode())
+        return [{"n_accepted": int(acc[c]), "decisions": self._decs[c].copy() if trace else None,
+                 "d_omega": self._doms[c].copy() if trace else None} for c in range(n)]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.gfmc_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def cluster_min_ctas(L: int, M: int, precision: str = "fp32_mixed") -> int:
