@@ -1579,80 +1579,80 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                         }
                     }
                 }
-            } else
-            for (int m = 1; m <= p.nsteps; ++m) {
-                if (!wait_neighbours(p, cta, phase + (unsigned)m, 100 + m)) return;
-                const R2* rd = (m & 1) ? buf1 : buf0;  // r_m of every site
-                R2* wr = (m & 1) ? buf0 : buf1;        // receives r_{m+1}; held r_{m-1}
-                R2 nxt[kVec];
-                if constexpr (sizeof(R) == 4) {
-                    // issue all 42 neighbour loads before the first use (latency-bound path)
-                    R2 nv[kVec][6];
-                    if (active) {
-    #pragma unroll
-                        for (int v = 0; v < kVec; ++v)
-    #pragma unroll
-                            for (int d = 0; d < 6; ++d) nv[v][d] = ldcg2(rd + (size_t)v * N + nb[d]);
+            } else {
+                // FP32: one site per thread, all 42 neighbour loads issued before the first use
+                // (latency-bound path).  When a CTA's tile fits 7 warps (p.helper7), warp 7 has
+                // no site and is the helper: after the compute warps' stores (named barrier 2)
+                // it publishes the CTA's flag and waits for the neighbours' flags of the next
+                // step (named barrier 3) while the compute warps form the Gram sums, so the
+                // release fence and the poll's round trip overlap the sums.
+                const bool helper = p.helper7 != 0;
+                __shared__ int s_go32;
+                if (helper && warp == kWarps - 1) {
+                    for (int w = 0; w < 2; ++w)
+                        for (int e = lane; e < kEntries; e += 32) g32[w][kWarps - 1][e] = 0.0f;
+                    bool ok = true;
+                    for (int m = 1; m <= p.nsteps + 1 && ok; ++m) {
+                        if (m > 1) {
+                            nbar_sync(2, kThreads);
+                            if (lane == 0 && p.ncta > 1 && !(p.stall && cta == 0))
+                                st_release_u32(&p.flags[cta], phase + (unsigned)m);
+                        }
+                        if (m <= p.nsteps) {
+                            ok = warp_wait_neighbours(p, cta, phase + (unsigned)m, 100 + m, lane);
+                            if (lane == 0) s_go32 = ok ? 1 : 0;
+                            nbar_arrive(3, kThreads);
+                        }
                     }
-                    if (m >= 2) flush112(m - 1);
-                    if (active) {
+                    if (!ok) return;
+                } else {
+                    for (int m = 1; m <= p.nsteps; ++m) {
+                        if (helper) {
+                            nbar_sync(3, kThreads);
+                            if (!s_go32) return;
+                        } else if (!wait_neighbours(p, cta, phase + (unsigned)m, 100 + m)) {
+                            return;
+                        }
+                        const R2* rd = (m & 1) ? buf1 : buf0;  // r_m of every site
+                        R2* wr = (m & 1) ? buf0 : buf1;        // receives r_{m+1}; held r_{m-1}
+                        R2 nxt[kVec];
+                        R2 nv[kVec][6];
+                        if (active) {
+    #pragma unroll
+                            for (int v = 0; v < kVec; ++v)
+    #pragma unroll
+                                for (int d = 0; d < 6; ++d) nv[v][d] = ldcg2(rd + (size_t)v * N + nb[d]);
+                        }
+                        if (m >= 2) flush112(m - 1);
+                        if (active) {
+    #pragma unroll
+                            for (int v = 0; v < kVec; ++v) {
+                                R2 acc = c_make<R2>(0, 0);
+    #pragma unroll
+                                for (int d = 0; d < 6; ++d) c_fma(acc, h[d], nv[v][d]);
+                                nxt[v] = c_make<R2>(fma((R)2, acc.x, -prv[v].x), fma((R)2, acc.y, -prv[v].y));
+                                if (m < p.nsteps) stcg2(wr + (size_t)v * N + i, nxt[v]);
+                            }
+                        } else {
+    #pragma unroll
+                            for (int v = 0; v < kVec; ++v) nxt[v] = c_make<R2>(0, 0);
+                        }
+                        // r_{m+1} is stored: neighbours may start step m+1 while this CTA forms its dots
+                        if (helper) nbar_arrive(2, kThreads);
+                        else publish(p, cta, phase + (unsigned)m + 1u);
+                        // Gram entries e = 0..55: e < 28 -> conj(r_m^j) r_m^k, else conj(r_m^j) r_{m+1}^k,
+                        // (j, k) the upper pair e mod 28; 4 chunks of 14 complex values, warp butterfly.
+                        gram_chunk_reduce_raw<R, R2, 0>(cur, nxt, lane, g32[m & 1][warp]);
+                        gram_chunk_reduce_raw<R, R2, 1>(cur, nxt, lane, g32[m & 1][warp]);
+                        gram_chunk_reduce_raw<R, R2, 2>(cur, nxt, lane, g32[m & 1][warp]);
+                        gram_chunk_reduce_raw<R, R2, 3>(cur, nxt, lane, g32[m & 1][warp]);
     #pragma unroll
                         for (int v = 0; v < kVec; ++v) {
-                            R2 acc = c_make<R2>(0, 0);
-    #pragma unroll
-                            for (int d = 0; d < 6; ++d) c_fma(acc, h[d], nv[v][d]);
-                            nxt[v] = c_make<R2>(fma((R)2, acc.x, -prv[v].x), fma((R)2, acc.y, -prv[v].y));
-                            if (m < p.nsteps) stcg2(wr + (size_t)v * N + i, nxt[v]);
+                            prv[v] = cur[v];
+                            cur[v] = nxt[v];
                         }
-                    } else {
-    #pragma unroll
-                        for (int v = 0; v < kVec; ++v) nxt[v] = c_make<R2>(0, 0);
-                    }
-                } else if (active) {
-                    // h holds 2 Htilde here: r_{m+1} = -r_{m-1} + sum_d (2 h_d) r_m(nb_d), FMAs only
-    #pragma unroll
-                    for (int v = 0; v < kVec; ++v) {
-                        const R2* cv = rd + (size_t)v * N;
-                        R2 acc = c_make<R2>(-prv[v].x, -prv[v].y);
-    #pragma unroll
-                        for (int d = 0; d < 6; ++d) c_fma(acc, h[d], ldcg2(cv + nb[d]));
-                        nxt[v] = acc;
-                        if (m < p.nsteps) stcg2(wr + (size_t)v * N + i, nxt[v]);
-                    }
-                } else {
-    #pragma unroll
-                    for (int v = 0; v < kVec; ++v) nxt[v] = c_make<R2>(0, 0);
-                }
-                double* prow = p.partial + ((size_t)(m - 1) * p.ncta + cta) * kEntries;
-                if constexpr (sizeof(R) == 8) {
-                    // stage r_m, r_{m+1} and -i times each of the own site for the Gram sums
-    #pragma unroll
-                    for (int v = 0; v < kVec; ++v) {
-                        dyn[v * kStage + tid] = cur[v];
-                        dyn[(kVec + v) * kStage + tid] = nxt[v];
-                        dyn[(2 * kVec + v) * kStage + tid] = minus_i(cur[v]);
-                        dyn[(3 * kVec + v) * kStage + tid] = minus_i(nxt[v]);
                     }
                 }
-                // r_{m+1} is stored: neighbours may start step m+1 while this CTA forms its dots
-                publish(p, cta, phase + (unsigned)m + 1u);
-                if constexpr (sizeof(R) == 8) {
-                    gram_smem_f64(dyn, s1 - s0, &red[0][0], prow);
-                } else {
-                    // Gram entries e = 0..55: e < 28 -> conj(r_m^j) r_m^k, else conj(r_m^j) r_{m+1}^k,
-                    // (j, k) the upper pair e mod 28; 4 chunks of 14 complex values, warp butterfly.
-                    gram_chunk_reduce_raw<R, R2, 0>(cur, nxt, lane, g32[m & 1][warp]);
-                    gram_chunk_reduce_raw<R, R2, 1>(cur, nxt, lane, g32[m & 1][warp]);
-                    gram_chunk_reduce_raw<R, R2, 2>(cur, nxt, lane, g32[m & 1][warp]);
-                    gram_chunk_reduce_raw<R, R2, 3>(cur, nxt, lane, g32[m & 1][warp]);
-                }
-    #pragma unroll
-                for (int v = 0; v < kVec; ++v) {
-                    prv[v] = cur[v];
-                    cur[v] = nxt[v];
-                }
-            }
-            if constexpr (sizeof(R) == 4) {
                 __syncthreads();
                 flush112(p.nsteps);
             }

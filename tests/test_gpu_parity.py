@@ -249,6 +249,23 @@ def test_bad_site_and_timeout_status(G):
         assert ch.delta_omega(3, 1.0, 1.0) == ref
 
 
+def test_fp32_timeout_status(G):
+    """FP32-mixed: CTA 0 withholds its tagged values, the CTAs reading them run
+    out of a short budget and the launch ends with GFMC_ETIMEOUT; the handle
+    stays usable and gives the same answer afterwards."""
+    L, M = 8, 64
+    sp = inputs.uniform_sphere(L, 0)
+    with chain(G, L, sp, M, num_ctas=4, precision="fp32_mixed") as ch:
+        ref = ch.delta_omega(3, 1.0, 1.0)
+        ch.set_wait_budget(20_000_000)
+        ch.inject_stall(True)
+        with pytest.raises(G.GfmcError) as e:
+            ch.delta_omega(3, 1.0, 1.0)
+        assert e.value.status == G.GFMC_ETIMEOUT
+        ch.set_wait_budget(4_000_000_000)
+        assert ch.delta_omega(3, 1.0, 1.0) == ref
+
+
 # ---------------------------------------------------------------------------
 # the paper's recursion on the proposal's vectors (o, v; o+v and o+iv by linearity)
 # ---------------------------------------------------------------------------
