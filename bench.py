@@ -594,6 +594,14 @@ def main():
             line["batching_clusters"] = run_batching_clusters(stream, max(3, args.steps // 2), 3,
                                                               args.batch_updates, flush)
 
+    if not args.no_mixed:
+        # FP32-mixed against the FP64 path on the same chain: Delta Omega error per
+        # update (target <= 1e-4 t) and moment error by band of n
+        from paper_1303_6016_gb300 import precision_report
+        prec = precision_report.run(L=L, Ms=(M,), n_sites=4)
+        line["fp32_mixed"]["error_vs_fp64"] = [
+            {k: r[k] for k in ("spins", "M", "domega_err_max", "domega_rel_err_max", "moment_err_by_n")} for r in prec]
+
     if not args.no_serving:
         from paper_1303_6016_gb300 import serving
         line["serving"] = serving.sweep(rates=(10, 100), seconds=3.0, K=2, drain_s=8.0)
