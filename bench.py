@@ -317,7 +317,10 @@ def run_batching_clusters(stream, steps, warmup, updates, flush):
     import torch
     from paper_1303_6016_gb300 import batch
     chains, Ls, Ts = batch.c4_chains(M=1024, recursion="proposal")
-    runner = batch.ClusterRunner(chains)
+    t0 = time.perf_counter()
+    tuner = batch.ClusterTuner(M=1024, precision="fp32_mixed")
+    runner = batch.ClusterRunner(chains, tuner, updates=updates)
+    tune_s = time.perf_counter() - t0
     for _ in range(warmup):
         runner.run(updates)
     per = []
@@ -334,7 +337,8 @@ def run_batching_clusters(stream, steps, warmup, updates, flush):
     by_L = {str(int(L)): c for L, c in sorted(zip(Ls, runner.cluster_ctas))}
     # the same steps captured once in a CUDA graph (gfmc_plan_*) and replayed
     from paper_1303_6016_gb300 import gfmc
-    with gfmc.Plan(chains, [updates] * n, runner.cluster_ctas, schedule="clusters") as plan:
+    ordered, sizes = runner.ordered()
+    with gfmc.Plan(ordered, [updates] * n, sizes, schedule="clusters") as plan:
         plan.launch(warmup)
         plan.sync(trace=False)
         perg = []
@@ -356,7 +360,8 @@ def run_batching_clusters(stream, steps, warmup, updates, flush):
             "stencil_gbs": sum(bytes_u) * updates / (total / steps / 1000.0) / 1e9,
             "graph": {"value": n * updates * steps / (totg / 1000.0), "unit": UNIT, "ms_per_step": totg / steps,
                       "note": "one CUDA graph launch per step (gfmc_plan_launch), no host work between steps"},
-            "cluster_ctas_by_L": by_L, "recursion": "proposal",
+            "cluster_ctas_by_L": by_L, "recursion": "proposal", "autotune_s": tune_s,
+            "tuned_ms_per_step": runner.makespan * 1e3 if runner.makespan else None,
             "config": "the batching workload (64 chains, L from {8,12,16,24,32}, M = 1024, FP32-mixed), "
                       "each chain on one thread-block cluster holding its lattice in shared memory"}
 

@@ -193,8 +193,9 @@ gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_update
  * distributed shared memory; one hardware cluster barrier
  * per recursion step (Eq. recursive), no global-memory exchange.  Clusters are
  * independent: chains of the same precision and cluster size share a launch,
- * launches of different groups overlap, and clusters need not all be resident
- * at once.  Results as gfmc_updates would give them (up to the rounding order
+ * launches of different groups overlap (issued in the order of each group's
+ * first chain in `chains`, so a caller lists its longest chains first), and
+ * clusters need not all be resident at once.  Results as gfmc_updates would give them (up to the rounding order
  * of the sums); the outputs are as for gfmc_run_batch.  GFMC_EINVAL when a
  * chain's lattice does not fit in the shared memory of its cluster (56 bytes
  * per site FP32, 112 FP64, N / C sites per CTA; the tail reuses that space as

@@ -133,22 +133,153 @@ class BatchRunner:
         return out
 
 
+CLUSTER_SIZES = (1, 2, 4, 8, 16)
+
+
+def list_schedule(jobs, sms: int) -> float:
+    """Makespan of jobs (cluster CTAs, seconds) started in the given order on
+    `sms` SMs, each as soon as enough SMs are free, later jobs filling gaps
+    that earlier ones cannot use (the device's cluster dispatch)."""
+    import heapq
+    now, free, running, waiting = 0.0, sms, [], list(jobs)
+    while waiting or running:
+        k = 0
+        while k < len(waiting):
+            C, d = waiting[k]
+            if C <= free:
+                free -= C
+                heapq.heappush(running, (now + d, C))
+                waiting.pop(k)
+            else:
+                k += 1
+        if not running:
+            raise ValueError("a job needs more SMs than the device has")
+        now, C = heapq.heappop(running)
+        free += C
+        while running and running[0][0] <= now:
+            free += heapq.heappop(running)[1]
+    return now
+
+
+class ClusterTuner:
+    """Update times of the cluster engine per lattice size and cluster size,
+    measured on the device, and the choice of cluster sizes and launch order
+    for a batch: every assignment of a size to each lattice class is run
+    through the list-scheduling model and the one with the shortest makespan
+    wins; chains launch longest first."""
+
+    def __init__(self, M: int, precision: str = "fp32_mixed", probe_updates: int = 2, beta: float = 20.0,
+                 mu: float = -2.0, nodes: int = 0):
+        self.M, self.precision, self.probe_updates = M, precision, probe_updates
+        self.beta, self.mu, self.nodes = beta, mu, nodes
+        self.table = {}  # L -> {cluster size: seconds per update}
+
+    def measure(self, L: int) -> dict:
+        if L in self.table:
+            return self.table[L]
+        import torch
+        K = self.nodes or self.M
+        cmin = gfmc.cluster_min_ctas(L, max(self.M, K), self.precision)
+        res = {}
+        with gfmc.Chain(L, inputs.uniform_sphere(L, 0), M=self.M, precision=self.precision, beta=self.beta,
+                        mu=self.mu, recursion="proposal", nodes=self.nodes) as ch:
+            for C in CLUSTER_SIZES:
+                if C < cmin or L % C:
+                    continue
+                gfmc.run_clusters([ch], [1], [C], trace=False)  # warm-up
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                gfmc.run_clusters([ch], [self.probe_updates], [C], trace=False)
+                res[C] = (time.perf_counter() - t0) / self.probe_updates
+        self.table[L] = res
+        return res
+
+    def rank(self, Ls, updates, sms: int = 0, top: int = 0):
+        """Assignments (cluster size per chain, launch order, modelled makespan)
+        sorted by the modelled makespan; the first `top` (all if 0)."""
+        import itertools
+        sms = sms or device_ctas()
+        classes = sorted(set(int(L) for L in Ls))
+        tables = {L: self.measure(L) for L in classes}
+        out = []
+        for pick in itertools.product(*[sorted(tables[L]) for L in classes]):
+            size = dict(zip(classes, pick))
+            dur = [updates[c] * tables[int(L)][size[int(L)]] for c, L in enumerate(Ls)]
+            order = sorted(range(len(Ls)), key=lambda c: -dur[c])
+            span = list_schedule([(size[int(Ls[c])], dur[c]) for c in order], sms)
+            out.append(([size[int(L)] for L in Ls], order, span))
+        out.sort(key=lambda x: x[2])
+        return out[:top] if top else out
+
+    def choose(self, Ls, updates, sms: int = 0):
+        """The assignment with the shortest modelled makespan."""
+        return self.rank(Ls, updates, sms, top=1)[0]
+
+    def choose_measured(self, chains, updates, top: int = 8):
+        """The model's `top` assignments and the smallest-cluster one, each timed
+        for one step on probe chains of the batch's lattice sizes (the model
+        does not know how the device places clusters on its GPCs); the fastest
+        wins.  Returns (sizes, order, measured seconds per step)."""
+        import torch
+        Ls = [c.L for c in chains]
+        n = len(chains)
+        cands = self.rank(Ls, updates, top=top)
+        smallest = [min(self.measure(int(L))) for L in Ls]
+        cands.append((smallest, sorted(range(n), key=lambda c: -updates[c] * self.table[int(Ls[c])][smallest[c]]),
+                      None))
+        probes = [gfmc.Chain(c.L, inputs.uniform_sphere(c.L, 0), M=self.M, precision=self.precision, beta=self.beta,
+                             mu=self.mu, recursion="proposal", nodes=self.nodes, chain_id=k)
+                  for k, c in enumerate(chains)]
+        best = None
+        try:
+            for sizes, order, _ in cands:
+                chs = [probes[i] for i in order]
+                cs = [sizes[i] for i in order]
+                nu = [updates[i] for i in order]
+                gfmc.run_clusters(chs, nu, cs, trace=False)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                gfmc.run_clusters(chs, nu, cs, trace=False)
+                dt = time.perf_counter() - t0
+                if best is None or dt < best[2]:
+                    best = (sizes, order, dt)
+        finally:
+            for p in probes:
+                p.close()
+        return best
+
+
 class ClusterRunner:
     """Runs chains with the recursion on the proposal's vectors on
-    thread-block clusters (gfmc_run_clusters): each chain on the smallest
-    cluster whose shared memory holds its lattice -- the fewest SMs per chain,
-    hence the most chains in flight -- all chains in one call (one launch per
-    cluster size and precision, the launches overlapping)."""
+    thread-block clusters (gfmc_run_clusters).  With a ClusterTuner the
+    cluster sizes and the launch order are the fastest, timed on probe
+    chains, of the list-scheduling model's best assignments and the
+    smallest-cluster one; without one each chain takes the smallest cluster
+    whose shared memory holds its lattice (the fewest SMs per chain)."""
 
-    def __init__(self, chains):
+    def __init__(self, chains, tuner: "ClusterTuner" = None, updates: int = 4):
         self.chains = list(chains)
-        self.cluster_ctas = [gfmc.cluster_min_ctas(c.L, max(c.M, c.K), c.precision) for c in self.chains]
+        n = len(self.chains)
+        if tuner is None:
+            self.cluster_ctas = [gfmc.cluster_min_ctas(c.L, max(c.M, c.K), c.precision) for c in self.chains]
+            self.order = list(range(n))
+            self.makespan = None
+        else:
+            self.cluster_ctas, self.order, self.makespan = tuner.choose_measured(self.chains, [updates] * n)
+
+    def ordered(self):
+        """(chains, cluster sizes) in launch order."""
+        return [self.chains[i] for i in self.order], [self.cluster_ctas[i] for i in self.order]
 
     def run(self, updates_per_chain, trace: bool = False):
         n = len(self.chains)
         updates = list(updates_per_chain) if hasattr(updates_per_chain, "__len__") else [updates_per_chain] * n
-        res = gfmc.run_clusters(self.chains, updates, self.cluster_ctas, trace=trace)
-        return [dict(r, cluster_ctas=c) for r, c in zip(res, self.cluster_ctas)]
+        chs, cs = self.ordered()
+        res = gfmc.run_clusters(chs, [updates[i] for i in self.order], cs, trace=trace)
+        out = [None] * n
+        for k, i in enumerate(self.order):
+            out[i] = dict(res[k], cluster_ctas=self.cluster_ctas[i])
+        return out
 
 
 def c4_chains(n_chains: int = 64, M: int = 1024, precision: str = "fp32_mixed", seed: int = 4,

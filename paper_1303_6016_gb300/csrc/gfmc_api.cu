@@ -927,8 +927,8 @@ gfmc_status gfmc_run_clusters(gfmc_t* chains, int n_chains, const int64_t* n_upd
             (e = cudaMemsetAsync(P.n_mag, 0, sizeof(long long), s)) != cudaSuccess)
             return cuda_fail(nullptr, e, "clearing control words");
     }
-    // largest clusters first: they are the hardest to place and, per chain, the longest
-    std::stable_sort(groups.begin(), groups.end(), [](const Group& a, const Group& b) { return a.C > b.C; });
+    // groups launch in the order of their first chain in `chains` (the caller's
+    // priority: a scheduler puts its longest chains first)
     for (const auto& g : groups) {
         int active = 0;
         const int smem = (int)g.vec_bytes + g.work;
@@ -1168,8 +1168,7 @@ gfmc_status gfmc_plan_create(gfmc_t* chains, int n_chains, const int64_t* n_upda
             const std::pair<int, int> k(chains[c]->precision, ctas[c]);
             if (std::find(keys.begin(), keys.end(), k) == keys.end()) keys.push_back(k);
         }
-        // largest clusters first: they are the hardest to place and, per chain, the longest
-        std::stable_sort(keys.begin(), keys.end(), [](auto a, auto b) { return a.second > b.second; });
+        // groups launch in the order of their first chain in `chains` (the caller's priority)
         for (const auto& k : keys) {
             Group g{k.first, k.second, (int)jobs.size(), 0, 0};
             for (int c = 0; c < n_chains; ++c) {

@@ -75,3 +75,4 @@ def test_dead_replica_is_detected_by_survivor():
     assert procs[1].exitcode == 3
     status, _ = q.get(timeout=5)
     assert status == "error"
+
