@@ -463,8 +463,7 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
         (e = dalloc(h, &P.err, 4)) != cudaSuccess || (e = dalloc(h, &h->d_nacc, 1)) != cudaSuccess ||
         (e = dalloc(h, &h->d_nmag, 1)) != cudaSuccess)
         return bail(cuda_fail(h, e, "allocating chain state"));
-    P.helper7 = (h->precision == GFMC_PREC_FP32_MIXED && !h->multi_site &&
-                 (N + ncta - 1) / ncta <= gfmc::kThreads - 32) ? 1 : 0;
+    P.helper7 = (!h->multi_site && (N + ncta - 1) / ncta <= gfmc::kThreads - 32) ? 1 : 0;
     if (prefetch) {
         int* d_wp = nullptr;
         int2* d_w = nullptr;

@@ -1398,8 +1398,35 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                     p.partial[((size_t)(m - 1) * p.ncta + cta) * kEntries + tid] = sum;
                 }
             };
+            // With every tile within 7 warps (p.helper7), warp 7 has no site: it publishes
+            // the CTA's flag after the stencil (named barrier 2) and polls the neighbours'
+            // flags of the next step (named barrier 3) while warps 0-6 form the sums.
+            const bool helper = p.helper7 != 0;
+            __shared__ int s_go2;
+            if (helper && warp == kWarps - 1) {
+                for (int e = lane; e < 16; e += 32) w8[e >> 3][kWarps - 1][e & 7] = (R)0;
+                bool ok = true;
+                for (int m = 1; m <= p.nsteps + 1 && ok; ++m) {
+                    if (m > 1) {
+                        nbar_sync(2, kThreads);
+                        if (lane == 0 && p.ncta > 1 && !(p.stall && cta == 0))
+                            st_release_u32(&p.flags[cta], phase + (unsigned)m);
+                    }
+                    if (m <= p.nsteps) {
+                        ok = warp_wait_neighbours(p, cta, phase + (unsigned)m, 100 + m, lane);
+                        if (lane == 0) s_go2 = ok ? 1 : 0;
+                        nbar_arrive(3, kThreads);
+                    }
+                }
+                if (!ok) return;
+            } else
             for (int m = 1; m <= p.nsteps; ++m) {
-                if (!wait_neighbours(p, cta, phase + (unsigned)m, 100 + m)) return;
+                if (helper) {
+                    nbar_sync(3, kThreads);
+                    if (!s_go2) return;
+                } else if (!wait_neighbours(p, cta, phase + (unsigned)m, 100 + m)) {
+                    return;
+                }
                 const R2* rd = (m & 1) ? buf1 : buf0;
                 R2* wr = (m & 1) ? buf0 : buf1;
                 R2 nv[2][6];
@@ -1424,7 +1451,8 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                     nxt[0] = c_make<R2>(0, 0);
                     nxt[1] = c_make<R2>(0, 0);
                 }
-                publish(p, cta, phase + (unsigned)m + 1u);
+                if (helper) nbar_arrive(2, kThreads);
+                else publish(p, cta, phase + (unsigned)m + 1u);
                 // |r_m^o|^2, |r_m^v|^2, <r_m^o|r_m^v>, Re<r_m^o|r_m+1^o>, Re<r_m^v|r_m+1^v>, <r_m^o|r_m+1^v>
                 const R2 a = cur[0], b = cur[1], na = nxt[0], nbv = nxt[1];
                 R v8[8];

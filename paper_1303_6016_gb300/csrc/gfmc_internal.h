@@ -64,8 +64,9 @@ struct Params {
     const int2* win;        // [win_ptr[ncta]]
     int win_max;
     int prefetch;
-    // FP32 single-chain engine: every tile fits 7 warps, so warp 7 publishes and
-    // polls the flags while the other warps form the Gram sums
+    // single-chain engines on 256 threads (FP32 unit vectors, proposal vectors):
+    // every tile fits 7 warps, so warp 7 publishes and polls the flags while
+    // the other warps form the Gram sums
     int helper7;
 
     // synchronisation
