@@ -456,7 +456,7 @@ def run_reference(args, rank, world, dist):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(L, M, U, "fp64"),
+        "config": dict(workload_config(L, M, U, "fp64"), l2="not applicable: the CPU oracle"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{U} update per step from the start of sweep 0 at L={L}, M={M}"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
