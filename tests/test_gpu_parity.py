@@ -344,3 +344,34 @@ def test_lorentz_sweep_matches_oracle(G):
         assert abs(out["d_omega"][q] - res["d_omega"][q]) <= dom_tol(res["d_omega"][q])
         if own[q] != bool(out["decisions"][q]):
             assert abs(res["ratio"][q] - res["u"][q]) < TIE
+
+
+# ---------------------------------------------------------------------------
+# tile layouts of the single-chain engines: the FP64 engine's prefetched runs
+# of sites (ragged tiles, tiles across plane boundaries, y-wrap rows) and the
+# FP32 engine with and without warp 7 as the flag helper (tiles of <= 224
+# sites or more)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("L,ncta", [(20, 0), (10, 7), (24, 152), (9, 5), (16, 17)])
+def test_fp64_tile_layouts_match_oracle(G, L, ncta):
+    M = 64
+    sp = inputs.uniform_sphere(L, 40 + L)
+    with chain(G, L, sp, M, num_ctas=ncta, seed=3) as ch:
+        N = L ** 3
+        for o in (0, N // 3 + 1, N - 1):
+            assert np.abs(ch.moments(o) - O.moments(L, sp, o, M)).max() <= MOM_TOL, o
+        out = ch.updates(6)
+    check_trace_against_oracle(L, sp, M, out, 6, seed=3)
+
+
+@pytest.mark.parametrize("L,ncta", [(8, 2), (8, 3), (12, 9)])
+def test_fp32_with_and_without_the_helper_warp(G, L, ncta):
+    """(8, 2): 256-site tiles, no helper; (8, 3) and (12, 9): tiles within 7
+    warps, warp 7 publishes and polls.  Delta Omega within 1e-4 t of the oracle."""
+    M = 64
+    sp = inputs.uniform_sphere(L, 50 + ncta)
+    with chain(G, L, sp, M, num_ctas=ncta, precision="fp32_mixed", seed=4) as ch:
+        out = ch.updates(5)
+    res = O.updates(L, sp, 5, M, beta=20.0, chem=-2.0, seed=4, forced=out["decisions"].astype(np.int8))
+    assert np.abs(out["d_omega"] - res["d_omega"]).max() <= 1e-4
