@@ -538,10 +538,9 @@ __device__ __forceinline__ double2 minus_i(double2 z)
     return make_double2(z.y, __hiloint2double(__double2hiint(z.x) ^ 0x80000000, __double2loint(z.x)));
 }
 
-// NAMED: the CTA's compute warps (threads 0..kThreads-1) meet at named barrier
-// 1 instead of __syncthreads (a helper warp runs elsewhere meanwhile).
-template <bool NAMED = false>
-__device__ __forceinline__ void gram_smem_f64(const double2* sr, int T, double* gsum, double* out)
+// The units' partial sums go to gsum[g][kEntries]; gram_groups_f64 adds the
+// groups in order once every unit has written (the caller's barrier).
+__device__ __forceinline__ void gram_units_f64(const double2* sr, int T, double* gsum)
 {
     const int tid = threadIdx.x;
     if (tid < kGramUnits * kGramGroups) {
@@ -590,7 +589,12 @@ __device__ __forceinline__ void gram_smem_f64(const double2* sr, int T, double* 
             gs[eim + 1] = 0.0;
         }
     }
-    if constexpr (NAMED) nbar_sync(1, kThreads); else __syncthreads();
+}
+
+// out[e] = sum over the kGramGroups groups of gsum, in order (threads e < kEntries).
+__device__ __forceinline__ void gram_groups_f64(const double* gsum, double* out)
+{
+    const int tid = threadIdx.x;
     if (tid < kEntries) {
         double s = gsum[tid];
 #pragma unroll
@@ -600,7 +604,10 @@ __device__ __forceinline__ void gram_smem_f64(const double2* sr, int T, double* 
 }
 
 // FP64 Gram sums accumulated over one staged chunk of up to kThreads sites
-// (thread (entry e, group g) as in gram_smem_f64), into the thread's re, im.
+// (rows r_m^v at sr[v*kStage + s], r_{m+1}^v at sr[(7+v)*kStage + s]) into the
+// thread's re, im: thread tid < 224 takes entry e = tid mod 56 (e < 28 the
+// pair e of <r_m|r_m>, else pair e-28 of <r_m|r_{m+1}>) over the sites
+// s = g, g+4, ... of group g = tid / 56.
 __device__ __forceinline__ void gram_smem_acc(const double2* sr, int T, double& re, double& im)
 {
     const int tid = threadIdx.x;
@@ -1554,8 +1561,11 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                     if (!ok) return;
                 } else {
                     for (int m = 1; m <= p.nsteps; ++m) {
+                        // barrier 3 also ends every compute warp's Gram units of step m-1
                         nbar_sync(3, NT);
                         if (!s_go) return;
+                        if (m >= 2)
+                            gram_groups_f64(&red[0][0], p.partial + ((size_t)(m - 2) * p.ncta + cta) * kEntries);
                         const R2* rd = (m & 1) ? buf1 : buf0;  // r_m of every site
                         R2* wr = (m & 1) ? buf0 : buf1;        // receives r_{m+1}; held r_{m-1}
                         R2 nxt[kVec];
@@ -1598,14 +1608,15 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                         // complete for the Gram sums once the compute warps meet at barrier 1
                         nbar_arrive(2, NT);
                         nbar_sync(1, kThreads);
-                        gram_smem_f64<true>(dyn, s1 - s0, &red[0][0],
-                                            p.partial + ((size_t)(m - 1) * p.ncta + cta) * kEntries);
+                        gram_units_f64(dyn, s1 - s0, &red[0][0]);
     #pragma unroll
                         for (int v = 0; v < kVec; ++v) {
                             prv[v] = cur[v];
                             cur[v] = nxt[v];
                         }
                     }
+                    nbar_sync(1, kThreads);
+                    gram_groups_f64(&red[0][0], p.partial + ((size_t)(p.nsteps - 1) * p.ncta + cta) * kEntries);
                 }
             } else {
                 // FP32: one site per thread, all 42 neighbour loads issued before the first use
