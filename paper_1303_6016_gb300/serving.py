@@ -31,15 +31,26 @@ from . import gfmc, inputs
 
 # Slots of the request loop (CTAs each); 144 of the 152 SMs, the rest stay free
 # for the set-up kernels of chains created while the server runs.
-SLOTS = [16] * 4 + [8] * 6 + [4] * 6 + [2] * 4
+SLOTS = [32] + [16] * 2 + [8] * 6 + [4] * 6 + [2] * 4
 
 
-def preferred_team(L: int) -> int:
-    if L >= 32:
+def job_work(L: int, M: int, precision: str) -> float:
+    """Relative cost of one update: sites x recursion steps, FP64 weighted by
+    the FP64/FP32 throughput ratio of the team engine (about 4)."""
+    return L ** 3 * M * (4.0 if precision == "fp64" else 1.0)
+
+
+def preferred_team(L: int, M: int = 1024, precision: str = "fp32_mixed") -> int:
+    """Slot size for a job: the costliest jobs (FP64 at the largest L and M)
+    get the widest slot so that they do not set the tail latency alone."""
+    w = job_work(L, M, precision)
+    if w >= 2.0e8:
+        return 32
+    if w >= 4.0e7:
         return 16
-    if L >= 24:
+    if w >= 1.0e7:
         return 8
-    if L >= 16:
+    if w >= 2.5e6:
         return 4
     return 2
 
@@ -103,8 +114,10 @@ class Scheduler:
         self.used += fb
         return True
 
-    def _slot_for(self, L):
-        want = preferred_team(L)
+    def _slot_for(self, c):
+        sp = self.specs[c]
+        L = sp["L"]
+        want = preferred_team(L, sp["M"], sp["precision"])
         cand = sorted((s for s in self.free if self.slots[s] <= L ** 3),
                       key=lambda s: (abs(self.slots[s] - want), -self.slots[s]))
         return cand[0] if cand else None
@@ -126,7 +139,7 @@ class Scheduler:
                 if c in self.busy_chain or not self._resident(c):
                     waiting.append((t_arr, c))
                     continue
-                s = self._slot_for(self.specs[c]["L"])
+                s = self._slot_for(c)
                 if s is None:
                     waiting.append((t_arr, c))
                     continue
