@@ -1082,7 +1082,8 @@ template <> struct GramAcc<double> {
 // barrier and no FP64 arithmetic.  The cluster barrier is split: a CTA
 // arrives once its stores of r_{m+1} are issued, reduces its warps' sums,
 // then waits.  U sites per thread have all their loads issued before any
-// arithmetic.
+// arithmetic; U = 1 (the 16 warps of an FP32 CTA hide the shared-memory
+// latency, and two sites per thread spilled registers and measured slower).
 template <class R, int NT>
 __device__ bool cluster_steps2(const Params& p, int rank, typename Cx<R>::T* vs, const int* s_loc,
                                const double2* s_c)
@@ -1091,7 +1092,7 @@ __device__ bool cluster_steps2(const Params& p, int rank, typename Cx<R>::T* vs,
     using R2 = typename Cx<R>::T;
     using Q = SOV<R>;
     using B = BondSm<R>;
-    constexpr int U = (sizeof(R) == 4 && NT <= NT) ? 2 : 1;
+    constexpr int U = 1;
     cg::cluster_group cl = cg::this_cluster();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int N = p.N, L = p.L, C = p.ncta, LL = L * L, T = N / C, P = L / C;
