@@ -143,3 +143,13 @@ def test_full_size_delta_omega_on_2m_nodes(G):
     dref, _ = O.delta_omega_from_moments(L, sp, mu, O.kernel(M), o, th, ph, beta=20.0, chem=-2.0,
                                          nodes=2 * M)
     assert abs(d - dref) <= dom_tol(dref)
+
+
+def test_largest_moment_count_on_2m_nodes(G):
+    """M = 4096 on K = 8192 nodes: the largest FFT (128 KB of shared memory)."""
+    L, M = 4, 4096
+    sp = inputs.uniform_sphere(L, 77)
+    with G.Chain(L, sp, M=M, beta=20.0, mu=-2.0, nodes=2 * M) as ch:
+        d = ch.delta_omega(9, 2.0, 1.0)
+    ref = O.delta_omega(L, sp, 9, 2.0, 1.0, M, beta=20.0, chem=-2.0, nodes=2 * M)
+    assert abs(d - ref) <= dom_tol(ref)
