@@ -1096,6 +1096,12 @@ __device__ bool cluster_steps2(const Params& p, int rank, typename Cx<R>::T* vs,
     cg::cluster_group cl = cg::this_cluster();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int N = p.N, L = p.L, C = p.ncta, LL = L * L, T = N / C, P = L / C;
+    // column walk when the threads share the columns evenly (whole columns when
+    // LL is a multiple of NT, else NT / LL segments of P / nseg planes each) and
+    // a segment has two planes or more to reuse r_m along
+    const int nseg = NT >= LL && NT % LL == 0 ? NT / LL : 1;
+    const bool colmode = (nseg > 1 || LL % NT == 0) && P % nseg == 0 && P / nseg >= 2;
+    const int S = P / nseg, seg0 = nseg > 1 ? tid / LL : 0, col0 = tid - seg0 * LL, z0 = seg0 * S;
     const int s0 = rank * T;
     Q* vq = (Q*)vs;
     B* fb = (B*)(vq + 2 * (size_t)T);
@@ -1171,6 +1177,59 @@ __device__ bool cluster_steps2(const Params& p, int rank, typename Cx<R>::T* vs,
         Q* wr = vq + (size_t)(b ^ 1) * T;
         const unsigned rd_off = (unsigned)b * (unsigned)T * (unsigned)sizeof(Q);
         GramAcc<R> g;
+        if (colmode) {
+            // columns along z: a thread walks the S sites of each of its column
+            // segments with a window of r_m below / at / above the site in
+            // registers, so a site costs 4 in-plane loads, the one above, its
+            // r_{m-1} and 5 bonds (the backward z bond is the forward z bond of
+            // the site below)
+            for (int col = col0; col < LL; col += NT) {
+                const int y = (int)__umulhi((unsigned)col, p.divL);
+                const int x = col - y * L;
+                const int dxp = x == L - 1 ? -(L - 1) : 1, dxm = x == 0 ? L - 1 : -1;
+                const int dyp = y == L - 1 ? -(L - 1) * L : L, dym = y == 0 ? (L - 1) * L : -L;
+                Q below, cz = rd[z0 * LL + col];
+                B hzb;
+                if (z0 == 0) {  // the site below is in the slab's top plane of the CTA below
+                    const int top = (P - 1) * LL + col;
+                    ld_dsm(base_dn + rd_off + (unsigned)top * (unsigned)sizeof(Q), below);
+                    ld_dsm(base_dn + fb_off + (unsigned)(2 * T + top) * (unsigned)sizeof(B), hzb);
+                } else {
+                    below = rd[(z0 - 1) * LL + col];
+                    hzb = fb[2 * T + (z0 - 1) * LL + col];
+                }
+                for (int zl = z0; zl < z0 + S; ++zl) {
+                    const int sl = zl * LL + col;
+                    Q nv[4], above;
+                    B h[5];
+                    if (zl == P - 1) ld_dsm(base_up + rd_off + (unsigned)col * (unsigned)sizeof(Q), above);
+                    else above = rd[sl + LL];
+                    nv[0] = rd[sl + dxp];
+                    nv[1] = rd[sl + dxm];
+                    nv[2] = rd[sl + dyp];
+                    nv[3] = rd[sl + dym];
+                    h[0] = fb[sl];
+                    h[1] = fb[sl + dxm];
+                    h[2] = fb[T + sl];
+                    h[3] = fb[T + sl + dym];
+                    h[4] = fb[2 * T + sl];
+                    const Q prv = wr[sl];
+                    Stencil<R> st;
+                    st.add(h[0], nv[0], true);
+                    st.add(h[1], nv[1], false);
+                    st.add(h[2], nv[2], true);
+                    st.add(h[3], nv[3], false);
+                    st.add(h[4], above, true);
+                    st.add(hzb, below, false);
+                    const Q nx = st.next(prv);
+                    wr[sl] = nx;
+                    g.add(cz, nx);
+                    below = cz;
+                    cz = above;
+                    hzb = h[4];
+                }
+            }
+        } else
         for (int sl0 = tid; sl0 < T; sl0 += U * NT) {
             Q nv[U][6], cur[U], prv[U];
             B h[U][6];

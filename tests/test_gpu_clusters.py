@@ -96,7 +96,7 @@ def test_clusters_continue_a_chain_and_a_full_sweep_measures(G):
 def test_fp32_clusters_equal_the_chain_alone(G):
     """FP32-mixed chains on clusters of 1 to 16 CTAs against the same chains on
     the single-chain engine."""
-    specs = [(8, 1), (8, 4), (12, 4), (16, 8), (16, 16)]
+    specs = [(8, 1), (8, 4), (12, 4), (16, 1), (16, 2), (16, 8), (16, 16)]
     M, n = 128, 40
     mix, alone = [], []
     for c, (L, _) in enumerate(specs):
