@@ -477,6 +477,22 @@ __device__ __forceinline__ void gram_fill(const R2 (&rc)[kVec], const R2 (&rn)[k
     if constexpr (Q + 1 < 14) gram_fill<R, R2, C, Q + 1>(rc, rn, vals);
 }
 
+// As gram_fill, for two sites (a, b) summed in the thread before the warp sums.
+template <class R, class R2, int C, int Q>
+__device__ __forceinline__ void gram_fill2(const R2 (&ca)[kVec], const R2 (&na)[kVec], const R2 (&cb)[kVec],
+                                           const R2 (&nb)[kVec], R (&vals)[32])
+{
+    constexpr int e = 14 * C + Q;
+    constexpr int g = e / kPairs, pp = e % kPairs;
+    constexpr int j = pair_j(pp), k = pair_k(pp);
+    const R2 x = ca[j], u = cb[j];
+    const R2 y = (g == 0) ? ca[k] : na[k];
+    const R2 w = (g == 0) ? cb[k] : nb[k];
+    vals[2 * Q] = fma(x.x, y.x, fma(x.y, y.y, fma(u.x, w.x, u.y * w.y)));
+    vals[2 * Q + 1] = (g == 0 && j == k) ? (R)0 : fma(x.x, y.y, fma(-x.y, y.x, fma(u.x, w.y, -(u.y * w.x))));
+    if constexpr (Q + 1 < 14) gram_fill2<R, R2, C, Q + 1>(ca, na, cb, nb, vals);
+}
+
 // conj(x_j) y_k for the 14 entries of chunk C, summed over the warp; lane l < 28
 // stores real component l of the chunk into dst[28 C + l].
 template <class R, class R2, int C>
@@ -503,13 +519,15 @@ __device__ __forceinline__ void gram_chunk_reduce_raw(const R2 (&rc)[kVec], cons
     if (lane < 28) dst[28 * C + lane] = s;
 }
 
-// As gram_chunk_reduce, but adding the chunk's warp sums to dst.
+// As gram_chunk_reduce for the products of two sites per thread, adding the
+// chunk's warp sums to dst.
 template <class R, class R2, int C>
-__device__ __forceinline__ void gram_chunk_accumulate(const R2 (&rc)[kVec], const R2 (&rn)[kVec], int lane,
-                                                      double* dst)
+__device__ __forceinline__ void gram_chunk_accumulate2(const R2 (&ca)[kVec], const R2 (&na)[kVec],
+                                                       const R2 (&cb)[kVec], const R2 (&nb)[kVec], int lane,
+                                                       double* dst)
 {
     R vals[32];
-    gram_fill<R, R2, C, 0>(rc, rn, vals);
+    gram_fill2<R, R2, C, 0>(ca, na, cb, nb, vals);
 #pragma unroll
     for (int qq = 28; qq < 32; ++qq) vals[qq] = (R)0;
     const R s = warp_reduce_scatter32(vals, lane);
@@ -710,14 +728,13 @@ __device__ bool team_steps(const Params& p, int cta, unsigned phase, typename Cx
         R2* wr = (m & 1) ? buf0 : buf1;        // r_{m-1}, overwritten by r_{m+1}
         double* prow = p.partial + ((size_t)(m - 1) * p.ncta + cta) * kEntries;
         if constexpr (sizeof(R) == 4) {
-            // chunks of kThreads sites, one per thread: all loads issued before the first use,
-            // Gram sums by warp butterfly per chunk into this warp's FP64 row of red
+            // chunks of kThreads sites, one per thread: all loads issued before the first use;
+            // the Gram products of two chunks summed in the thread, then by warp butterfly
+            // into this warp's FP64 row of red
             for (int e = lane; e < kEntries; e += 32) red[warp][e] = 0.0;
             const int T = s1 - s0;
             const int nch = (T + kThreads - 1) / kThreads;
-            for (int c = 0; c < nch; ++c) {
-                const int i = s0 + c * kThreads + tid;
-                R2 cur[kVec], nxt[kVec];
+            auto site = [&](int i, R2 (&cur)[kVec], R2 (&nxt)[kVec]) {
                 if (i < s1) {
                     int nb[6];
                     site_nbrs(i, L, p.divL, p.divLL, nb);
@@ -746,10 +763,15 @@ __device__ bool team_steps(const Params& p, int cta, unsigned phase, typename Cx
                         nxt[v] = c_make<R2>(0, 0);
                     }
                 }
-                gram_chunk_accumulate<R, R2, 0>(cur, nxt, lane, red[warp]);
-                gram_chunk_accumulate<R, R2, 1>(cur, nxt, lane, red[warp]);
-                gram_chunk_accumulate<R, R2, 2>(cur, nxt, lane, red[warp]);
-                gram_chunk_accumulate<R, R2, 3>(cur, nxt, lane, red[warp]);
+            };
+            for (int c = 0; c < nch; c += 2) {
+                R2 ca[kVec], na[kVec], cb[kVec], nb2[kVec];
+                site(s0 + c * kThreads + tid, ca, na);
+                site(s0 + (c + 1) * kThreads + tid, cb, nb2);  // past s1 (odd nch): zeros
+                gram_chunk_accumulate2<R, R2, 0>(ca, na, cb, nb2, lane, red[warp]);
+                gram_chunk_accumulate2<R, R2, 1>(ca, na, cb, nb2, lane, red[warp]);
+                gram_chunk_accumulate2<R, R2, 2>(ca, na, cb, nb2, lane, red[warp]);
+                gram_chunk_accumulate2<R, R2, 3>(ca, na, cb, nb2, lane, red[warp]);
             }
             publish(p, cta, phase + (unsigned)m + 1u);
             if (tid < kEntries) {
@@ -867,28 +889,34 @@ __device__ bool team_steps2(const Params& p, int cta, unsigned phase, typename C
         R acc[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) acc[e] = (R)0;
-        for (int i = s0 + tid; i < s1; i += kThreads) {
+        // one site's operands: its bonds, the neighbours' r_m of o and v, its r_m and r_{m-1}
+        struct Ops {
+            R2 h[6], nv[2][6], cur[2], pv[2];
+        };
+        auto load = [&](int i, Ops& q) {
             int nb[6];
             site_nbrs(i, L, p.divL, p.divLL, nb);
-            R2 h[6], nv[2][6];
 #pragma unroll
-            for (int d = 0; d < 6; ++d) h[d] = hop_of(hop, N, i, d, nb[d]);
-#pragma unroll
-            for (int v = 0; v < 2; ++v)
-#pragma unroll
-                for (int d = 0; d < 6; ++d) nv[v][d] = vm.ld(rd + (size_t)v * N + nb[d]);
-            R2 cur[2], nxt[2];
+            for (int d = 0; d < 6; ++d) q.h[d] = hop_of(hop, N, i, d, nb[d]);
 #pragma unroll
             for (int v = 0; v < 2; ++v) {
-                cur[v] = vm.ld(rd + (size_t)v * N + i);
-                const R2 pv = vm.ld(wr + (size_t)v * N + i);
+#pragma unroll
+                for (int d = 0; d < 6; ++d) q.nv[v][d] = vm.ld(rd + (size_t)v * N + nb[d]);
+                q.cur[v] = vm.ld(rd + (size_t)v * N + i);
+                q.pv[v] = vm.ld(wr + (size_t)v * N + i);
+            }
+        };
+        auto step = [&](int i, const Ops& q) {
+            R2 nxt[2];
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
                 R2 a = c_make<R2>(0, 0);
 #pragma unroll
-                for (int d = 0; d < 6; ++d) c_fma(a, h[d], nv[v][d]);
-                nxt[v] = c_make<R2>(fma((R)2, a.x, -pv.x), fma((R)2, a.y, -pv.y));
+                for (int d = 0; d < 6; ++d) c_fma(a, q.h[d], q.nv[v][d]);
+                nxt[v] = c_make<R2>(fma((R)2, a.x, -q.pv[v].x), fma((R)2, a.y, -q.pv[v].y));
                 if (m < p.nsteps) vm.st(wr + (size_t)v * N + i, nxt[v]);
             }
-            const R2 a = cur[0], b = cur[1], na = nxt[0], nbv = nxt[1];
+            const R2 a = q.cur[0], b = q.cur[1], na = nxt[0], nbv = nxt[1];
             acc[0] = fma(a.x, a.x, fma(a.y, a.y, acc[0]));
             acc[1] = fma(b.x, b.x, fma(b.y, b.y, acc[1]));
             acc[2] = fma(a.x, b.x, fma(a.y, b.y, acc[2]));
@@ -897,6 +925,24 @@ __device__ bool team_steps2(const Params& p, int cta, unsigned phase, typename C
             acc[5] = fma(b.x, nbv.x, fma(b.y, nbv.y, acc[5]));
             acc[6] = fma(a.x, nbv.x, fma(a.y, nbv.y, acc[6]));
             acc[7] = fma(a.x, nbv.y, fma(-a.y, nbv.x, acc[7]));
+        };
+        if constexpr (sizeof(R) == 4) {
+            // two sites per pass, both sites' loads issued before the first use
+            // (the sites are still summed in the order i, i + kThreads, ...)
+            for (int i = s0 + tid; i < s1; i += 2 * kThreads) {
+                const int j = i + kThreads;
+                Ops qa, qb;
+                load(i, qa);
+                if (j < s1) load(j, qb);
+                step(i, qa);
+                if (j < s1) step(j, qb);
+            }
+        } else {
+            for (int i = s0 + tid; i < s1; i += kThreads) {
+                Ops q;
+                load(i, q);
+                step(i, q);
+            }
         }
         publish(p, cta, phase + (unsigned)m + 1u);
         const R s8 = warp_reduce_scatter8(acc, lane);
