@@ -66,6 +66,27 @@ template <class T> __device__ __forceinline__ void c_fma(T& acc, T h, T r)
     acc.y = fma(h.y, r.x, acc.y);
 }
 
+// sum over the six bonds of h_d r_d (complex).  FP64: c_fma in bond order.
+// FP32: packed FMAs, (Re h)(Re r, Im r) and (Im h)(Re r, Im r) summed apart
+// and combined at the end (two packed FMAs per bond instead of four FMAs).
+__device__ __forceinline__ double2 bond_sum6(const double2 (&h)[6], const double2 (&r)[6])
+{
+    double2 a = make_double2(0.0, 0.0);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) c_fma(a, h[d], r[d]);
+    return a;
+}
+__device__ __forceinline__ float2 bond_sum6(const float2 (&h)[6], const float2 (&r)[6])
+{
+    float2 A = make_float2(0.f, 0.f), B = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int d = 0; d < 6; ++d) {
+        A = __ffma2_rn(make_float2(h[d].x, h[d].x), r[d], A);
+        B = __ffma2_rn(make_float2(h[d].y, h[d].y), r[d], B);
+    }
+    return make_float2(A.x - B.y, A.y + B.x);
+}
+
 __device__ __forceinline__ double2 dmul(double2 a, double2 b)
 {
     return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -750,9 +771,7 @@ __device__ bool team_steps(const Params& p, int cta, unsigned phase, typename Cx
                     }
 #pragma unroll
                     for (int v = 0; v < kVec; ++v) {
-                        R2 a = c_make<R2>(0, 0);
-#pragma unroll
-                        for (int d = 0; d < 6; ++d) c_fma(a, h[d], nv[v][d]);
+                        const R2 a = bond_sum6(h, nv[v]);
                         nxt[v] = c_make<R2>(fma((R)2, a.x, -pv[v].x), fma((R)2, a.y, -pv[v].y));
                         if (m < p.nsteps) vm.st(wr + (size_t)v * N + i, nxt[v]);
                     }
@@ -910,9 +929,7 @@ __device__ bool team_steps2(const Params& p, int cta, unsigned phase, typename C
             R2 nxt[2];
 #pragma unroll
             for (int v = 0; v < 2; ++v) {
-                R2 a = c_make<R2>(0, 0);
-#pragma unroll
-                for (int d = 0; d < 6; ++d) c_fma(a, q.h[d], q.nv[v][d]);
+                const R2 a = bond_sum6(q.h, q.nv[v]);
                 nxt[v] = c_make<R2>(fma((R)2, a.x, -q.pv[v].x), fma((R)2, a.y, -q.pv[v].y));
                 if (m < p.nsteps) vm.st(wr + (size_t)v * N + i, nxt[v]);
             }
