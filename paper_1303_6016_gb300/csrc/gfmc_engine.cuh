@@ -509,8 +509,23 @@ __device__ __forceinline__ void gram_fill2(const R2 (&ca)[kVec], const R2 (&na)[
     const R2 x = ca[j], u = cb[j];
     const R2 y = (g == 0) ? ca[k] : na[k];
     const R2 w = (g == 0) ? cb[k] : nb[k];
-    vals[2 * Q] = fma(x.x, y.x, fma(x.y, y.y, fma(u.x, w.x, u.y * w.y)));
-    vals[2 * Q + 1] = (g == 0 && j == k) ? (R)0 : fma(x.x, y.y, fma(-x.y, y.x, fma(u.x, w.y, -(u.y * w.x))));
+    if constexpr (sizeof(R) == 4) {
+        // packed: P = (Re x)(Re y, Im y) + (Re u)(Re w, Im w), Q likewise with
+        // Im x, Im u; Re = P.x + Q.y, Im = P.y - Q.x
+        if constexpr (g == 0 && j == k) {
+            const float2 S = __ffma2_rn(u, u, __fmul2_rn(x, x));
+            vals[2 * Q] = S.x + S.y;
+            vals[2 * Q + 1] = 0.f;
+        } else {
+            const float2 Pp = __ffma2_rn(make_float2(u.x, u.x), w, __fmul2_rn(make_float2(x.x, x.x), y));
+            const float2 Qp = __ffma2_rn(make_float2(u.y, u.y), w, __fmul2_rn(make_float2(x.y, x.y), y));
+            vals[2 * Q] = Pp.x + Qp.y;
+            vals[2 * Q + 1] = Pp.y - Qp.x;
+        }
+    } else {
+        vals[2 * Q] = fma(x.x, y.x, fma(x.y, y.y, fma(u.x, w.x, u.y * w.y)));
+        vals[2 * Q + 1] = (g == 0 && j == k) ? (R)0 : fma(x.x, y.y, fma(-x.y, y.x, fma(u.x, w.y, -(u.y * w.x))));
+    }
     if constexpr (Q + 1 < 14) gram_fill2<R, R2, C, Q + 1>(ca, na, cb, nb, vals);
 }
 
