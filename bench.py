@@ -66,8 +66,8 @@ def update_work(L: int, M: int, real_bytes: int, nv: int = 7):
 # were taken from: bench.py reports them as roofline.traffic while the hash of
 # those sources is unchanged, and null otherwise.
 TRAFFIC_SOURCES = ("gfmc_engine.cuh", "gfmc_k64.cu", "gfmc_k32.cu", "gfmc_internal.h")
-TRAFFIC_HASH = "ce0550d0a9b829cc"
-TRAFFIC_PER_UPDATE = {"fp64": 31.777536e6, "fp32_mixed": 34.307072e6}
+TRAFFIC_HASH = "7e6543fba30ff9e5"
+TRAFFIC_PER_UPDATE = {"fp64": 41.604864e6, "fp32_mixed": 40.905344e6}
 
 
 def engine_sources_hash() -> str:
@@ -243,7 +243,7 @@ def sweep_latency(gfmc, inputs, stream, L, M, precision, sweeps, warmup=2):
             "p99_ms": p99}
 
 
-def run_batching(stream, steps, warmup, updates, flush, recursion="unit_vectors"):
+def run_batching(stream, steps, warmup, updates, flush, recursion="unit_vectors", graphs=True):
     """64 independent FP32-mixed chains, L from {8,12,16,24,32}, T ~ U[0.02, 0.2],
     M = 1024, in team-engine launches planned by the autotuner; a step runs
     `updates` updates of every chain."""
@@ -276,7 +276,7 @@ def run_batching(stream, steps, warmup, updates, flush, recursion="unit_vectors"
     nv = 2 if recursion == "proposal" else 7
     _, bytes_u = zip(*[update_work(int(L), 1024, 4, nv) for L in Ls])
     graph = None
-    if len(plan) == 1:
+    if graphs and len(plan) == 1:
         # the same step captured once in a CUDA graph (gfmc_plan_*) and replayed
         from paper_1303_6016_gb300 import gfmc
         w, tc = plan[0]
@@ -309,7 +309,7 @@ def run_batching(stream, steps, warmup, updates, flush, recursion="unit_vectors"
                       "mu = -2t, M = 1024, FP32-mixed, spins uniform (seed = chain index)"}
 
 
-def run_batching_clusters(stream, steps, warmup, updates, flush):
+def run_batching_clusters(stream, steps, warmup, updates, flush, graphs=True):
     """The 64-chain batching workload on thread-block clusters (proposal-vector
     recursion, FP32-mixed): each chain's lattice in the shared memory of the
     smallest cluster that holds it; a step runs `updates` updates of every
@@ -336,30 +336,33 @@ def run_batching_clusters(stream, steps, warmup, updates, flush):
     n = len(chains)
     by_L = {str(int(L)): c for L, c in sorted(zip(Ls, runner.cluster_ctas))}
     # the same steps captured once in a CUDA graph (gfmc_plan_*) and replayed
-    from paper_1303_6016_gb300 import gfmc
-    ordered, sizes = runner.ordered()
-    with gfmc.Plan(ordered, [updates] * n, sizes, schedule="clusters") as plan:
-        plan.launch(warmup)
-        plan.sync(trace=False)
-        perg = []
-        for k in range(steps):
-            flush.fill_(k)
-            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s.record()
-            plan.launch(1)
-            e.record()
-            e.synchronize()
-            perg.append(s.elapsed_time(e))
-        plan.sync(trace=False)
-    totg = sum(perg)
+    graph = None
+    if graphs:
+        from paper_1303_6016_gb300 import gfmc
+        ordered, sizes = runner.ordered()
+        with gfmc.Plan(ordered, [updates] * n, sizes, schedule="clusters") as plan:
+            plan.launch(warmup)
+            plan.sync(trace=False)
+            perg = []
+            for k in range(steps):
+                flush.fill_(k)
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.record()
+                plan.launch(1)
+                e.record()
+                e.synchronize()
+                perg.append(s.elapsed_time(e))
+            plan.sync(trace=False)
+        totg = sum(perg)
+        graph = {"value": n * updates * steps / (totg / 1000.0), "unit": UNIT, "ms_per_step": totg / steps,
+                 "note": "one CUDA graph launch per step (gfmc_plan_launch), no host work between steps"}
     for ch in chains:
         ch.close()
     _, bytes_u = zip(*[update_work(int(L), 1024, 4, 2) for L in Ls])
     return {"value": n * updates * steps / (total / 1000.0), "unit": UNIT, "chains": n,
             "updates_per_chain_per_step": updates, "ms_per_step": total / steps,
             "stencil_gbs": sum(bytes_u) * updates / (total / steps / 1000.0) / 1e9,
-            "graph": {"value": n * updates * steps / (totg / 1000.0), "unit": UNIT, "ms_per_step": totg / steps,
-                      "note": "one CUDA graph launch per step (gfmc_plan_launch), no host work between steps"},
+            "graph": graph,
             "cluster_ctas_by_L": by_L, "recursion": "proposal", "autotune_s": tune_s,
             "tuned_ms_per_step": runner.makespan * 1e3 if runner.makespan else None,
             "config": "the batching workload (64 chains, L from {8,12,16,24,32}, M = 1024, FP32-mixed), "
@@ -491,6 +494,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-variant", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="skip the CUDA-graph replays of the batch steps")
     ap.add_argument("--batch-updates", type=int, default=4)
     ap.add_argument("--latency-sweeps", type=int, default=5)
     args = ap.parse_args()
@@ -592,12 +597,14 @@ def main():
                            "ms_per_update": totv2 / args.steps / Um}}
 
     if not args.no_batch:
-        line["batching"] = run_batching(stream, max(3, args.steps // 2), 3, args.batch_updates, flush)
+        graphs = not args.no_graph
+        line["batching"] = run_batching(stream, max(3, args.steps // 2), 3, args.batch_updates, flush,
+                                        graphs=graphs)
         if not args.no_variant:
             line["batching_proposal_recursion"] = run_batching(stream, max(3, args.steps // 2), 3,
-                                                               args.batch_updates, flush, "proposal")
+                                                               args.batch_updates, flush, "proposal", graphs)
             line["batching_clusters"] = run_batching_clusters(stream, max(3, args.steps // 2), 3,
-                                                              args.batch_updates, flush)
+                                                              args.batch_updates, flush, graphs)
 
     if not args.no_mixed:
         # FP32-mixed against the FP64 path on the same chain: Delta Omega error per
