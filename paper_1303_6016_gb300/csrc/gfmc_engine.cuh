@@ -555,8 +555,20 @@ __device__ __forceinline__ void gram_chunk_reduce_raw(const R2 (&rc)[kVec], cons
     if (lane < 28) dst[28 * C + lane] = s;
 }
 
-// As gram_chunk_reduce for the products of two sites per thread, adding the
-// chunk's warp sums to dst.
+// As gram_chunk_reduce, but adding the chunk's warp sums to dst.
+template <class R, class R2, int C>
+__device__ __forceinline__ void gram_chunk_accumulate(const R2 (&rc)[kVec], const R2 (&rn)[kVec], int lane,
+                                                      double* dst)
+{
+    R vals[32];
+    gram_fill<R, R2, C, 0>(rc, rn, vals);
+#pragma unroll
+    for (int qq = 28; qq < 32; ++qq) vals[qq] = (R)0;
+    const R s = warp_reduce_scatter32(vals, lane);
+    if (lane < 28) dst[28 * C + lane] += (double)s;
+}
+
+// As gram_chunk_accumulate for the products of two sites per thread.
 template <class R, class R2, int C>
 __device__ __forceinline__ void gram_chunk_accumulate2(const R2 (&ca)[kVec], const R2 (&na)[kVec],
                                                        const R2 (&cb)[kVec], const R2 (&nb)[kVec], int lane,
@@ -725,7 +737,7 @@ __device__ __forceinline__ void site_nbrs(int i, int L, unsigned mL, unsigned mL
 // Phase 0 and the stencil steps of one update for a team CTA whose tile may
 // hold any number of sites: every vector value lives in memory (vm), the
 // thread walks its sites s0 + tid, s0 + tid + kThreads, ...
-template <class R, class V>
+template <class R, class V, bool WIDE = true>
 __device__ bool team_steps(const Params& p, int cta, unsigned phase, typename Cx<R>::T* buf0,
                            typename Cx<R>::T* buf1, const int* s_loc, double (*red)[kEntries], double2* dyn,
                            V vm)
@@ -798,14 +810,25 @@ __device__ bool team_steps(const Params& p, int cta, unsigned phase, typename Cx
                     }
                 }
             };
-            for (int c = 0; c < nch; c += 2) {
-                R2 ca[kVec], na[kVec], cb[kVec], nb2[kVec];
-                site(s0 + c * kThreads + tid, ca, na);
-                site(s0 + (c + 1) * kThreads + tid, cb, nb2);  // past s1 (odd nch): zeros
-                gram_chunk_accumulate2<R, R2, 0>(ca, na, cb, nb2, lane, red[warp]);
-                gram_chunk_accumulate2<R, R2, 1>(ca, na, cb, nb2, lane, red[warp]);
-                gram_chunk_accumulate2<R, R2, 2>(ca, na, cb, nb2, lane, red[warp]);
-                gram_chunk_accumulate2<R, R2, 3>(ca, na, cb, nb2, lane, red[warp]);
+            if constexpr (WIDE) {
+                for (int c = 0; c < nch; c += 2) {
+                    R2 ca[kVec], na[kVec], cb[kVec], nb2[kVec];
+                    site(s0 + c * kThreads + tid, ca, na);
+                    site(s0 + (c + 1) * kThreads + tid, cb, nb2);  // past s1 (odd nch): zeros
+                    gram_chunk_accumulate2<R, R2, 0>(ca, na, cb, nb2, lane, red[warp]);
+                    gram_chunk_accumulate2<R, R2, 1>(ca, na, cb, nb2, lane, red[warp]);
+                    gram_chunk_accumulate2<R, R2, 2>(ca, na, cb, nb2, lane, red[warp]);
+                    gram_chunk_accumulate2<R, R2, 3>(ca, na, cb, nb2, lane, red[warp]);
+                }
+            } else {
+                for (int c = 0; c < nch; ++c) {
+                    R2 ca[kVec], na[kVec];
+                    site(s0 + c * kThreads + tid, ca, na);
+                    gram_chunk_accumulate<R, R2, 0>(ca, na, lane, red[warp]);
+                    gram_chunk_accumulate<R, R2, 1>(ca, na, lane, red[warp]);
+                    gram_chunk_accumulate<R, R2, 2>(ca, na, lane, red[warp]);
+                    gram_chunk_accumulate<R, R2, 3>(ca, na, lane, red[warp]);
+                }
             }
             publish(p, cta, phase + (unsigned)m + 1u);
             if (tid < kEntries) {
@@ -864,7 +887,7 @@ __device__ bool team_steps(const Params& p, int cta, unsigned phase, typename Cx
 
 // Phase 0 and the steps of one update of a team CTA for the recursion on the
 // proposal's vectors o and v (any number of sites per thread, vectors in vm).
-template <class R, class V>
+template <class R, class V, bool WIDE = true>
 __device__ bool team_steps2(const Params& p, int cta, unsigned phase, typename Cx<R>::T* buf0,
                             typename Cx<R>::T* buf1, const int* s_loc, const double2* s_c,
                             double (*red)[kEntries], V vm)
@@ -958,7 +981,7 @@ __device__ bool team_steps2(const Params& p, int cta, unsigned phase, typename C
             acc[6] = fma(a.x, nbv.x, fma(a.y, nbv.y, acc[6]));
             acc[7] = fma(a.x, nbv.y, fma(-a.y, nbv.x, acc[7]));
         };
-        if constexpr (sizeof(R) == 4) {
+        if constexpr (WIDE && sizeof(R) == 4) {
             // two sites per pass, both sites' loads issued before the first use
             // (the sites are still summed in the order i, i + kThreads, ...)
             for (int i = s0 + tid; i < s1; i += 2 * kThreads) {
@@ -1394,7 +1417,10 @@ template <int VARIANT> __device__ __forceinline__ bool chain_barrier(const Param
 // vectors |o> and |v> = Delta~|o> only: the paper's recursion on the
 // combined vectors o, v, o+v, o+iv (Algorithm 1) reduced by linearity to two
 // recursions and the cross product <o|T_n|v>; single-chain variant only.
-template <class R, int VARIANT, int NV = kVec, int NT = kThreads>
+// WIDE: the team variant's FP32 paths take two sites per thread per pass (more
+// registers); the server kernel, which holds every instantiation in one kernel,
+// takes one.
+template <class R, int VARIANT, int NV = kVec, int NT = kThreads, bool WIDE = true>
 __device__ __forceinline__ void run_chain(const Params& p, const int cta, double2* dyn,
                                           typename Cx<R>::T* vec_smem)
 {
@@ -1837,15 +1863,17 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
             cluster_steps2<R, NT>(p, cta, vec_smem, s_loc, s_c);
         } else if constexpr (NV == 2) {
             if (vec_smem) {
-                if (!team_steps2<R>(p, cta, phase, buf0, buf1, s_loc, s_c, red, SmemVec{})) return;
+                if (!team_steps2<R, SmemVec, WIDE>(p, cta, phase, buf0, buf1, s_loc, s_c, red, SmemVec{})) return;
             } else {
-                if (!team_steps2<R>(p, cta, phase, buf0, buf1, s_loc, s_c, red, GlobalVec{})) return;
+                if (!team_steps2<R, GlobalVec, WIDE>(p, cta, phase, buf0, buf1, s_loc, s_c, red, GlobalVec{}))
+                    return;
             }
         } else {
             if (vec_smem) {
-                if (!team_steps<R>(p, cta, phase, buf0, buf1, s_loc, red, dyn, SmemVec{})) return;
+                if (!team_steps<R, SmemVec, WIDE>(p, cta, phase, buf0, buf1, s_loc, red, dyn, SmemVec{})) return;
             } else {
-                if (!team_steps<R>(p, cta, phase, buf0, buf1, s_loc, red, dyn, GlobalVec{})) return;
+                if (!team_steps<R, GlobalVec, WIDE>(p, cta, phase, buf0, buf1, s_loc, red, dyn, GlobalVec{}))
+                    return;
             }
         }
         phase += (unsigned)p.nsteps + 1u;

@@ -87,11 +87,11 @@ __global__ void __launch_bounds__(kThreads, 1) gfmc_server_kernel(ServerArgs a)
         if (cmd == kExit) return;
         last = cmd;
         if (s_prec == 0) {
-            if (sp.nv == 2) run_chain<double, 1, 2>(sp, s_cta, work, nullptr);
-            else run_chain<double, 1>(sp, s_cta, work, nullptr);
+            if (sp.nv == 2) run_chain<double, 1, 2, kThreads, false>(sp, s_cta, work, nullptr);
+            else run_chain<double, 1, kVec, kThreads, false>(sp, s_cta, work, nullptr);
         } else {
-            if (sp.nv == 2) run_chain<float, 1, 2>(sp, s_cta, work, nullptr);
-            else run_chain<float, 1>(sp, s_cta, work, nullptr);
+            if (sp.nv == 2) run_chain<float, 1, 2, kThreads, false>(sp, s_cta, work, nullptr);
+            else run_chain<float, 1, kVec, kThreads, false>(sp, s_cta, work, nullptr);
         }
         grid_barrier(sp, 9);  // every CTA of the slot is done with the job
         if (s_cta == 0 && threadIdx.x == 0) {
