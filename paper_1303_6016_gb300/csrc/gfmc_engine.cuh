@@ -1274,8 +1274,8 @@ __device__ bool cluster_steps2(const Params& p, int rank, typename Cx<R>::T* vs,
 
     for (int m = 1; m <= p.nsteps; ++m) {
         const int b = m & 1;  // buffer of r_m; the other holds r_{m-1}, overwritten by r_{m+1}
-        const Q* rd = vq + (size_t)b * T;
-        Q* wr = vq + (size_t)(b ^ 1) * T;
+        const Q* __restrict__ rd = vq + (size_t)b * T;
+        Q* __restrict__ wr = vq + (size_t)(b ^ 1) * T;
         const unsigned rd_off = (unsigned)b * (unsigned)T * (unsigned)sizeof(Q);
         GramAcc<R> g;
         if (colmode) {
@@ -1299,6 +1299,7 @@ __device__ bool cluster_steps2(const Params& p, int rank, typename Cx<R>::T* vs,
                     below = rd[(z0 - 1) * LL + col];
                     hzb = fb[2 * T + (z0 - 1) * LL + col];
                 }
+#pragma unroll 2
                 for (int zl = z0; zl < z0 + S; ++zl) {
                     const int sl = zl * LL + col;
                     Q nv[4], above;
@@ -1555,6 +1556,11 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 stcg2(buf1 + (size_t)N + i, cur[1]);
             }
             publish(p, cta, phase + 1);
+            if constexpr (sizeof(R) == 8) {
+                // the FP64 steps use 2 Htilde (exact scaling) so each step is FMAs only
+#pragma unroll
+                for (int d = 0; d < 6; ++d) h[d] = c_make<R2>(2 * h[d].x, 2 * h[d].y);
+            }
 
             // ---- steps: two recursions and the 8 real products of the doubling ----
             // Each warp leaves its 8 sums of step m (type R) in w8[m & 1]; they are added
@@ -1612,10 +1618,16 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 if (active) {
 #pragma unroll
                     for (int v = 0; v < 2; ++v) {
-                        R2 acc = c_make<R2>(0, 0);
+                        if constexpr (sizeof(R) == 8) {
+                            // h holds 2 Htilde: r_{m+1} = -r_{m-1} + sum_d (2 h_d) r_m(nb_d)
+                            R2 acc = c_make<R2>(-prv[v].x, -prv[v].y);
 #pragma unroll
-                        for (int d = 0; d < 6; ++d) c_fma(acc, h[d], nv[v][d]);
-                        nxt[v] = c_make<R2>(fma((R)2, acc.x, -prv[v].x), fma((R)2, acc.y, -prv[v].y));
+                            for (int d = 0; d < 6; ++d) c_fma(acc, h[d], nv[v][d]);
+                            nxt[v] = acc;
+                        } else {
+                            const R2 acc = bond_sum6(h, nv[v]);
+                            nxt[v] = c_make<R2>(fma((R)2, acc.x, -prv[v].x), fma((R)2, acc.y, -prv[v].y));
+                        }
                         if (m < p.nsteps) stcg2(wr + (size_t)v * N + i, nxt[v]);
                     }
                 } else {
