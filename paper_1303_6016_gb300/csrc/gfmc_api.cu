@@ -1392,6 +1392,7 @@ struct gfmc_server_ctx {
     cudaStream_t run_stream = nullptr, post_stream = nullptr;
     gfmc::SlotCtl* d_slots = nullptr;
     unsigned* d_shutdown = nullptr;
+    unsigned* d_quiesce = nullptr;
     volatile unsigned* h_done = nullptr;
     unsigned* d_done = nullptr;
     std::vector<unsigned> posted;
@@ -1435,10 +1436,16 @@ gfmc_status server_ensure_running(gfmc_server_ctx* s)
             (e = cudaStreamSynchronize(s->post_stream)) != cudaSuccess)
             return sfail(s, GFMC_ECUDA, "resetting slot commands: %s", cudaGetErrorString(e));
     }
+    static const unsigned zero2[2] = {0u, 0u};
+    if ((e = cudaMemcpyAsync(s->d_quiesce, zero2, sizeof(zero2), cudaMemcpyHostToDevice, s->post_stream)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(s->post_stream)) != cudaSuccess)
+        return sfail(s, GFMC_ECUDA, "resetting the idle count: %s", cudaGetErrorString(e));
     gfmc::ServerArgs a;
     a.slots = s->d_slots;
     a.done = s->d_done;
     a.shutdown = s->d_shutdown;
+    a.quiesce = s->d_quiesce;
     a.nslots = s->nslots;
     a.idle_budget = s->idle_budget;
     if ((e = gfmc::launch_server(a, s->grid, s->smem, s->run_stream)) != cudaSuccess)
@@ -1481,6 +1488,7 @@ gfmc_status gfmc_server_create(int n_slots, const int* slot_ctas, int max_M, gfm
         (e = cudaStreamCreateWithFlags(&s->post_stream, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaMalloc(&s->d_slots, sizeof(gfmc::SlotCtl) * n_slots)) != cudaSuccess ||
         (e = cudaMalloc(&s->d_shutdown, sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMalloc(&s->d_quiesce, 2 * sizeof(unsigned))) != cudaSuccess ||
         (e = cudaHostAlloc((void**)&s->h_done, sizeof(unsigned) * n_slots, cudaHostAllocMapped)) != cudaSuccess ||
         (e = cudaHostGetDevicePointer((void**)&s->d_done, (void*)s->h_done, 0)) != cudaSuccess)
         return bail(sfail(nullptr, e == cudaErrorMemoryAllocation ? GFMC_ENOMEM : GFMC_ECUDA, "server set-up: %s",
@@ -1625,6 +1633,7 @@ void gfmc_server_destroy(gfmc_server_t s)
         if (s->chain[k]) s->chain[k]->in_server = false;
     if (s->d_slots) cudaFree(s->d_slots);
     if (s->d_shutdown) cudaFree(s->d_shutdown);
+    if (s->d_quiesce) cudaFree(s->d_quiesce);
     if (s->h_done) cudaFreeHost((void*)s->h_done);
     if (s->run_stream) cudaStreamDestroy(s->run_stream);
     if (s->post_stream) cudaStreamDestroy(s->post_stream);

@@ -118,8 +118,9 @@ struct ServerArgs {
     SlotCtl* slots;
     unsigned* done;           // host-mapped: last completed sequence number per slot
     const unsigned* shutdown; // nonzero: every slot exits when idle
+    unsigned* quiesce;        // [0] slots idle for idle_budget, [1] nonzero: the launch ends (host-cleared)
     int nslots;
-    long long idle_budget;    // cycles a slot waits for work before the launch ends
+    long long idle_budget;    // cycles without work after which a slot counts as idle
 };
 
 // Launchers (defined in the kernel translation units).

@@ -9,19 +9,27 @@
 // Mailbox protocol of a slot (all waits bounded):
 //   host    writes the job (copy engine), then the slot's sequence number;
 //   CTA 0   of the slot polls the sequence number; on a new one it publishes
-//           it in the slot's command word, on shutdown or after idle_budget
-//           cycles without work it publishes EXIT;
+//           it in the slot's command word; on shutdown, or once every slot
+//           of the launch has been idle for idle_budget cycles, it publishes
+//           EXIT;
 //   others  poll the command word and follow it, so a slot never splits;
 //   slot    runs the job (run_chain, multi-site variant), meets at the job's
 //           barrier, and CTA 0 writes the sequence number into the host-mapped
 //           done word.
-// A posted job that the kernel did not take before an idle exit is taken by
-// the next launch (each launch starts from the done words).
+// The launch ends as a whole: a slot idle for idle_budget cycles joins the
+// launch's idle count (and leaves it when work arrives); the slot whose entry
+// makes every slot idle raises the exit word, which every slot's CTA 0 obeys.
+// A slot that exited on its own while others stayed busy would leave its next
+// job waiting for the whole launch to end.  A slot idle for kIdleCap budgets
+// exits regardless, so every wait stays bounded.  A posted job that the
+// kernel did not take before the exit is taken by the next launch (each
+// launch starts from the done words).
 #include "gfmc_engine.cuh"
 
 namespace gfmc {
 
 constexpr unsigned kExit = 0xFFFFFFFFu;
+constexpr long long kIdleCap = 64;  // idle budgets after which a slot exits even if others are busy
 
 __device__ __forceinline__ void st_release_sys_u32(unsigned* a, unsigned v)
 {
@@ -54,13 +62,24 @@ __global__ void __launch_bounds__(kThreads, 1) gfmc_server_kernel(ServerArgs a)
             unsigned cmd = kExit;
             const long long t0 = clock64();
             if (s_cta == 0) {
+                bool idle = false;  // this slot is counted in quiesce[0]
                 for (;;) {
                     const unsigned q = ld_acquire_u32(&sl->seq);
                     if (q != last) {
+                        if (idle) {
+                            if (ld_acquire_u32(a.quiesce + 1) != 0u) break;  // ending: the job goes to the next launch
+                            atomicSub(a.quiesce, 1u);
+                        }
                         cmd = q;
                         break;
                     }
-                    if (ld_acquire_u32(a.shutdown) != 0u || clock64() - t0 > a.idle_budget) break;
+                    if (ld_acquire_u32(a.shutdown) != 0u || ld_acquire_u32(a.quiesce + 1) != 0u) break;
+                    const long long waited = clock64() - t0;
+                    if (!idle && waited > a.idle_budget) {
+                        idle = true;
+                        if (atomicAdd(a.quiesce, 1u) + 1u == (unsigned)a.nslots) st_release_u32(a.quiesce + 1, 1u);
+                    }
+                    if (waited > kIdleCap * a.idle_budget) break;
                     __nanosleep(500);
                 }
                 st_release_u32(&sl->cmd, cmd);
@@ -71,8 +90,8 @@ __global__ void __launch_bounds__(kThreads, 1) gfmc_server_kernel(ServerArgs a)
                         cmd = c;
                         break;
                     }
-                    // the slot's CTA 0 always answers within idle_budget; allow it twice that
-                    if (clock64() - t0 > 2 * a.idle_budget + a.idle_budget / 2) break;
+                    // the slot's CTA 0 answers within kIdleCap idle budgets; allow it two more
+                    if (clock64() - t0 > (kIdleCap + 2) * a.idle_budget) break;
                     __nanosleep(500);
                 }
             }

@@ -100,6 +100,31 @@ def test_consecutive_jobs_continue_the_chain_and_idle_relaunch(G):
     ch.close()
 
 
+def test_idle_slot_takes_a_job_while_another_slot_is_busy(G):
+    """A slot idle for longer than the idle budget stays in the launch while
+    another slot works, so a job posted to it runs at once instead of waiting
+    for the busy slot's job and a relaunch."""
+    long_ch = G.Chain(12, inputs.uniform_sphere(12, 5), M=1024, seed=3)   # FP64, about 77 ms per update on 1 CTA
+    short_ch = G.Chain(6, inputs.uniform_sphere(6, 6), M=64, seed=4)
+    with G.Server([1, 1], max_M=1024) as srv:
+        srv.submit(0, long_ch, 60)
+        time.sleep(1.6)  # longer than the idle budget: slot 1 has been idle since the launch
+        t0 = time.time()
+        srv.submit(1, short_ch, 5)
+        r1 = None
+        while r1 is None:
+            r1 = srv.poll(1)
+            assert time.time() - t0 < 120.0, "server job did not finish"
+            time.sleep(0.001)
+        dt = time.time() - t0
+        assert srv.poll(0) is None, "the long job ended first: lengthen it"
+        assert dt < 0.5, dt
+        wait_all(srv, [0])
+    assert long_ch.counter == 60 and short_ch.counter == 5
+    long_ch.close()
+    short_ch.close()
+
+
 def test_busy_slot_and_busy_chain_are_rejected(G):
     L, M = 8, 64
     a = G.Chain(L, inputs.uniform_sphere(L, 1), M=M)
