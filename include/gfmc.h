@@ -262,9 +262,10 @@ void gfmc_plan_destroy(gfmc_plan_t plan);
  * are admitted as soon as a slot is free and their work overlaps on the
  * device (independent chains, Sec. 3.2).  Chain state stays in device memory
  * across jobs.  A job gives the same results as gfmc_updates on the same
- * chain, up to the rounding order of the slot's sums.  A slot that receives no
- * work for about a second lets the launch end; the next submit or poll
- * starts it again.
+ * chain, up to the rounding order of the slot's sums.  Once every slot has
+ * received no work for about a second the launch ends; the next submit or
+ * poll starts it again.  An idle slot stays in the launch while other slots
+ * work, so a job posted to it starts at once.
  * ------------------------------------------------------------------------ */
 typedef struct gfmc_server_ctx* gfmc_server_t;
 
