@@ -1842,9 +1842,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                         if (active) {
     #pragma unroll
                             for (int v = 0; v < kVec; ++v) {
-                                R2 acc = c_make<R2>(0, 0);
-    #pragma unroll
-                                for (int d = 0; d < 6; ++d) c_fma(acc, h[d], nv[v][d]);
+                                const R2 acc = bond_sum6(h, nv[v]);
                                 nxt[v] = c_make<R2>(fma((R)2, acc.x, -prv[v].x), fma((R)2, acc.y, -prv[v].y));
                                 if (m < p.nsteps) stcg2(wr + (size_t)v * N + i, nxt[v]);
                             }
