@@ -271,7 +271,7 @@ def run_batching(stream, steps, warmup, updates, flush, recursion="unit_vectors"
     teams = {}
     for w, tc in plan:
         for i, t in zip(w, tc):
-            teams.setdefault(int(Ls[i]), set()).add(int(t))
+            teams.setdefault(int(Ls[i]), set()).add(int(t))  # 0: shares a one-CTA team
     n = len(chains)
     nv = 2 if recursion == "proposal" else 7
     _, bytes_u = zip(*[update_work(int(L), 1024, 4, nv) for L in Ls])
@@ -302,6 +302,8 @@ def run_batching(stream, steps, warmup, updates, flush, recursion="unit_vectors"
     return {"value": n * updates * steps / (total / 1000.0), "unit": UNIT, "chains": n, "graph": graph,
             "updates_per_chain_per_step": updates, "ms_per_step": total / steps,
             "launches_per_step": len(plan), "team_ctas_by_L": {str(k): sorted(v) for k, v in sorted(teams.items())},
+            "shared_ctas": sum(1 for w, tc in plan for k in range(len(tc)) if tc[k] == 1 and k + 1 < len(tc)
+                               and tc[k + 1] == 0),
             "lattice_counts": {str(int(L)): int((Ls == L).sum()) for L in sorted(set(Ls.tolist()))},
             "stencil_gbs": sum(bytes_u) * updates / (total / steps / 1000.0) / 1e9,
             "autotune_s": tune_s, "recursion": recursion,

@@ -169,6 +169,10 @@ gfmc_status gfmc_get_counter(gfmc_t h, uint64_t* update_counter);
  *   team_ctas    CTAs for each chain, 1 <= team_ctas[c] <= min(N, 1024)
  *                (NULL: 1 each); the chain's per-CTA buffers grow as needed.  A one-CTA team keeps its recursion
  *                vectors in shared memory when they fit (L <= 12 FP32, L <= 10 FP64).
+ *                team_ctas[c] = 0: chain c runs after chain c-1 on that chain's one CTA
+ *                (team_ctas[c-1] is 1 or 0, the same recursion), so one CTA can run
+ *                several small chains one after another and leave the other CTAs to
+ *                large ones.
  *   n_accepted   host uint64[n_chains] or NULL.
  *   decisions    host array of n_chains pointers to uint8[n_updates[c]] (the array
  *                or any entry may be NULL); d_omega_trace likewise with double.
@@ -220,8 +224,9 @@ gfmc_status gfmc_cluster_min_ctas(int L, int M, int precision, int* cluster_ctas
 typedef struct gfmc_plan_ctx* gfmc_plan_t;
 
 /* How a plan places its chains: GFMC_SCHEDULE_TEAMS -- one cooperative launch,
- * chain c on a team of ctas[c] CTAs, as gfmc_run_batch (every precision and
- * recursion, the chains of one precision); GFMC_SCHEDULE_CLUSTERS -- chain c on
+ * chain c on a team of ctas[c] CTAs (0: after chain c-1 on its one CTA), as
+ * gfmc_run_batch (every recursion, the chains of one precision);
+ * GFMC_SCHEDULE_CLUSTERS -- chain c on
  * a thread-block cluster of ctas[c] CTAs holding its lattice, as
  * gfmc_run_clusters (chains on the proposal's vectors). */
 enum { GFMC_SCHEDULE_TEAMS = 0, GFMC_SCHEDULE_CLUSTERS = 1 };

@@ -10,9 +10,11 @@ cluster that holds its lattice in shared memory (``ClusterRunner``,
 The autotuner measures, on the device, the time of one update of a probe
 chain of each lattice size at candidate team sizes, then shares the device's
 CTAs among the chains of a batch so that the slowest chain finishes first as
-early as possible (greedy: repeatedly double the team of the chain with the
-longest projected time while the CTAs last).  Chains that do not fit in one
-launch are run in waves.
+early as possible (greedy: repeatedly grow the team of the chain with the
+longest projected time to the next probed size while the CTAs last, small
+chains sharing one CTA one after another when that frees CTAs for the large
+ones).  Chains that do not
+fit in one launch are run in waves.
 
     from paper_1303_6016_gb300 import batch
     tuner = batch.Autotuner(M=1024, precision="fp32_mixed")
@@ -27,7 +29,9 @@ import numpy as np
 
 from . import gfmc, inputs
 
-CANDIDATES = (1, 2, 4, 8, 16, 32, 64)
+# team sizes the autotuner probes (the tiles are contiguous site ranges, so any
+# size works; the in-between sizes let a large chain's team grow in small steps)
+CANDIDATES = (1, 2, 3, 4, 5, 6, 8, 12, 16, 24, 32, 64)
 
 
 def device_ctas() -> int:
@@ -94,6 +98,69 @@ class Autotuner:
             if not grown:
                 return tc
 
+    def pack(self, Ls, budget: int, work=None, kinds=None):
+        """As allocate, but small chains may share one CTA and run one after
+        another (gfmc_run_batch's team size 0), which leaves CTAs to the large
+        chains.  Greedy on the projected time of each unit (a team of one
+        chain, or a shared one-CTA team: the sum of its chains' one-CTA
+        times): grow the slowest unit's team; when the CTAs run out, merge the
+        two fastest one-CTA units while the merged unit stays faster than the
+        slowest; only chains of one kind (recursion) share a CTA.  Returns
+        (order, team sizes): chain order[k] gets tc[k] CTAs, 0 meaning after
+        order[k-1] on its CTA."""
+        work = [1.0] * len(Ls) if work is None else list(work)
+        kinds = [0] * len(Ls) if kinds is None else list(kinds)
+        tables = [self.measure(L) for L in Ls]
+        units = [[min(t), [c]] for c, t in enumerate(tables)]  # [team size, chains]
+        used = sum(u[0] for u in units)
+        if used > budget:
+            raise ValueError(f"{len(Ls)} chains need at least {used} CTAs, the device holds {budget}")
+
+        def t_unit(u):
+            if len(u[1]) == 1:
+                c = u[1][0]
+                return tables[c][u[0]] * work[c]
+            return sum(tables[c][1] * work[c] for c in u[1])
+
+        while True:
+            units.sort(key=t_unit, reverse=True)
+            top = units[0]
+            t_max = t_unit(top)
+            if len(top[1]) > 1:
+                break
+            c = top[1][0]
+            bigger = sorted(t for t in tables[c] if t > top[0])
+            if not bigger or tables[c][bigger[0]] >= tables[c][top[0]]:
+                break
+            nxt = bigger[0]
+            need = used + nxt - top[0] - budget
+            while need > 0:
+                ones = sorted((u for u in units[1:] if u[0] == 1 and all(1 in tables[k] for k in u[1])), key=t_unit)
+                pair = None
+                for x in range(len(ones)):
+                    for y in range(x + 1, len(ones)):
+                        if kinds[ones[x][1][0]] == kinds[ones[y][1][0]]:
+                            if pair is None or t_unit(ones[x]) + t_unit(ones[y]) < t_unit(pair[0]) + t_unit(pair[1]):
+                                pair = (ones[x], ones[y])
+                            break
+                if pair is None or t_unit(pair[0]) + t_unit(pair[1]) >= t_max:
+                    break
+                a, b = pair
+                a[1].extend(b[1])
+                units.remove(b)
+                used -= 1
+                need -= 1
+            if need > 0:
+                break
+            used += nxt - top[0]
+            top[0] = nxt
+        order, tc = [], []
+        for size, members in units:
+            for k, c in enumerate(members):
+                order.append(c)
+                tc.append(size if k == 0 else 0)
+        return order, tc
+
 
 class BatchRunner:
     """Runs a list of chains as batches of the team engine."""
@@ -118,8 +185,9 @@ class BatchRunner:
             waves.append(cur)
         plan = []
         for w in waves:
-            tc = self.tuner.allocate([Ls[i] for i in w], self.budget, [updates[i] for i in w])
-            plan.append((w, tc))
+            order, tc = self.tuner.pack([Ls[i] for i in w], self.budget, [updates[i] for i in w],
+                                        [self.chains[i].recursion for i in w])
+            plan.append(([w[k] for k in order], tc))
         return plan
 
     def run(self, updates_per_chain, trace: bool = False):
@@ -129,7 +197,7 @@ class BatchRunner:
         for w, tc in self.plan(updates):
             res = gfmc.run_batch([self.chains[i] for i in w], [updates[i] for i in w], team_ctas=tc, trace=trace)
             for k, i in enumerate(w):
-                out[i] = dict(res[k], team_ctas=tc[k])
+                out[i] = dict(res[k], team_ctas=tc[k])  # 0: shares the CTA of the chain before it
         return out
 
 

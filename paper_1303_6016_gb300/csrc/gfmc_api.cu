@@ -241,6 +241,24 @@ gfmc_status run_engine(gfmc_ctx* h, Params& P)
 // waits for a running server launch.
 void release(gfmc_ctx*, void*) {}
 
+// Team size of chain c in a batch: 1 .. min(N, 1024) CTAs, or 0 -- chain c
+// runs after chain c-1 on its one CTA (chain c-1 has 1 or 0 and the same
+// recursion).
+gfmc_status check_team_size(gfmc_ctx* const* chains, const int* ctas, int c)
+{
+    const int tc = ctas ? ctas[c] : 1;
+    const int tmax = std::min(chains[c]->N, 1024);
+    if (tc == 0) {
+        if (c == 0 || ctas[c - 1] > 1)
+            return fail(nullptr, GFMC_EINVAL, "team_ctas[%d] = 0 must follow a one-CTA team", c);
+        if (chains[c - 1]->recursion != chains[c]->recursion)
+            return fail(nullptr, GFMC_EINVAL, "chain %d shares a CTA with a chain on another recursion", c);
+        return GFMC_OK;
+    }
+    if (tc < 1 || tc > tmax) return fail(nullptr, GFMC_EINVAL, "team_ctas[%d] = %d outside [0, %d]", c, tc, tmax);
+    return GFMC_OK;
+}
+
 // Grow the per-CTA buffers of h to hold a team of tc CTAs.
 gfmc_status ensure_team_capacity(gfmc_ctx* h, int tc)
 {
@@ -672,9 +690,8 @@ gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_update
         if (h->precision != prec) return fail(nullptr, GFMC_EINVAL, "chain %d has another precision", c);
         if (h->device != dev) return fail(nullptr, GFMC_EINVAL, "chain %d lives on another device", c);
         if (n_updates[c] < 0) return fail(nullptr, GFMC_EINVAL, "n_updates[%d] < 0", c);
-        const int tc = team_ctas ? team_ctas[c] : 1;
-        const int tmax = std::min(h->N, 1024);
-        if (tc < 1 || tc > tmax) return fail(nullptr, GFMC_EINVAL, "team_ctas[%d] = %d outside [1, %d]", c, tc, tmax);
+        gfmc_status st = check_team_size(chains, team_ctas, c);
+        if (st != GFMC_OK) return st;
     }
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
@@ -693,7 +710,7 @@ gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_update
         const int tc = team_ctas ? team_ctas[c] : 1;
         const int nvc = chains[c]->recursion == GFMC_RECURSION_PROPOSAL ? 2 : gfmc::kVec;
         const size_t vb = 2 * (size_t)nvc * chains[c]->N * vsz;
-        if (tc == 1 && vb + work + reserve <= (size_t)dev_smem) {
+        if (tc <= 1 && vb + work + reserve <= (size_t)dev_smem) {
             resident[c] = 1;
             vec_bytes = std::max(vec_bytes, (vb + 255) & ~(size_t)255);
         }
@@ -708,10 +725,11 @@ gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_update
                     "shared memory; run it in smaller parts", grid, maxc, smem);
 
     std::vector<gfmc::TeamJob> jobs(n_chains);
-    int cta0 = 0;
+    int cta0 = 0, last0 = 0;
     for (int c = 0; c < n_chains; ++c) {
         gfmc_ctx* h = chains[c];
-        const int tc = team_ctas ? team_ctas[c] : 1;
+        const int given = team_ctas ? team_ctas[c] : 1;
+        const int tc = given == 0 ? 1 : given;  // 0: after chain c-1 on its one CTA
         gfmc_status st = ensure_trace(h, std::max<int64_t>(n_updates[c], 1));
         if (st == GFMC_OK) st = ensure_team_capacity(h, tc);
         if (st != GFMC_OK) return fail(nullptr, st, "chain %d: %s", c, h->err.c_str());
@@ -734,9 +752,12 @@ gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_update
         P.stall = 0;
         P.nv = h->recursion == GFMC_RECURSION_PROPOSAL ? 2 : gfmc::kVec;
         jobs[c].p = P;
-        jobs[c].cta0 = cta0;
+        if (given > 0) {
+            last0 = cta0;
+            cta0 += tc;
+        }
+        jobs[c].cta0 = last0;
         jobs[c].vec_smem = resident[c];
-        cta0 += tc;
         if ((e = cudaMemsetAsync(P.flags, 0, sizeof(unsigned) * tc, s)) != cudaSuccess ||
             (e = cudaMemsetAsync(P.bar, 0, sizeof(unsigned) * 2, s)) != cudaSuccess ||
             (e = cudaMemsetAsync(P.err, 0, sizeof(int) * 4, s)) != cudaSuccess ||
@@ -1114,8 +1135,8 @@ gfmc_status gfmc_plan_create(gfmc_t* chains, int n_chains, const int64_t* n_upda
                 return fail(nullptr, GFMC_EINVAL, "chain %d: %d z-planes do not split over %d CTAs", c, h->L, C);
         } else {
             if (h->precision != prec) return fail(nullptr, GFMC_EINVAL, "chain %d has another precision", c);
-            if (C < 1 || C > std::min(h->N, 1024))
-                return fail(nullptr, GFMC_EINVAL, "ctas[%d] = %d outside [1, %d]", c, C, std::min(h->N, 1024));
+            gfmc_status st = check_team_size(chains, ctas, c);
+            if (st != GFMC_OK) return st;
         }
     }
     cudaError_t e;
@@ -1214,7 +1235,7 @@ gfmc_status gfmc_plan_create(gfmc_t* chains, int n_chains, const int64_t* n_upda
         for (int c = 0; c < n_chains; ++c) {
             const int nvc = chains[c]->recursion == GFMC_RECURSION_PROPOSAL ? 2 : gfmc::kVec;
             const size_t vb = 2 * (size_t)nvc * chains[c]->N * vsz;
-            if (ctas[c] == 1 && vb + work + reserve <= (size_t)dev_smem) {
+            if (ctas[c] <= 1 && vb + work + reserve <= (size_t)dev_smem) {
                 resident[c] = 1;
                 vec_bytes = std::max(vec_bytes, (vb + 255) & ~(size_t)255);
             }
@@ -1228,10 +1249,10 @@ gfmc_status gfmc_plan_create(gfmc_t* chains, int n_chains, const int64_t* n_upda
         if (team_grid > maxc)
             return bail(fail(nullptr, GFMC_EINVAL, "the batch needs %d co-resident CTAs, the device holds %d", team_grid,
                              maxc));
-        int cta0 = 0;
+        int cta0 = 0, last0 = 0;
         for (int c = 0; c < n_chains; ++c) {
             gfmc_ctx* h = chains[c];
-            const int tc = ctas[c];
+            const int tc = ctas[c] == 0 ? 1 : ctas[c];  // 0: after chain c-1 on its one CTA
             gfmc_status st = ensure_trace(h, n_updates[c]);
             if (st == GFMC_OK) st = ensure_team_capacity(h, tc);
             if (st == GFMC_OK) st = use_team_plan(h, tc);
@@ -1243,10 +1264,13 @@ gfmc_status gfmc_plan_create(gfmc_t* chains, int n_chains, const int64_t* n_upda
             P.nv = h->recursion == GFMC_RECURSION_PROPOSAL ? 2 : gfmc::kVec;
             gfmc::TeamJob j{};
             j.p = P;
-            j.cta0 = cta0;
+            if (ctas[c] > 0) {
+                last0 = cta0;
+                cta0 += tc;
+            }
+            j.cta0 = last0;
             j.vec_smem = resident[c];
             jobs.push_back(j);
-            cta0 += tc;
             p->chains.push_back(h);
             p->caller.push_back(c);
             p->n_upd.push_back(n_updates[c]);

@@ -2197,16 +2197,46 @@ __global__ void __launch_bounds__(kThreads, 1) gfmc_team_engine(const TeamJob* _
     if (threadIdx.x == 0) {
         int j = 0;
         while (j + 1 < njobs && jobs[j + 1].cta0 <= (int)blockIdx.x) ++j;
+        // several one-CTA chains may share this CTA (same cta0): start at the first
+        while (j > 0 && jobs[j - 1].cta0 == jobs[j].cta0) --j;
         s_job = j;
-        s_cta = (int)blockIdx.x - jobs[j].cta0;
-        s_vs = jobs[j].vec_smem;
-        sp = jobs[j].p;
     }
     __syncthreads();
     using R2 = typename Cx<R>::T;
-    R2* vs = s_vs ? (R2*)dyn_all : nullptr;
-    if (sp.nv == 2) run_chain<R, 1, 2>(sp, s_cta, dyn_all + vec_bytes / (int)sizeof(double2), vs);
-    else run_chain<R, 1>(sp, s_cta, dyn_all + vec_bytes / (int)sizeof(double2), vs);
+    // the chains of this CTA's team, one after another: one chain unless the
+    // team is a shared one-CTA team, whose chains all use one recursion
+    auto load = [&]() {
+        if (threadIdx.x == 0) {
+            const int j = s_job;
+            s_cta = (int)blockIdx.x - jobs[j].cta0;
+            s_vs = jobs[j].vec_smem;
+            sp = jobs[j].p;
+        }
+        __syncthreads();
+    };
+    auto next = [&]() -> bool {
+        __syncthreads();  // every thread is done with sp and the shared memory
+        if (threadIdx.x == 0) {
+            const int j = s_job + 1;
+            s_job = (j < njobs && jobs[j].cta0 == jobs[j - 1].cta0) ? j : -1;
+        }
+        __syncthreads();
+        return s_job >= 0;
+    };
+    load();
+    if (sp.nv == 2) {
+        do {
+            run_chain<R, 1, 2>(sp, s_cta, dyn_all + vec_bytes / (int)sizeof(double2), s_vs ? (R2*)dyn_all : nullptr);
+            if (!next()) break;
+            load();
+        } while (true);
+    } else {
+        do {
+            run_chain<R, 1>(sp, s_cta, dyn_all + vec_bytes / (int)sizeof(double2), s_vs ? (R2*)dyn_all : nullptr);
+            if (!next()) break;
+            load();
+        } while (true);
+    }
 }
 
 // A batch of chains, one thread-block cluster per chain (cluster size C = the

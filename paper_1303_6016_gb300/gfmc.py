@@ -153,6 +153,7 @@ class Chain:
         self.K = int(nodes) if nodes else self.M  # Chebyshev nodes of G and of the quadrature
         self.t, self.mu, self.beta = float(t), float(mu), float(beta)
         self.precision = precision
+        self.recursion = recursion
         opt = Options()
         lib.gfmc_default_options(ctypes.byref(opt))
         opt.precision = PRECISIONS[precision]

@@ -33,3 +33,38 @@ def test_cluster_tuner_picks_the_shortest_modelled_makespan():
     durs = [4 * tuner.table[Ls[c]][sizes[c]] for c in order]
     assert durs == sorted(durs, reverse=True)
     assert all(tuner.table[L].get(C) is not None for L, C in zip(Ls, sizes))
+
+
+def test_team_packer_shares_ctas_and_shortens_the_slowest_team():
+    """Small chains share one-CTA teams (team size 0 after a 1) so that the
+    large chains' teams can grow: the packed plan fits the budget, every chain
+    appears once, every 0 follows a one-CTA team, and the slowest unit is no
+    slower than the plan without sharing."""
+    from paper_1303_6016_gb300.batch import Autotuner
+    tuner = Autotuner.__new__(Autotuner)
+    # seconds per update at each team size (the team engine's shape: about
+    # 1/n for large lattices, flat for small ones)
+    base = {8: 3.4e-3, 12: 9.2e-3, 16: 18e-3, 24: 59e-3, 32: 134e-3}
+    tuner.table = {L: {n: t / n + 1.5e-3 * (n > 1) for n in (1, 2, 3, 4, 5, 6, 8, 12, 16)} for L, t in base.items()}
+    Ls = [8] * 8 + [12] * 11 + [16] * 17 + [24] * 10 + [32] * 18
+    budget = 152
+    plain = tuner.allocate(Ls, budget)
+    order, tc = tuner.pack(Ls, budget)
+    assert sorted(order) == list(range(len(Ls)))
+    assert sum(tc) <= budget and tc[0] >= 1
+    units = []
+    for k, (c, t) in enumerate(zip(order, tc)):
+        if t == 0:
+            assert tc[k - 1] in (0, 1)
+            units[-1][1].append(c)
+        else:
+            units.append((t, [c]))
+
+    def t_unit(u):
+        t, cs = u
+        return tuner.table[Ls[cs[0]]][t] if len(cs) == 1 else sum(tuner.table[Ls[c]][1] for c in cs)
+
+    t_plain = max(tuner.table[L][t] for L, t in zip(Ls, plain))
+    t_packed = max(t_unit(u) for u in units)
+    assert any(len(cs) > 1 for _, cs in units)
+    assert t_packed < t_plain

@@ -118,9 +118,64 @@ def test_batch_rejects_oversubscription_and_bad_team(G):
         G.run_batch(chains, 1, team_ctas=[152, 152])  # more CTAs than the device holds at once
     assert e.value.status == G.GFMC_EINVAL
     with pytest.raises(G.GfmcError) as e:
-        G.run_batch(chains, 1, team_ctas=[0, 1])
+        G.run_batch(chains, 1, team_ctas=[0, 1])  # a shared team needs a one-CTA team before it
     assert e.value.status == G.GFMC_EINVAL
-    for ch in chains:
+    with pytest.raises(G.GfmcError) as e:
+        G.run_batch(chains, 1, team_ctas=[2, 0])  # ... not a two-CTA one
+    assert e.value.status == G.GFMC_EINVAL
+    prop = G.Chain(8, inputs.uniform_sphere(8, 0), M=M, precision="fp32_mixed", recursion="proposal")
+    with pytest.raises(G.GfmcError) as e:
+        G.run_batch([chains[0], prop], 1, team_ctas=[1, 0])  # ... nor one on another recursion
+    assert e.value.status == G.GFMC_EINVAL
+    assert all(ch.counter == 0 for ch in chains + [prop])
+    for ch in chains + [prop]:
+        ch.close()
+
+
+@pytest.mark.parametrize("prec,recursion", [("fp32_mixed", "unit_vectors"), ("fp64", "unit_vectors"),
+                                            ("fp32_mixed", "proposal")])
+def test_chains_sharing_a_cta_equal_the_chains_alone(G, prec, recursion):
+    """Chains with team size 0 run after the chain before them on its one CTA:
+    each gives bitwise the trace and spins it gives alone on a one-CTA team,
+    with multi-CTA teams before, between and after the shared ones (lattices
+    in shared memory and in global memory, ragged update counts)."""
+    M = 64
+    specs = [(6, 2, 5), (8, 1, 7), (5, 0, 4), (12, 0, 9), (4, 0, 3), (10, 3, 6), (7, 1, 8), (9, 0, 5), (6, 2, 4)]
+    mk = lambda c, L: G.Chain(L, inputs.uniform_sphere(L, 60 + c), M=M, precision=prec, seed=9, chain_id=c,
+                              recursion=recursion, beta=12.0)
+    mix = [mk(c, L) for c, (L, _, _) in enumerate(specs)]
+    outs = G.run_batch(mix, [n for (_, _, n) in specs], team_ctas=[t for (_, t, _) in specs])
+    for c, (L, t, n) in enumerate(specs):
+        with mk(c, L) as alone:
+            ref = G.run_batch([alone], [n], team_ctas=[max(t, 1)])[0]
+            spins = alone.get_spins()
+        assert np.array_equal(outs[c]["decisions"], ref["decisions"]), c
+        assert np.array_equal(outs[c]["d_omega"], ref["d_omega"]), c
+        assert np.array_equal(mix[c].get_spins(), spins), c
+        assert mix[c].counter == n
+    for ch in mix:
+        ch.close()
+
+
+def test_batch_plan_with_shared_ctas_equals_calls(G):
+    """A graph-captured step of a batch with a shared one-CTA team equals the
+    same step run by gfmc_run_batch."""
+    M, n = 64, [5, 3, 4, 6]
+    specs = [(8, 2), (6, 1), (5, 0), (7, 0)]
+    mk = lambda c, L: G.Chain(L, inputs.uniform_sphere(L, 80 + c), M=M, precision="fp32_mixed", seed=2,
+                              chain_id=c)
+    ref = [mk(c, L) for c, (L, _) in enumerate(specs)]
+    got = [mk(c, L) for c, (L, _) in enumerate(specs)]
+    tcs = [t for (_, t) in specs]
+    for _ in range(2):
+        last = G.run_batch(ref, n, team_ctas=tcs)
+    with G.Plan(got, n, tcs, schedule="teams") as plan:
+        plan.launch(2)
+        out = plan.sync()
+    for c in range(len(specs)):
+        assert np.array_equal(out[c]["d_omega"], last[c]["d_omega"]), c
+        assert np.array_equal(got[c].get_spins(), ref[c].get_spins()), c
+    for ch in ref + got:
         ch.close()
 
 
