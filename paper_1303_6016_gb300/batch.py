@@ -70,11 +70,12 @@ class Autotuner:
         self.table[L] = res
         return res
 
-    def allocate(self, Ls, budget: int, work=None) -> list:
+    def allocate(self, Ls, budget: int, work=None, sizes=None) -> list:
         """Team sizes for chains of lattice sizes Ls within `budget` CTAs.
-        work[c] is the number of updates chain c will run (default equal)."""
+        work[c] is the number of updates chain c will run (default equal);
+        sizes, if given, restricts the team sizes considered."""
         work = [1.0] * len(Ls) if work is None else list(work)
-        tables = [self.measure(L) for L in Ls]
+        tables = [{k: v for k, v in self.measure(L).items() if sizes is None or k in sizes} for L in Ls]
         tc = [min(t) for t in tables]
         used = sum(tc)
         if used > budget:
@@ -169,9 +170,65 @@ class BatchRunner:
         self.chains = list(chains)
         self.tuner = tuner
         self.budget = budget or device_ctas()
+        self._plans = {}
+
+    def candidates(self, w, updates):
+        """Distinct team plans (order, team sizes) for the chains w of one
+        wave: packed (small chains sharing CTAs), every probed size without
+        sharing, and power-of-two sizes only."""
+        Ls = [self.chains[i].L for i in w]
+        work = [updates[i] for i in w]
+        out = [self.tuner.pack(Ls, self.budget, work, [self.chains[i].recursion for i in w])]
+        ident = list(range(len(w)))
+        out.append((ident, self.tuner.allocate(Ls, self.budget, work)))
+        out.append((ident, self.tuner.allocate(Ls, self.budget, work, sizes=(1, 2, 4, 8, 16, 32, 64))))
+        seen, uniq = set(), []
+        for order, tc in out:
+            key = tuple(zip(order, tc))
+            if key not in seen:
+                seen.add(key)
+                uniq.append((order, tc))
+        return uniq
+
+    def choose(self, w, updates):
+        """The fastest candidate plan of wave w, each timed for one step on
+        probe chains of the wave's lattice sizes and recursions (the probe
+        times of chains alone do not show how the chains of a full batch
+        share the L2)."""
+        import torch
+        cands = self.candidates(w, updates)
+        if len(cands) == 1:
+            return cands[0]
+        t = self.tuner
+        probes = [gfmc.Chain(self.chains[i].L, inputs.uniform_sphere(self.chains[i].L, 0), M=t.M,
+                             precision=t.precision, beta=t.beta, mu=t.mu, recursion=self.chains[i].recursion,
+                             chain_id=k) for k, i in enumerate(w)]
+        best = None
+        try:
+            for order, tc in cands:
+                chs = [probes[k] for k in order]
+                nu = [updates[w[k]] for k in order]
+                gfmc.run_batch(chs, nu, team_ctas=tc, trace=False)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                gfmc.run_batch(chs, nu, team_ctas=tc, trace=False)
+                dt = time.perf_counter() - t0
+                if best is None or dt < best[0]:
+                    best = (dt, order, tc)
+        finally:
+            for p in probes:
+                p.close()
+        return best[1], best[2]
 
     def plan(self, updates):
-        """Waves of (chain indices, team sizes) that each fit the device."""
+        """Waves of (chain indices, team sizes) that each fit the device
+        (chosen once per list of update counts)."""
+        key = tuple(updates)
+        if key not in self._plans:
+            self._plans[key] = self._plan(updates)
+        return self._plans[key]
+
+    def _plan(self, updates):
         Ls = [c.L for c in self.chains]
         need = [min(self.tuner.measure(L)) for L in Ls]
         waves, cur, used = [], [], 0
@@ -185,8 +242,7 @@ class BatchRunner:
             waves.append(cur)
         plan = []
         for w in waves:
-            order, tc = self.tuner.pack([Ls[i] for i in w], self.budget, [updates[i] for i in w],
-                                        [self.chains[i].recursion for i in w])
+            order, tc = self.choose(w, updates)
             plan.append(([w[k] for k in order], tc))
         return plan
 
