@@ -17,6 +17,12 @@
  *   - d(z) is the full 7x7 determinant by LU (no 2x2 reduction),
  *   - the phase is unwrapped node by node and summed in order.
  *
+ * Threads: when built with OpenMP, the loops over sites (Htilde x and the
+ * recursion's 2 Htilde a_n - a_{n-1}) and the loop over the Green's-function
+ * nodes run on orc_set_threads() threads.  Each iteration of those loops
+ * computes one output on its own, in the same order of terms as with one
+ * thread, so every result is bitwise the same for any thread count.
+ *
  * Conventions
  *   N = L^3 sites, periodic, site i = x + L*(y + L*z) (x fastest).
  *   Local order: 0 = o, 1 = +x, 2 = -x, 3 = +y, 4 = -y, 5 = +z, 6 = -z.
@@ -33,6 +39,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef double complex cx;
 
@@ -106,9 +115,29 @@ static void build_htilde(int L, const double* spins, double t, double a,
     free(chi);
 }
 
-/* out = Htilde * in. */
+/* Threads used by the loops marked below (1 when built without OpenMP). */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* out = Htilde * in (rows in parallel; each row's sum in the order d = 0..5). */
 static void apply_htilde(long N, const long* nb, const cx* h, const cx* in, cx* out)
 {
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < N; ++i) {
         cx s = 0.0;
         for (int d = 0; d < 6; ++d) s += h[6 * i + d] * in[nb[6 * i + d]];
@@ -189,6 +218,7 @@ int orc_moments(int L, const double* spins, double t, double a, long o, int M,
         cx *prev = a0, *cur = a1, *next = a2;
         for (int n = 2; n < M; ++n) {
             apply_htilde(N, nb, h, cur, next);
+#pragma omp parallel for schedule(static)
             for (long i = 0; i < N; ++i) next[i] = 2.0 * next[i] - prev[i];
             for (int j = 0; j < 7; ++j) mu[(j * 7 + k) * (long)M + n] = next[loc[j]];
             cx* tmp = prev;
@@ -397,14 +427,18 @@ int orc_delta_omega_from_moments(int L, const double* spins, double t, double ch
     if (st) return st;
     double* arg = (double*)malloc(sizeof(double) * K);
     if (!arg) return ORC_ENOMEM;
+    int bad = 0;
+    /* nodes in parallel: each node's G and d_k on their own */
+#pragma omp parallel for schedule(static) reduction(|| : bad)
     for (int k = 0; k < K; ++k) {
         cx G[49];
         double dk[2];
         orc_green7(M, K, mu, g, k, (double*)G);
         orc_det_one_plus_gd((const double*)G, (const double*)D, dk);
-        if (!isfinite(dk[0]) || !isfinite(dk[1])) { free(arg); return ORC_ENUMERIC; }
+        if (!isfinite(dk[0]) || !isfinite(dk[1])) bad = 1;
         arg[k] = atan2(dk[1], dk[0]);
     }
+    if (bad) { free(arg); return ORC_ENUMERIC; }
     double phase = arg[K - 1];
     double worst = fabs(phase);
     double sum = 0.0;

@@ -441,6 +441,42 @@ def test_philox_matches_second_implementation():
         assert O.philox4x32_10(ctr, key) == _philox_ref(ctr, key)
 
 
+def test_philox_known_answers():
+    """Philox4x32-10 against the known-answer vectors published with the
+    generator (Salmon, Moraes, Dror, Shaw, SC'11, and the known-answer file of
+    its reference distribution, Random123): a wrong multiplier, Weyl constant,
+    round count or output permutation changes every one of them."""
+    kat = [
+        ((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
+        ((0xFFFFFFFF,) * 4, (0xFFFFFFFF,) * 2, (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
+        ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
+         (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1)),
+    ]
+    for ctr, key, want in kat:
+        assert O.philox4x32_10(list(ctr), list(key)) == list(want)
+
+
+def test_results_do_not_depend_on_the_thread_count():
+    """The oracle's parallel loops (sites of Htilde x and of the recursion,
+    nodes of the Green's function) leave every result bitwise unchanged."""
+    L, M = 6, 128
+    sp = inputs.uniform_sphere(L, 3)
+    nmax = max(2, O.max_threads())
+    out = {}
+    for n in (1, nmax):
+        O.set_threads(n)
+        mu = O.moments(L, sp, 17, M)
+        d = O.delta_omega(L, sp, 17, 1.1, 0.4, M, beta=20.0, chem=-2.0)
+        res = O.updates(L, sp, 6, M, beta=20.0, chem=-2.0, seed=1)
+        out[n] = (mu, d, res["d_omega"], res["spins"])
+    O.set_threads(nmax)
+    a, b = out[1], out[nmax]
+    np.testing.assert_array_equal(a[0], b[0])
+    assert a[1] == b[1]
+    np.testing.assert_array_equal(a[2], b[2])
+    np.testing.assert_array_equal(a[3], b[3])
+
+
 def test_draws_are_uniform():
     n = 20000
     d = np.array([O.draw(1, 0, u) for u in range(n)])
