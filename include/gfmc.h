@@ -62,12 +62,29 @@ enum { GFMC_KERNEL_JACKSON = 0, GFMC_KERNEL_LORENTZ = 1 };
  *                 with the last two formed by linearity, so two recursions and
  *                 <o|T_n|v> give all four sequences. */
 enum { GFMC_RECURSION_UNIT_VECTORS = 0, GFMC_RECURSION_PROPOSAL = 1 };
+/* Engine of a single chain's gfmc_moments / gfmc_delta_omega / gfmc_updates /
+ * gfmc_sweep calls on the unit-vector recursion:
+ * AUTO            -- VECTOR_CLUSTERS where it applies, else GRID;
+ * GRID            -- one persistent launch over the whole GPU: each CTA a tile
+ *                    of sites, neighbour CTAs synchronised through flags in
+ *                    global memory, the moments from the doubling of Eq. mu2
+ *                    (r_0 .. r_{M/2}, Gram sums of the 7 vectors);
+ * VECTOR_CLUSTERS -- FP32-mixed chains with L = 32 only: the 7 recursions run
+ *                    side by side, each on its own thread-block cluster of 16
+ *                    CTAs that holds the whole vector in shared memory, and
+ *                    the moments are the entries mu_n^{jk} = (T_n(Htilde) e_k)
+ *                    at l_j of the plain recursion (Eq. recursive, n up to
+ *                    M - 1, no doubling, no dot products); needs 7 such
+ *                    clusters resident at once (GFMC_EINVAL from gfmc_create
+ *                    otherwise). */
+enum { GFMC_ENGINE_AUTO = 0, GFMC_ENGINE_GRID = 1, GFMC_ENGINE_VECTOR_CLUSTERS = 2 };
 
 typedef struct {
     /* GFMC_PREC_FP64: recursion vectors, stencil, moments and quadrature in FP64.
-     * GFMC_PREC_FP32_MIXED: recursion vectors and stencil in FP32 complex, dot
-     * products summed in FP32 within a warp and in FP64 above it; moments,
-     * Green's function, determinant and quadrature in FP64. */
+     * GFMC_PREC_FP32_MIXED: recursion vectors and stencil in FP32 complex
+     * (moments read off the vectors, or dot products summed in FP32 within a
+     * warp and in FP64 above it, by engine); combined moments, Green's
+     * function, determinant and quadrature in FP64. */
     int precision;
     /* Kernel g_n damping the moments (Sec. 2.2, mu~_m = mu_m g_m):
      * GFMC_KERNEL_JACKSON (default) or GFMC_KERNEL_LORENTZ
@@ -90,10 +107,12 @@ typedef struct {
      * moments), which takes out most of the quadrature error of Eq. d_seff2.
      * Any other value is GFMC_EINVAL. */
     int nodes;
+    int engine; /* GFMC_ENGINE_* */
 } gfmc_options;
 
 /* Fill *opt with the defaults (FP64, Jackson, a = 6.05|t|, seed 1, chain 0,
- * default stream, automatic CTA count, unit-vector recursion, K = M nodes). */
+ * default stream, automatic CTA count, unit-vector recursion, K = M nodes,
+ * automatic engine). */
 void gfmc_default_options(gfmc_options* opt);
 
 /* Create a chain (Sec. 2.1: the spin configuration and H({S}); Sec. 3.3.2:
@@ -114,7 +133,8 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
 
 /* The raw (undamped) local moments of the current configuration
  * (Sec. 2.2: mu_m = <i|T_m(Htilde)|i> and Eq. recursive, extended to the 7x7
- * block of o and its neighbours; obtained with the doubling of Eq. mu2).
+ * block of o and its neighbours; obtained with the doubling of Eq. mu2, or read
+ * off the plain recursion by the VECTOR_CLUSTERS engine).
  *   site    o in [0, N).
  *   mu_out  host complex128 [7][7][M] as interleaved doubles (re, im):
  *           mu_out[2*((j*7 + k)*M + n) + {0,1}] = <l_j| T_n(Htilde) |l_k>. */

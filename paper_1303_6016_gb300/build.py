@@ -18,7 +18,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgfmc.so")
-SOURCES = ["gfmc_api.cu", "gfmc_setup.cu", "gfmc_k64.cu", "gfmc_k32.cu", "gfmc_static.cu", "gfmc_server.cu"]
+SOURCES = ["gfmc_api.cu", "gfmc_setup.cu", "gfmc_k64.cu", "gfmc_k32.cu", "gfmc_kvc.cu", "gfmc_static.cu",
+           "gfmc_server.cu"]
 HEADERS = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))] + [
     os.path.join(ROOT, "include", "gfmc.h")]
 

@@ -28,6 +28,9 @@ struct gfmc_ctx {
     long long budget = 4000000000LL;
     int stall_next = 0;
     int recursion = 0;  // GFMC_RECURSION_*
+    // FP32-mixed L = 32 chain on seven thread-block clusters (one per unit
+    // vector): single-chain calls on the unit-vector recursion use it
+    bool vcl = false;
     Params P{};
     std::vector<void*> allocs;
     // growable output buffers of the sweep mode
@@ -219,8 +222,11 @@ gfmc_status run_engine(gfmc_ctx* h, Params& P)
                                             : gfmc::launch_team_f32(h->d_job, 1, P.ncta, 0, smem, h->stream);
     } else {
         const int nv = (h->recursion == GFMC_RECURSION_PROPOSAL && P.mode != gfmc::MODE_MOMENTS) ? 2 : gfmc::kVec;
-        e = h->precision == GFMC_PREC_FP64 ? gfmc::launch_engine_f64(P, nv, h->stream)
-                                            : gfmc::launch_engine_f32(P, nv, h->stream);
+        if (h->vcl && nv == gfmc::kVec)
+            e = gfmc::launch_vcluster_f32(P, h->stream);
+        else
+            e = h->precision == GFMC_PREC_FP64 ? gfmc::launch_engine_f64(P, nv, h->stream)
+                                                : gfmc::launch_engine_f32(P, nv, h->stream);
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "launching the GFMC engine");
     int err[4] = {0, 0, 0, 0};
@@ -346,6 +352,7 @@ void gfmc_default_options(gfmc_options* opt)
     opt->num_ctas = 0;
     opt->recursion = GFMC_RECURSION_UNIT_VECTORS;
     opt->nodes = 0;
+    opt->engine = GFMC_ENGINE_AUTO;
 }
 
 gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double beta, int M,
@@ -376,6 +383,11 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
     const int K = opt.nodes == 0 ? M : opt.nodes;
     if (K != M && K != 2 * M)
         return fail(nullptr, GFMC_EINVAL, "nodes = %d must be 0, M = %d or 2M = %d", opt.nodes, M, 2 * M);
+    if (opt.engine != GFMC_ENGINE_AUTO && opt.engine != GFMC_ENGINE_GRID && opt.engine != GFMC_ENGINE_VECTOR_CLUSTERS)
+        return fail(nullptr, GFMC_EINVAL, "unknown engine %d", opt.engine);
+    if (opt.engine == GFMC_ENGINE_VECTOR_CLUSTERS && (opt.precision != GFMC_PREC_FP32_MIXED || L != gfmc::kVcLattice))
+        return fail(nullptr, GFMC_EINVAL, "the vector-cluster engine runs FP32-mixed chains with L = %d",
+                    gfmc::kVcLattice);
 
     gfmc_ctx* h = new (std::nothrow) gfmc_ctx;
     if (!h) return fail(nullptr, GFMC_ENOMEM, "host allocation failed");
@@ -416,6 +428,17 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
     if ((e = gfmc::team_max_ctas(h->precision, gfmc::engine_smem_bytes(K), &maxt)) != cudaSuccess)
         return bail(cuda_fail(h, e, "querying team occupancy"));
     maxc = std::min(maxc, maxt);
+    if (opt.engine != GFMC_ENGINE_GRID && h->precision == GFMC_PREC_FP32_MIXED && L == gfmc::kVcLattice) {
+        // seven clusters of 16 CTAs must be resident at once (they meet at global counters)
+        int ncl = 0;
+        if ((e = gfmc::vcluster_max_clusters(K, &ncl)) != cudaSuccess) {
+            cudaGetLastError();
+            ncl = 0;
+        }
+        h->vcl = ncl >= gfmc::kVec;
+        if (!h->vcl && opt.engine == GFMC_ENGINE_VECTOR_CLUSTERS)
+            return bail(fail(h, GFMC_EINVAL, "the device holds %d of the 7 clusters of 16 CTAs the engine needs", ncl));
+    }
     const int N = h->N;
     int ncta = opt.num_ctas;
     if (ncta <= 0) {
@@ -472,8 +495,9 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
         (e = dalloc(h, &P.partial, (size_t)P.nsteps * ncta * gfmc::kEntries)) != cudaSuccess ||
         (e = dalloc(h, &P.fftin, 4 * (size_t)M)) != cudaSuccess ||
         (e = dalloc(h, &P.gnode, 4 * (size_t)K)) != cudaSuccess ||
-        (e = dalloc(h, &P.qpart, 2 * (size_t)ncta)) != cudaSuccess ||
-        (e = dalloc(h, &P.magpart, 3 * (size_t)ncta)) != cudaSuccess ||
+        (e = dalloc(h, &P.qpart, 2 * (size_t)std::max(ncta, 16))) != cudaSuccess ||
+        (e = dalloc(h, &P.magpart, 3 * (size_t)std::max(ncta, 16))) != cudaSuccess ||
+        (h->vcl && (e = dalloc(h, &P.mom32, 49 * (size_t)M)) != cudaSuccess) ||
         (e = dalloc(h, &P.mom_out, 49 * (size_t)M)) != cudaSuccess ||
         (e = dalloc(h, &d_ts, tstart.size())) != cudaSuccess || (e = dalloc(h, &d_np, nptr.size())) != cudaSuccess ||
         (e = dalloc(h, &d_ni, nidx.size() + 1)) != cudaSuccess ||

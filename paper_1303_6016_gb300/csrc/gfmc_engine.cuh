@@ -1390,6 +1390,146 @@ __device__ bool cluster_steps2(const Params& p, int rank, typename Cx<R>::T* vs,
     return true;
 }
 
+// ---------------------------------------------------------------------------
+// pieces of an update's tail shared by the engines
+// ---------------------------------------------------------------------------
+
+// K-point FFT of the four damped, twisted sequences p.fftin (zero beyond M)
+// and G_V(w_k) = (2i / sin theta_k) chi_k at the K nodes (Sec. 2.2, Eqs.
+// green_short and green_fft; chi_{2j} = gamma_j, chi_{2j+1} = conj
+// gamma_{K-j-1} for the real sequences).  CTA `cta` of `ncta` takes the
+// sequences V = cta, cta + ncta, ...; dyn holds K double2.
+template <int NT>
+__device__ __forceinline__ void tail_fft_nodes(const Params& p, int cta, int ncta, double2* dyn)
+{
+    const int tid = threadIdx.x, K = p.K, M = p.M;
+    int lg = 0;
+    while ((1 << lg) < K) ++lg;
+    for (int V = cta; V < 4; V += ncta) {
+        double2* x = dyn;
+        for (int n = tid; n < K; n += NT)
+            x[__brev((unsigned)n) >> (32 - lg)] =
+                n < M ? __ldcg(p.fftin + (size_t)V * M + n) : make_double2(0.0, 0.0);
+        __syncthreads();
+        for (int half = 1, lh = 0; half < K; half <<= 1, ++lh) {
+            const int tstride = K >> (lh + 1);
+            for (int b = tid; b < (K >> 1); b += NT) {
+                const int grp = b >> lh, pos = b & (half - 1);
+                const int i0 = (grp << (lh + 1)) + pos, i1 = i0 + half;
+                const double2 w = __ldcg(p.fftw + (size_t)pos * tstride);
+                const double2 u = x[i0], t = dmul(w, x[i1]);
+                x[i0] = dadd(u, t);
+                x[i1] = dsub(u, t);
+            }
+            __syncthreads();
+        }
+        for (int k = tid; k < K; k += NT) {
+            const double2 chi = (k & 1) ? dconj(x[K - 1 - (k >> 1)]) : x[k >> 1];
+            const double sc = 2.0 / __ldcg(p.sinth + k);
+            p.gnode[(size_t)V * K + k] = make_double2(-sc * chi.y, sc * chi.x);
+        }
+        __syncthreads();
+    }
+}
+
+// d_k = (1 + G_ov)(1 + G_vo) - G_oo G_vv at the nodes of CTA `cta` of `ncta`
+// (Sec. 2.2, Eq. d_z_green and the mixed elements), its continuous phase
+// increments and their Chebyshev-Gauss sum against the cumulative weights C_k
+// (Eq. d_seff2): p.qpart[2 cta] = the CTA's part of sum_k inc_k C_k,
+// p.qpart[2 cta + 1] = its largest |increment|.  sarg: room for K / ncta + 2
+// doubles.
+template <int NT>
+__device__ __forceinline__ void tail_phase_sums(const Params& p, int cta, int ncta, double* sarg)
+{
+    const int tid = threadIdx.x, K = p.K;
+    const int k0 = (int)(((long long)cta * K) / ncta);
+    const int k1 = (int)(((long long)(cta + 1) * K) / ncta);
+    const int kend = min(k1 + 1, K);
+    for (int k = k0 + tid; k < kend; k += NT) {
+        const double2 Goo = __ldcg(p.gnode + k), Gvv = __ldcg(p.gnode + (size_t)K + k);
+        const double2 Gp = __ldcg(p.gnode + 2 * (size_t)K + k), Gq = __ldcg(p.gnode + 3 * (size_t)K + k);
+        const double2 Am = dsub(dsub(Gp, Goo), Gvv);  // G_ov + G_vo
+        const double2 Bm = dsub(dsub(Gq, Goo), Gvv);  // i (G_ov - G_vo)
+        // G_ov = (A - iB)/2, G_vo = (A + iB)/2
+        const double2 Gov = make_double2(0.5 * (Am.x + Bm.y), 0.5 * (Am.y - Bm.x));
+        const double2 Gvo = make_double2(0.5 * (Am.x - Bm.y), 0.5 * (Am.y + Bm.x));
+        const double2 d = dsub(dmul(make_double2(1.0 + Gov.x, Gov.y), make_double2(1.0 + Gvo.x, Gvo.y)),
+                               dmul(Goo, Gvv));
+        if (!isfinite(d.x) || !isfinite(d.y)) set_error(p, ERR_NUMERIC, 40, k);
+        sarg[k - k0] = atan2(d.y, d.x);
+    }
+    __syncthreads();
+    double part = 0.0, mx = 0.0;
+    for (int k = k0 + tid; k < k1; k += NT) {
+        double inc;
+        if (k == K - 1) {
+            inc = sarg[k - k0];
+        } else {
+            inc = sarg[k - k0] - sarg[k + 1 - k0];
+            if (inc > CUDART_PI) inc -= 2.0 * CUDART_PI;
+            else if (inc <= -CUDART_PI) inc += 2.0 * CUDART_PI;
+        }
+        part += inc * __ldcg(p.cumw + k);
+        mx = fmax(mx, fabs(inc));
+    }
+    double ps, pm;
+    block_sum_max<NT>(part, mx, &ps, &pm);
+    if (tid == 0) {
+        p.qpart[2 * cta] = ps;
+        p.qpart[2 * cta + 1] = pm;
+    }
+}
+
+// The local patch of an accepted move (Algorithm 1, H <- H + Delta): thread
+// `who` in 0..5 rewrites one of the 6 bonds of o, thread 6 the spin of o.
+__device__ __forceinline__ void patch_site(const Params& p, int o, const int* s_loc, double thn, double phn, int who)
+{
+    const int N = p.N;
+    if (who == 6) {
+        p.spins[2 * o] = thn;
+        p.spins[2 * o + 1] = phn;
+    } else {
+        const int alpha = who >> 1;
+        const bool fwd = (who & 1) == 0;
+        const int j = s_loc[who + 1];  // o+e_alpha (fwd) or o-e_alpha
+        double cn, xn, yn, cj, xj, yj;
+        spinor3(thn, phn, cn, xn, yn);
+        spinor3(__ldcg(p.spins + 2 * j), __ldcg(p.spins + 2 * j + 1), cj, xj, yj);
+        // fwd: Htilde_{o, o+e} = -t <chi'_o|chi_j>/a stored at o;
+        // bwd: Htilde_{o-e, o} = -t <chi_j|chi'_o>/a stored at o-e
+        const double2 ov = fwd ? overlap3(cn, xn, yn, cj, xj, yj) : overlap3(cj, xj, yj, cn, xn, yn);
+        const double2 hv = make_double2(-p.t * ov.x / p.a, -p.t * ov.y / p.a);
+        const size_t at = (size_t)alpha * N + (fwd ? o : j);
+        p.hop64[at] = hv;
+        p.hop32[at] = make_float2((float)hv.x, (float)hv.y);
+    }
+}
+
+// The sums of S = (sin th cos ph, sin th sin ph, cos th) over sites [s0, s1)
+// into p.magpart[3 cta ..] (Algorithm 1, the measurement after a sweep).
+template <int NT>
+__device__ __forceinline__ void magnetisation_partial(const Params& p, int s0, int s1, int cta)
+{
+    const int tid = threadIdx.x;
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int si = s0 + tid; si < s1; si += NT) {
+        const double th = __ldcg(p.spins + 2 * si), ph = __ldcg(p.spins + 2 * si + 1);
+        double st, ct, sp, cp;
+        sincos(th, &st, &ct);
+        sincos(ph, &sp, &cp);
+        sx += st * cp;
+        sy += st * sp;
+        sz += ct;
+    }
+    double a0, b0;
+    block_sum_max<NT>(sx, 0.0, &a0, &b0);
+    if (tid == 0) p.magpart[3 * cta] = a0;
+    block_sum_max<NT>(sy, 0.0, &a0, &b0);
+    if (tid == 0) p.magpart[3 * cta + 1] = a0;
+    block_sum_max<NT>(sz, 0.0, &a0, &b0);
+    if (tid == 0) p.magpart[3 * cta + 2] = a0;
+}
+
 // Barrier of all CTAs of a chain: the grid barrier of a cooperative team, or
 // the hardware barrier of the chain's cluster (VARIANT 2; no wait can time out,
 // so every CTA of a cluster always runs the same sequence of barriers).
@@ -2011,77 +2151,11 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
 
         // ---- K-point FFT of the four sequences (zero beyond M) and G_V at the K nodes ----
         const int K = p.K;
-        {
-            int lg = 0;
-            while ((1 << lg) < K) ++lg;
-            for (int V = cta; V < 4; V += p.ncta) {
-                double2* x = dyn;
-                for (int n = tid; n < K; n += NT)
-                    x[__brev((unsigned)n) >> (32 - lg)] =
-                        n < M ? __ldcg(p.fftin + (size_t)V * M + n) : make_double2(0.0, 0.0);
-                __syncthreads();
-                for (int half = 1, lh = 0; half < K; half <<= 1, ++lh) {
-                    const int tstride = K >> (lh + 1);
-                    for (int b = tid; b < (K >> 1); b += NT) {
-                        const int grp = b >> lh, pos = b & (half - 1);
-                        const int i0 = (grp << (lh + 1)) + pos, i1 = i0 + half;
-                        const double2 w = __ldcg(p.fftw + (size_t)pos * tstride);
-                        const double2 u = x[i0], t = dmul(w, x[i1]);
-                        x[i0] = dadd(u, t);
-                        x[i1] = dsub(u, t);
-                    }
-                    __syncthreads();
-                }
-                for (int k = tid; k < K; k += NT) {
-                    const double2 chi = (k & 1) ? dconj(x[K - 1 - (k >> 1)]) : x[k >> 1];
-                    const double sc = 2.0 / __ldcg(p.sinth + k);
-                    p.gnode[(size_t)V * K + k] = make_double2(-sc * chi.y, sc * chi.x);
-                }
-                __syncthreads();
-            }
-        }
+        tail_fft_nodes<NT>(p, cta, p.ncta, dyn);
         if (!chain_barrier<VARIANT>(p, 3)) return;
 
         // ---- d_k, continuous phase, Chebyshev-Gauss partial sums ----
-        {
-            const int k0 = (int)(((long long)cta * K) / p.ncta);
-            const int k1 = (int)(((long long)(cta + 1) * K) / p.ncta);
-            const int kend = min(k1 + 1, K);
-            double* sarg = (double*)dyn;
-            for (int k = k0 + tid; k < kend; k += NT) {
-                const double2 Goo = __ldcg(p.gnode + k), Gvv = __ldcg(p.gnode + (size_t)K + k);
-                const double2 Gp = __ldcg(p.gnode + 2 * (size_t)K + k), Gq = __ldcg(p.gnode + 3 * (size_t)K + k);
-                const double2 Am = dsub(dsub(Gp, Goo), Gvv);  // G_ov + G_vo
-                const double2 Bm = dsub(dsub(Gq, Goo), Gvv);  // i (G_ov - G_vo)
-                // G_ov = (A - iB)/2, G_vo = (A + iB)/2
-                const double2 Gov = make_double2(0.5 * (Am.x + Bm.y), 0.5 * (Am.y - Bm.x));
-                const double2 Gvo = make_double2(0.5 * (Am.x - Bm.y), 0.5 * (Am.y + Bm.x));
-                const double2 d = dsub(dmul(make_double2(1.0 + Gov.x, Gov.y), make_double2(1.0 + Gvo.x, Gvo.y)),
-                                       dmul(Goo, Gvv));
-                if (!isfinite(d.x) || !isfinite(d.y)) set_error(p, ERR_NUMERIC, 40, k);
-                sarg[k - k0] = atan2(d.y, d.x);
-            }
-            __syncthreads();
-            double part = 0.0, mx = 0.0;
-            for (int k = k0 + tid; k < k1; k += NT) {
-                double inc;
-                if (k == K - 1) {
-                    inc = sarg[k - k0];
-                } else {
-                    inc = sarg[k - k0] - sarg[k + 1 - k0];
-                    if (inc > CUDART_PI) inc -= 2.0 * CUDART_PI;
-                    else if (inc <= -CUDART_PI) inc += 2.0 * CUDART_PI;
-                }
-                part += inc * __ldcg(p.cumw + k);
-                mx = fmax(mx, fabs(inc));
-            }
-            double ps, pm;
-            block_sum_max<NT>(part, mx, &ps, &pm);
-            if (tid == 0) {
-                p.qpart[2 * cta] = ps;
-                p.qpart[2 * cta + 1] = pm;
-            }
-        }
+        tail_phase_sums<NT>(p, cta, p.ncta, (double*)dyn);
         if (!chain_barrier<VARIANT>(p, 4)) return;
 
         // ---- Delta Omega, Metropolis decision, patch ----
@@ -2109,48 +2183,12 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
         __syncthreads();
         if (p.mode == MODE_DELTA) return;
         nacc += (unsigned long long)s_acc;
-        if (cta == 0 && s_acc && tid < 7) {
-            const double thn = s_draw[0], phn = s_draw[1];
-            if (tid == 6) {
-                p.spins[2 * o] = thn;
-                p.spins[2 * o + 1] = phn;
-            } else {
-                const int alpha = tid >> 1;
-                const bool fwd = (tid & 1) == 0;
-                const int j = s_loc[tid + 1];  // o+e_alpha (fwd) or o-e_alpha
-                double cn, xn, yn, cj, xj, yj;
-                spinor3(thn, phn, cn, xn, yn);
-                spinor3(__ldcg(p.spins + 2 * j), __ldcg(p.spins + 2 * j + 1), cj, xj, yj);
-                // fwd: Htilde_{o, o+e} = -t <chi'_o|chi_j>/a stored at o;
-                // bwd: Htilde_{o-e, o} = -t <chi_j|chi'_o>/a stored at o-e
-                const double2 ov = fwd ? overlap3(cn, xn, yn, cj, xj, yj) : overlap3(cj, xj, yj, cn, xn, yn);
-                const double2 hv = make_double2(-p.t * ov.x / p.a, -p.t * ov.y / p.a);
-                const size_t at = (size_t)alpha * N + (fwd ? o : j);
-                p.hop64[at] = hv;
-                p.hop32[at] = make_float2((float)hv.x, (float)hv.y);
-            }
-        }
+        if (cta == 0 && s_acc && tid < 7) patch_site(p, o, s_loc, s_draw[0], s_draw[1], tid);
         if (!chain_barrier<VARIANT>(p, 5)) return;
 
         // ---- magnetisation after each completed sweep ----
         if ((upd + 1ull) % (unsigned long long)N == 0ull) {
-            double sx = 0.0, sy = 0.0, sz = 0.0;
-            for (int si = s0 + tid; si < s1; si += NT) {
-                const double th = __ldcg(p.spins + 2 * si), ph = __ldcg(p.spins + 2 * si + 1);
-                double st, ct, sp, cp;
-                sincos(th, &st, &ct);
-                sincos(ph, &sp, &cp);
-                sx += st * cp;
-                sy += st * sp;
-                sz += ct;
-            }
-            double a0, b0;
-            block_sum_max<NT>(sx, 0.0, &a0, &b0);
-            if (tid == 0) p.magpart[3 * cta] = a0;
-            block_sum_max<NT>(sy, 0.0, &a0, &b0);
-            if (tid == 0) p.magpart[3 * cta + 1] = a0;
-            block_sum_max<NT>(sz, 0.0, &a0, &b0);
-            if (tid == 0) p.magpart[3 * cta + 2] = a0;
+            magnetisation_partial<NT>(p, s0, s1, cta);
             if (!chain_barrier<VARIANT>(p, 6)) return;
             if (cta == 0 && tid == 0) {
                 double X = 0.0, Y = 0.0, Z = 0.0;

@@ -50,6 +50,8 @@ struct Params {
     double* qpart;    // [ncta][2]  (phase-sum partial, max |increment|)
     double* magpart;  // [ncta][3]
     double2* mom_out; // [7][7][M] full moment matrix (moments mode)
+    // vector-cluster engine: the direct moment entries r_n^k[l_j] at [k][j][n]
+    float2* mom32;    // [7][7][M]
 
     // tile partition of the sites over CTAs and the CTAs each tile reads from
     const int* tile_start;  // [ncta + 1]
@@ -150,6 +152,13 @@ int single_smem_bytes(int K, int precision, int win_max = 0);
 cudaError_t engine_static_smem_f64(int* out);
 cudaError_t engine_max_ctas(int precision, int K, int* out);
 cudaError_t launch_build_hoppings(const Params& p, cudaStream_t s);
+// FP32-mixed single chain on seven thread-block clusters of 16 CTAs, one per
+// local unit vector (L = 32 only; p.bar[0..1] are its update counters)
+cudaError_t launch_vcluster_f32(const Params& p, cudaStream_t s);
+// how many of that engine's clusters can be resident at once for K nodes
+cudaError_t vcluster_max_clusters(int K, int* out);
+constexpr int kVcLattice = 32;
+constexpr int kVcCtas = 16 * 7;
 cudaError_t launch_setup_tables(const Params& p, int kernel_kind, double lambda, cudaStream_t s);
 
 }  // namespace gfmc

@@ -1,0 +1,56 @@
+// Launch of the FP32-mixed single-chain engine on seven thread-block
+// clusters (one per local unit vector; gfmc_vcluster.cuh).
+#include "gfmc_vcluster.cuh"
+
+namespace gfmc {
+
+namespace {
+constexpr int kVcPP = 2;  // z pairs per thread: 512 threads per CTA
+
+int vc_smem(int K) { return VcGeo<kVcPP>::FIXED + K * (int)sizeof(double2); }
+
+cudaError_t vc_config(int K)
+{
+    cudaError_t e = cudaFuncSetAttribute(gfmc_vc_engine<kVcPP>, cudaFuncAttributeMaxDynamicSharedMemorySize, vc_smem(K));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gfmc_vc_engine<kVcPP>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+
+cudaLaunchConfig_t vc_launch_config(int K, cudaStream_t s, cudaLaunchAttribute* attr)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(kVcClusters * kVcC));
+    cfg.blockDim = dim3(VcGeo<kVcPP>::NT);
+    cfg.dynamicSmemBytes = (size_t)vc_smem(K);
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)kVcC;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+}  // namespace
+
+cudaError_t launch_vcluster_f32(const Params& p, cudaStream_t s)
+{
+    if (p.L != kVcL) return cudaErrorInvalidValue;
+    cudaError_t e = vc_config(p.K);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = vc_launch_config(p.K, s, attr);
+    return cudaLaunchKernelEx(&cfg, gfmc_vc_engine<kVcPP>, p);
+}
+
+cudaError_t vcluster_max_clusters(int K, int* out)
+{
+    cudaError_t e = vc_config(K);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = vc_launch_config(K, nullptr, attr);
+    return cudaOccupancyMaxActiveClusters(out, gfmc_vc_engine<kVcPP>, &cfg);
+}
+
+}  // namespace gfmc

@@ -25,6 +25,7 @@ GFMC_OK, GFMC_EINVAL, GFMC_ENOMEM, GFMC_ECUDA, GFMC_ETIMEOUT, GFMC_ENUMERIC = ra
 PRECISIONS = {"fp64": 0, "fp32_mixed": 1}
 KERNELS = {"jackson": 0, "lorentz": 1}
 RECURSIONS = {"unit_vectors": 0, "proposal": 1}
+ENGINES = {"auto": 0, "grid": 1, "vector_clusters": 2}
 
 # Names exported by libgfmc.so; include/gfmc.h declares exactly these.
 EXPORTS = ("gfmc_default_options", "gfmc_create", "gfmc_moments", "gfmc_delta_omega",
@@ -48,7 +49,7 @@ class Options(ctypes.Structure):
                 ("lorentz_lambda", ctypes.c_double), ("spectral_scale", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("chain_id", ctypes.c_uint32),
                 ("stream", ctypes.c_void_p), ("num_ctas", ctypes.c_int), ("recursion", ctypes.c_int),
-                ("nodes", ctypes.c_int)]
+                ("nodes", ctypes.c_int), ("engine", ctypes.c_int)]
 
 
 _lib = None
@@ -147,7 +148,7 @@ class Chain:
                  M: int = 256, precision: str = "fp64", kernel: str = "jackson",
                  lorentz_lambda: float = 4.0, spectral_scale: float = 0.0, seed: int = 1,
                  chain_id: int = 0, stream=None, num_ctas: int = 0, recursion: str = "unit_vectors",
-                 nodes: int = 0):
+                 nodes: int = 0, engine: str = "auto"):
         lib = load()
         self.L, self.N, self.M = int(L), int(L) ** 3, int(M)
         self.K = int(nodes) if nodes else self.M  # Chebyshev nodes of G and of the quadrature
@@ -167,6 +168,8 @@ class Chain:
         opt.num_ctas = int(num_ctas)
         opt.recursion = RECURSIONS[recursion]
         opt.nodes = int(nodes)
+        opt.engine = ENGINES[engine]
+        self.engine = engine
         sp = np.ascontiguousarray(spins, dtype=np.float64).reshape(-1, 2)
         if sp.shape[0] != self.N:
             raise ValueError(f"spins has {sp.shape[0]} rows, expected N = {self.N}")
