@@ -5,15 +5,12 @@
 namespace gfmc {
 
 namespace {
-constexpr int kVcPP = 2;  // z pairs per thread: 512 threads per CTA
-
-int vc_smem(int K) { return VcGeo<kVcPP>::FIXED + K * (int)sizeof(double2); }
+int vc_smem(int K) { return kVcFixedSmem + K * (int)sizeof(double2); }
 
 cudaError_t vc_config(int K)
 {
-    cudaError_t e = cudaFuncSetAttribute(gfmc_vc_engine<kVcPP>, cudaFuncAttributeMaxDynamicSharedMemorySize, vc_smem(K));
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(gfmc_vc_engine<kVcPP>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaError_t e = cudaFuncSetAttribute(gfmc_vc_engine, cudaFuncAttributeMaxDynamicSharedMemorySize, vc_smem(K));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(gfmc_vc_engine, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     return e;
 }
 
@@ -21,7 +18,7 @@ cudaLaunchConfig_t vc_launch_config(int K, cudaStream_t s, cudaLaunchAttribute* 
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(kVcClusters * kVcC));
-    cfg.blockDim = dim3(VcGeo<kVcPP>::NT);
+    cfg.blockDim = dim3(kVcNT);
     cfg.dynamicSmemBytes = (size_t)vc_smem(K);
     cfg.stream = s;
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -41,7 +38,7 @@ cudaError_t launch_vcluster_f32(const Params& p, cudaStream_t s)
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = vc_launch_config(p.K, s, attr);
-    return cudaLaunchKernelEx(&cfg, gfmc_vc_engine<kVcPP>, p);
+    return cudaLaunchKernelEx(&cfg, gfmc_vc_engine, p);
 }
 
 cudaError_t vcluster_max_clusters(int K, int* out)
@@ -50,7 +47,7 @@ cudaError_t vcluster_max_clusters(int K, int* out)
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = vc_launch_config(K, nullptr, attr);
-    return cudaOccupancyMaxActiveClusters(out, gfmc_vc_engine<kVcPP>, &cfg);
+    return cudaOccupancyMaxActiveClusters(out, gfmc_vc_engine, &cfg);
 }
 
 }  // namespace gfmc

@@ -9,22 +9,34 @@
 // holds the whole vector in shared memory: no Gram sums, no cross-CTA
 // reduction, M - 2 stencil steps per vector.
 //
-// Lattice split (L = 32): CTA (ry, rz) of the 4 x 4 cluster holds the pencil
-// x in [0, 32), y in [8 ry, 8 ry + 8), z in [8 rz, 8 rz + 8).  Two z-planes
-// (2p, 2p+1) of a column are packed, re = (Re r[2p], Re r[2p+1]) and im
-// likewise, so one fma.rn.f32x2 advances two sites.  Thread (x, yl, seg)
-// walks the PP pairs [seg PP, (seg+1) PP) of column (x, yl) and keeps their
-// r_m and r_{m-1} and the 2 Htilde bonds in registers.
+// Checkerboard.  Htilde only couples nearest neighbours, and with L even the
+// periodic cubic lattice is bipartite: T_n(Htilde) e_k is zero on every site
+// whose parity (x + y + z) mod 2 differs from parity(l_k) + n.  A step
+// therefore computes r_{n+1} on the half of the sites of parity
+// parity(l_k) + n + 1 only, from r_n on the other half, and overwrites
+// r_{n-1} in place (it lives on the same half).  The other half would give
+// exact zeros.
 //
-// Halo exchange: after a step, each face value is written into the neighbour
-// CTA's halo buffer with st.async, which completes the transaction count of
-// the neighbour's mbarrier (one per buffer parity).  A CTA waits only for
-// its four neighbours' 8 KB of faces, and only after it has formed every
-// contribution that does not need them: the halo terms of the face sites are
-// added after the wait.  Faces written in step m are read in step m + 1; the
-// symmetric neighbour relation orders the reuse of a halo buffer two steps
-// later (the site that reads a halo slot is the site whose value goes back to
-// the writer, after the read).
+// Lattice split (L = 32): CTA (ry, rz) of the 4 x 4 cluster holds the pencil
+// x in [0, 32), y in [8 ry, 8 ry + 8), z in [8 rz, 8 rz + 8).  A thread holds
+// one column (x, yl) of 8 sites; zl = g + 2 h + 4 q puts them in two groups
+// g of equal parity, each of two pairs q whose halves h are two sites two
+// planes apart.  Both sites of a pair are advanced by one fma.rn.f32x2.  At
+// each step one group of every column is active (the parity of the column,
+// cp, decides which); the warps are formed of columns of equal cp, so a warp
+// runs one code path.  The column's r_n, r_{n-1} and 2 Htilde bonds stay in
+// registers; the values its neighbours read live in one shared buffer in a
+// red-black layout (columns of odd and even x apart), updated in place.
+//
+// Halo exchange: every value on a face of the pencil is written into the
+// neighbour CTA's halo buffer with st.async, which completes the transaction
+// count of the neighbour's mbarrier (one per step parity; 4 KB per step).  A
+// CTA waits for its four neighbours' faces only after it has formed every
+// contribution that does not need them; the halo terms of its face sites are
+// added after the wait.  Halo slots are indexed by site, so the faces of
+// consecutive steps (opposite parities) never share a slot, and a slot is
+// rewritten two steps later only after the thread that reads it has sent its
+// own face back to the writer.
 //
 // The update's tail (combined moments with the kernel, FFT to the nodes,
 // determinant and phase quadrature, Metropolis, patch, magnetisation) runs
@@ -36,29 +48,38 @@
 
 namespace gfmc {
 
-constexpr int kVcL = 32;                  // lattice edge of this engine
-constexpr int kVcC = 16;                  // CTAs per cluster (4 x 4 pencils)
-constexpr int kVcPY = 8;                  // y rows per CTA
-constexpr int kVcNP = 4;                  // z pairs per CTA (8 planes)
-constexpr int kVcPT = 32 * kVcPY * kVcNP; // pairs per CTA
-constexpr int kVcClusters = kVec;         // one cluster per unit vector
-constexpr int kVcHaloBytes = 2 * kVcNP * 32 * 16 + 2 * kVcPY * 32 * 8;  // faces received per step
-
-template <int PP> struct VcGeo {
-    static constexpr int NSEG = kVcNP / PP;
-    static constexpr int NT = 32 * kVcPY * NSEG;
-    static constexpr int NW = NT / 32;
-    // dynamic shared memory: [2][NP][PY][32] PairV, [2 buf][2 side][NP][32] PairV,
-    // [2 buf][2 side][PY][32] float2, then the tail's work area
-    static constexpr int RB = 2 * kVcPT;
-    static constexpr int HY = 2 * 2 * kVcNP * 32;
-    static constexpr int HZ = 2 * 2 * kVcPY * 32;
-    static constexpr int FIXED = (RB + HY) * 16 + HZ * 8;
-};
+constexpr int kVcL = 32;      // lattice edge of this engine
+constexpr int kVcC = 16;      // CTAs per cluster (4 x 4 pencils)
+constexpr int kVcPY = 8;      // y rows per CTA (and z planes)
+constexpr int kVcNT = 256;    // one thread per column of the pencil
+constexpr int kVcNW = kVcNT / 32;
+constexpr int kVcClusters = kVec;  // one cluster per unit vector
+constexpr int kVcSlots = 2 * 2 * kVcPY * 32;  // pair slots of a CTA's buffer (all 2048 sites)
+constexpr int kVcHY = 2 * 2 * 2 * 32;         // y halo: [side][g][q][x] pair slots
+constexpr int kVcHZ = 2 * kVcPY * 32;         // z halo: [side][yl][x] values
+constexpr int kVcHaloBytes = 4096;            // faces a CTA receives per step (half of each face)
+constexpr int kVcFixedSmem = (kVcSlots + kVcHY) * 16 + kVcHZ * 8;
+constexpr int kVcArmTid = 32;   // warp 1: rows yl = 2, 3 (no y face)
+constexpr int kVcEmitTid = 64;  // warp 2: rows yl = 4, 5
 
 struct __align__(16) VcPair {
     float2 re, im;
 };
+
+// red-black slot of pair (g, q) of column (x, yl): columns of even and odd x
+// apart so that the x-neighbours a warp reads are contiguous
+__device__ __forceinline__ int vc_slot(int g, int q, int yl, int x)
+{
+    return ((((g * 2 + q) * kVcPY + yl) * 2 + (x & 1)) << 4) + (x >> 1);
+}
+__device__ __forceinline__ int vc_hy_slot(int side, int g, int q, int x)
+{
+    return ((((side * 2 + g) * 2 + q) * 2 + (x & 1)) << 4) + (x >> 1);
+}
+__device__ __forceinline__ int vc_hz_slot(int side, int yl, int x)
+{
+    return (((side * kVcPY + yl) * 2 + (x & 1)) << 4) + (x >> 1);
+}
 
 __device__ __forceinline__ unsigned vc_mapa(unsigned a, int rank)
 {
@@ -70,10 +91,15 @@ __device__ __forceinline__ void vc_mbar_init(unsigned a)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
 }
-// one arrival with the bytes of the next phase
+// one arrival with the bytes of the next phase.  Relaxed: the arrival only
+// opens the phase; the halo data become visible through the transaction
+// count of the writes themselves, and no earlier write of the arming thread
+// has to be ordered before it (a release arrival would wait for that
+// thread's own remote writes to land).
 __device__ __forceinline__ void vc_mbar_arm(unsigned a)
 {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(kVcHaloBytes) : "memory");
+    asm volatile("mbarrier.arrive.expect_tx.relaxed.cta.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(kVcHaloBytes)
+                 : "memory");
 }
 // bounded wait for the phase of the given parity; false when the budget ran out
 __device__ __forceinline__ bool vc_mbar_wait(unsigned a, unsigned parity, long long budget)
@@ -121,158 +147,163 @@ __device__ __forceinline__ bool vc_wait_geq(const Params& p, const unsigned* a, 
     return true;
 }
 
-// Per-thread state of one vector's recursion on one CTA.
-template <int PP> struct VcState {
-    float2 hr[PP][6], hi[PP][6];  // 2 Htilde of the pair's two sites: Re, Im (backward bonds conjugated)
-    VcPair A[PP], B[PP];          // two recursion vectors; the step overwrites the older one
+// One thread's column: 2 Htilde of its 8 sites by group, pair and direction
+// (+x, -x, +y, -y, +z, -z; Re and Im of the two halves, backward bonds
+// conjugated) and the two values of the recursion each site holds.
+struct VcColumn {
+    float2 hr[2][2][6], hi[2][2][6];
+    VcPair V[2][2];  // group g: r_n on the inactive group, r_{n-1} (then r_{n+1}) on the active one
 };
 
-template <int PP>
 struct VcCtx {
-    int x, yl, seg, p0, rank, ry, rz, vec;
-    VcPair* rb;        // [2][NP][PY][32]
-    VcPair* hy;        // [2][2][NP][32]
-    float2* hz;        // [2][2][PY][32]
+    int x, yl, rank, ry, rz, vec;
+    VcPair* rb;        // [kVcSlots] the CTA's values of the vector (red-black pair slots)
+    VcPair* hy;        // [kVcHY]
+    float2* hz;        // [kVcHZ]
     unsigned mb;       // this CTA's two mbarriers (shared::cta)
     // shared memory, the neighbours' shared::cluster addresses: halo buffers
     // of -y, +y, -z, +z, then their mbarriers in the same order
     const unsigned* ra;
 };
 
-// One step of the recursion on this thread's pairs: xv (r_{m-1}) becomes
-// r_{m+1} = 2 Htilde c - xv with c = r_m.  b = m & 1 is the buffer of r_m
-// (its halo faces arrive on mbarrier b).  Returns false (on every thread of
-// the CTA) when the wait for the faces ran out of budget.
-template <int PP>
-__device__ __forceinline__ bool vc_step(const VcCtx<PP>& k, const VcState<PP>& s, const VcPair (&c)[PP],
-                                        VcPair (&xv)[PP], int b, unsigned& phase, bool push, long long budget)
+// The faces of a column after its group G was advanced: the y-face rows send
+// both pairs to the CTA below / above in y; the column sends its new value on
+// plane zl = 0 (G = 0) to the CTA below in z or on zl = 7 (G = 1) above.
+template <int G>
+__device__ __forceinline__ void vc_push_faces(const VcCtx& k, const VcPair (&nx)[2], int b)
 {
-    constexpr int PY = kVcPY, NP = kVcNP;
-    const int x = k.x, yl = k.yl, nb = b ^ 1;
-    const VcPair* rd = k.rb + b * kVcPT;
-    VcPair* wr = k.rb + nb * kVcPT;
+    const int x = k.x, yl = k.yl;
+    if (yl == 0) {
+        vc_push4(k.ra[0] + 16u * (unsigned)vc_hy_slot(1, G, 0, x), nx[0], k.ra[4] + 8 * b);
+        vc_push4(k.ra[0] + 16u * (unsigned)vc_hy_slot(1, G, 1, x), nx[1], k.ra[4] + 8 * b);
+    } else if (yl == kVcPY - 1) {
+        vc_push4(k.ra[1] + 16u * (unsigned)vc_hy_slot(0, G, 0, x), nx[0], k.ra[5] + 8 * b);
+        vc_push4(k.ra[1] + 16u * (unsigned)vc_hy_slot(0, G, 1, x), nx[1], k.ra[5] + 8 * b);
+    }
+    if (G == 0)
+        vc_push2(k.ra[2] + 8u * (unsigned)vc_hz_slot(1, yl, x), nx[0].re.x, nx[0].im.x, k.ra[6] + 8 * b);
+    else
+        vc_push2(k.ra[3] + 8u * (unsigned)vc_hz_slot(0, yl, x), nx[1].re.y, nx[1].im.y, k.ra[7] + 8 * b);
+}
+
+// One step on group G of the thread's column: r_{m+1} = 2 Htilde r_m - r_{m-1}
+// with r_m on group 1 - G (registers, and the neighbours' columns in the
+// shared buffer) and r_{m-1} on group G, which it overwrites.  b = m & 1 is
+// the mbarrier of this step's halo faces; the step's own faces go to the
+// neighbours' barrier 1 - b when push is set.  Returns false when the wait
+// for the faces ran out of budget (that thread then sends nothing).
+template <int G>
+__device__ __forceinline__ bool vc_step(const VcCtx& k, VcColumn& c, int b, unsigned phase, bool push, long long budget)
+{
+    constexpr int PY = kVcPY, IG = 1 - G;
+    const int x = k.x, yl = k.yl;
     const int xp = (x + 1) & 31, xm = (x + 31) & 31;
     const bool fym = yl == 0, fyp = yl == PY - 1;
-    VcPair nx[PP];
+    const VcPair* rb = k.rb;
+    VcPair nx[2];
     // ---- every term that needs no halo ----
 #pragma unroll
-    for (int pp = 0; pp < PP; ++pp) {
-        const int p = k.p0 + pp;
-        const int pi = (p * PY + yl) * 32;
-        const VcPair vxp = rd[pi + xp], vxm = rd[pi + xm];
-        float2 P = make_float2(-xv[pp].re.x, -xv[pp].re.y), Q = make_float2(-xv[pp].im.x, -xv[pp].im.y);
+    for (int q = 0; q < 2; ++q) {
+        const VcPair vxp = rb[vc_slot(G, q, yl, xp)], vxm = rb[vc_slot(G, q, yl, xm)];
+        float2 P = make_float2(-c.V[G][q].re.x, -c.V[G][q].re.y), Q = make_float2(-c.V[G][q].im.x, -c.V[G][q].im.y);
         float2 S = make_float2(0.f, 0.f), W = make_float2(0.f, 0.f);
-        ff2(P, s.hr[pp][0], vxp.re);
-        ff2(Q, s.hr[pp][0], vxp.im);
-        ff2(S, s.hi[pp][0], vxp.im);
-        ff2(W, s.hi[pp][0], vxp.re);
-        ff2(P, s.hr[pp][1], vxm.re);
-        ff2(Q, s.hr[pp][1], vxm.im);
-        ff2(S, s.hi[pp][1], vxm.im);
-        ff2(W, s.hi[pp][1], vxm.re);
+        const float2* hr = c.hr[G][q];
+        const float2* hi = c.hi[G][q];
+        ff2(P, hr[0], vxp.re);
+        ff2(Q, hr[0], vxp.im);
+        ff2(S, hi[0], vxp.im);
+        ff2(W, hi[0], vxp.re);
+        ff2(P, hr[1], vxm.re);
+        ff2(Q, hr[1], vxm.im);
+        ff2(S, hi[1], vxm.im);
+        ff2(W, hi[1], vxm.re);
         if (!fyp) {
-            const VcPair v = rd[pi + 32 + x];
-            ff2(P, s.hr[pp][2], v.re);
-            ff2(Q, s.hr[pp][2], v.im);
-            ff2(S, s.hi[pp][2], v.im);
-            ff2(W, s.hi[pp][2], v.re);
+            const VcPair v = rb[vc_slot(G, q, yl + 1, x)];
+            ff2(P, hr[2], v.re);
+            ff2(Q, hr[2], v.im);
+            ff2(S, hi[2], v.im);
+            ff2(W, hi[2], v.re);
         }
         if (!fym) {
-            const VcPair v = rd[pi - 32 + x];
-            ff2(P, s.hr[pp][3], v.re);
-            ff2(Q, s.hr[pp][3], v.im);
-            ff2(S, s.hi[pp][3], v.im);
-            ff2(W, s.hi[pp][3], v.re);
+            const VcPair v = rb[vc_slot(G, q, yl - 1, x)];
+            ff2(P, hr[3], v.re);
+            ff2(Q, hr[3], v.im);
+            ff2(S, hi[3], v.im);
+            ff2(W, hi[3], v.re);
         }
-        // z: +z of the pair = (hi of this pair, lo of the pair above), -z = (hi of the pair below, lo of this);
-        // a half that lies in the neighbour CTA's plane is added after the wait (zero here)
-        float2 up = make_float2(0.f, 0.f), dn = make_float2(0.f, 0.f);  // (re, im) above the hi / below the lo plane
-        if (pp + 1 < PP) up = make_float2(c[pp + 1].re.x, c[pp + 1].im.x);
-        else if (p + 1 < NP) { const VcPair a = rd[pi + PY * 32 + x]; up = make_float2(a.re.x, a.im.x); }
-        if (pp > 0) dn = make_float2(c[pp - 1].re.y, c[pp - 1].im.y);
-        else if (p > 0) { const VcPair a = rd[pi - PY * 32 + x]; dn = make_float2(a.re.y, a.im.y); }
-        const float2 zpr = make_float2(c[pp].re.y, up.x), zpi = make_float2(c[pp].im.y, up.y);
-        const float2 zmr = make_float2(dn.x, c[pp].re.x), zmi = make_float2(dn.y, c[pp].im.x);
-        ff2(P, s.hr[pp][4], zpr);
-        ff2(Q, s.hr[pp][4], zpi);
-        ff2(S, s.hi[pp][4], zpi);
-        ff2(W, s.hi[pp][4], zpr);
-        ff2(P, s.hr[pp][5], zmr);
-        ff2(Q, s.hr[pp][5], zmi);
-        ff2(S, s.hi[pp][5], zmi);
-        ff2(W, s.hi[pp][5], zmr);
-        const float2 m1 = make_float2(-1.f, -1.f);
-        nx[pp].re = __ffma2_rn(S, m1, P);
-        nx[pp].im = __fadd2_rn(Q, W);
-        // a pair with no face value is final: store it now
-        if (!fym && !fyp && p > 0 && p + 1 < NP) wr[pi + x] = nx[pp];
+        // z-neighbours on the other group of the column: planes zl +- 1 of the pair's
+        // two sites (zl = G + 4q and G + 4q + 2); a plane outside the pencil is added
+        // after the wait (zero here)
+        float2 zpr, zpi, zmr, zmi;
+        if (G == 0) {
+            zpr = c.V[IG][q].re;
+            zpi = c.V[IG][q].im;
+            const float dr = q > 0 ? c.V[IG][q - 1].re.y : 0.f, di = q > 0 ? c.V[IG][q - 1].im.y : 0.f;
+            zmr = make_float2(dr, c.V[IG][q].re.x);
+            zmi = make_float2(di, c.V[IG][q].im.x);
+        } else {
+            zmr = c.V[IG][q].re;
+            zmi = c.V[IG][q].im;
+            const float ur = q < 1 ? c.V[IG][q + 1].re.x : 0.f, ui = q < 1 ? c.V[IG][q + 1].im.x : 0.f;
+            zpr = make_float2(c.V[IG][q].re.y, ur);
+            zpi = make_float2(c.V[IG][q].im.y, ui);
+        }
+        ff2(P, hr[4], zpr);
+        ff2(Q, hr[4], zpi);
+        ff2(S, hi[4], zpi);
+        ff2(W, hi[4], zpr);
+        ff2(P, hr[5], zmr);
+        ff2(Q, hr[5], zmi);
+        ff2(S, hi[5], zmi);
+        ff2(W, hi[5], zmr);
+        nx[q].re = __ffma2_rn(S, make_float2(-1.f, -1.f), P);
+        nx[q].im = __fadd2_rn(Q, W);
     }
-    // ---- the faces of the neighbours: wait, then the halo terms ----
-    // A CTA whose wait ran out does nothing more in this launch: no halo terms,
-    // no stores, no pushes, no re-arming of the barrier whose phase is still
-    // open.  So every push of a CTA is followed by a wait of its own (success,
-    // or the whole budget) before that CTA can reach the final cluster barrier,
-    // and no push is still in flight when its receiver leaves.
-    if (__syncthreads_or(!vc_mbar_wait(k.mb + 8 * b, phase, budget))) return false;
-    phase ^= 1u;
-    const VcPair* hyb = k.hy + b * 2 * NP * 32;
-    const float2* hzb = k.hz + b * 2 * PY * 32;
+    // pair IG has no site on a z face (the face planes zl = 0 and 7 are in pair G):
+    // outside the y-face rows it is final, store it now
+    if (!fym && !fyp) k.rb[vc_slot(G, IG, yl, x)] = nx[IG];
+    // ---- the neighbours' faces: wait, then the halo terms ----
+    const bool ok = vc_mbar_wait(k.mb + 8 * b, phase, budget);
 #pragma unroll
-    for (int pp = 0; pp < PP; ++pp) {
-        const int p = k.p0 + pp;
+    for (int q = 0; q < 2; ++q) {
         if (fym || fyp) {
             const int d = fym ? 3 : 2;
-            const VcPair v = hyb[((fym ? 0 : 1) * NP + p) * 32 + x];
+            const VcPair v = k.hy[vc_hy_slot(fym ? 0 : 1, G, q, x)];
             float2 S = make_float2(0.f, 0.f), W = make_float2(0.f, 0.f);
-            ff2(nx[pp].re, s.hr[pp][d], v.re);
-            ff2(nx[pp].im, s.hr[pp][d], v.im);
-            ff2(S, s.hi[pp][d], v.im);
-            ff2(W, s.hi[pp][d], v.re);
-            nx[pp].re = __ffma2_rn(S, make_float2(-1.f, -1.f), nx[pp].re);
-            nx[pp].im = __fadd2_rn(nx[pp].im, W);
-        }
-        if (pp + 1 == PP && p + 1 == NP) {  // above the top plane: the CTA above
-            const float2 v = hzb[(1 * PY + yl) * 32 + x];
-            const float2 h_r = s.hr[pp][4], h_i = s.hi[pp][4];
-            nx[pp].re.y = fmaf(h_r.y, v.x, fmaf(-h_i.y, v.y, nx[pp].re.y));
-            nx[pp].im.y = fmaf(h_r.y, v.y, fmaf(h_i.y, v.x, nx[pp].im.y));
-        }
-        if (pp == 0 && p == 0) {  // below the bottom plane: the CTA below
-            const float2 v = hzb[(0 * PY + yl) * 32 + x];
-            const float2 h_r = s.hr[pp][5], h_i = s.hi[pp][5];
-            nx[pp].re.x = fmaf(h_r.x, v.x, fmaf(-h_i.x, v.y, nx[pp].re.x));
-            nx[pp].im.x = fmaf(h_r.x, v.y, fmaf(h_i.x, v.x, nx[pp].im.x));
+            ff2(nx[q].re, c.hr[G][q][d], v.re);
+            ff2(nx[q].im, c.hr[G][q][d], v.im);
+            ff2(S, c.hi[G][q][d], v.im);
+            ff2(W, c.hi[G][q][d], v.re);
+            nx[q].re = __ffma2_rn(S, make_float2(-1.f, -1.f), nx[q].re);
+            nx[q].im = __fadd2_rn(nx[q].im, W);
         }
     }
-#pragma unroll
-    for (int pp = 0; pp < PP; ++pp) {
-        const int p = k.p0 + pp;
-        const int pi = (p * PY + yl) * 32 + x;
-        const bool face = fym || fyp || p == 0 || p + 1 == NP;
-        if (face) wr[pi] = nx[pp];
-        if (push) {
-            if (fym) vc_push4(k.ra[0] + 16u * (unsigned)(((nb * 2 + 1) * NP + p) * 32 + x), nx[pp], k.ra[4] + 8 * nb);
-            if (fyp) vc_push4(k.ra[1] + 16u * (unsigned)(((nb * 2 + 0) * NP + p) * 32 + x), nx[pp], k.ra[5] + 8 * nb);
-            if (p == 0)
-                vc_push2(k.ra[2] + 8u * (unsigned)(((nb * 2 + 1) * PY + yl) * 32 + x), nx[pp].re.x, nx[pp].im.x,
-                         k.ra[6] + 8 * nb);
-            if (p + 1 == NP)
-                vc_push2(k.ra[3] + 8u * (unsigned)(((nb * 2 + 0) * PY + yl) * 32 + x), nx[pp].re.y, nx[pp].im.y,
-                         k.ra[7] + 8 * nb);
-        }
-        xv[pp] = nx[pp];
+    if (G == 0) {  // plane zl = 0: its -z neighbour is the CTA below's plane 7
+        const float2 v = k.hz[vc_hz_slot(0, yl, x)];
+        const float2 h_r = c.hr[0][0][5], h_i = c.hi[0][0][5];
+        nx[0].re.x = fmaf(h_r.x, v.x, fmaf(-h_i.x, v.y, nx[0].re.x));
+        nx[0].im.x = fmaf(h_r.x, v.y, fmaf(h_i.x, v.x, nx[0].im.x));
+    } else {  // plane zl = 7: its +z neighbour is the CTA above's plane 0
+        const float2 v = k.hz[vc_hz_slot(1, yl, x)];
+        const float2 h_r = c.hr[1][1][4], h_i = c.hi[1][1][4];
+        nx[1].re.y = fmaf(h_r.y, v.x, fmaf(-h_i.y, v.y, nx[1].re.y));
+        nx[1].im.y = fmaf(h_r.y, v.y, fmaf(h_i.y, v.x, nx[1].im.y));
     }
-    return true;
+    // the faces first (the neighbours wait for them), then the local stores
+    if (push && ok) vc_push_faces<G>(k, nx, b ^ 1);
+    if (fym || fyp) k.rb[vc_slot(G, IG, yl, x)] = nx[IG];
+    k.rb[vc_slot(G, G, yl, x)] = nx[G];
+    c.V[G][0] = nx[0];
+    c.V[G][1] = nx[1];
+    return ok;
 }
 
 // The whole engine.  Grid: 7 clusters of 16 CTAs (cluster k runs the
 // recursion of e_{l_k}); p.ncta is unused (the tail runs on cluster 0's 16
-// CTAs).  Dynamic shared memory: VcGeo<PP>::FIXED + the tail's K double2.
-template <int PP>
-__global__ void __launch_bounds__(VcGeo<PP>::NT, 1) gfmc_vc_engine(const Params p)
+// CTAs).  Dynamic shared memory: kVcFixedSmem + the tail's K double2.
+__global__ void __launch_bounds__(kVcNT, 1) gfmc_vc_engine(const Params p)
 {
-    using G = VcGeo<PP>;
-    constexpr int NT = G::NT, NW = G::NW, PY = kVcPY, NP = kVcNP, CY = 4, CZ = 4;
+    constexpr int NT = kVcNT, NW = kVcNW, PY = kVcPY, CY = 4, CZ = 4;
     extern __shared__ __align__(16) unsigned char vc_dyn[];
     __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ int s_loc[kVec];
@@ -281,24 +312,26 @@ __global__ void __launch_bounds__(VcGeo<PP>::NT, 1) gfmc_vc_engine(const Params 
     __shared__ double2 s_mu[NW][kPairs];
     __shared__ int s_acc, s_dead;
     __shared__ unsigned s_ra[8];
-    __shared__ int s_lpos[kVec];  // where l_j sits in this CTA's buffers: 2 (pair slot) + half, or -1
+    __shared__ int s_lpos[kVec];  // l_j in this CTA: 2 (pair slot) + half, or -1
+    __shared__ int s_lpar[kVec];  // parity of l_j
 
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    VcCtx<PP> k;
+    VcCtx k;
     k.rank = (int)cl.block_rank();
     k.vec = (int)(blockIdx.x / kVcC);
     k.ry = k.rank % CY;
     k.rz = k.rank / CY;
-    k.x = lane;
-    k.yl = warp % PY;
-    k.seg = warp / PY;
-    k.p0 = k.seg * PP;
+    // warps 0-3: columns of even parity cp = (x + y + z0) mod 2, warps 4-7: odd; a
+    // half-warp is one y row (y0 and z0 are even)
+    const int cp = warp >> 2;
+    k.yl = 2 * (warp & 3) + (lane >> 4);
+    k.x = 2 * (lane & 15) + ((cp + k.yl) & 1);
     k.rb = (VcPair*)vc_dyn;
-    k.hy = k.rb + G::RB;
-    k.hz = (float2*)(k.hy + G::HY);
-    double2* tail_dyn = (double2*)(vc_dyn + G::FIXED);
+    k.hy = k.rb + kVcSlots;
+    k.hz = (float2*)(k.hy + kVcHY);
+    double2* tail_dyn = (double2*)(vc_dyn + kVcFixedSmem);
     const unsigned hy_s = (unsigned)__cvta_generic_to_shared(k.hy), hz_s = (unsigned)__cvta_generic_to_shared(k.hz);
     k.mb = (unsigned)__cvta_generic_to_shared(mbar);
     {
@@ -329,7 +362,7 @@ __global__ void __launch_bounds__(VcGeo<PP>::NT, 1) gfmc_vc_engine(const Params 
     const int N = p.N, L = kVcL, M = p.M, S = M - 2;
     const bool tail_cluster = k.vec == 0;
     const long long nupd = (p.mode == MODE_SWEEP) ? p.n_updates : 1;
-    const int y = k.ry * PY + k.yl, z0 = k.rz * 2 * NP;
+    const int y = k.ry * PY + k.yl, z0 = k.rz * PY;
     const int xp = (k.x + 1) & 31, xm = (k.x + 31) & 31, yp = (y + 1) % L, ym = (y + L - 1) % L;
     unsigned ph0 = 0, ph1 = 0;
     bool dead = false;
@@ -357,114 +390,128 @@ __global__ void __launch_bounds__(VcGeo<PP>::NT, 1) gfmc_vc_engine(const Params 
 
         // ---- the recursion of e_{l_vec} on this cluster ----
         if (!dead) {
-            VcState<PP> st;
+            VcColumn col;
             const int src = s_loc[k.vec];
+            const int c0 = (src % L + (src / L) % L + src / (L * L)) & 1;  // parity of r_0
+            const int g0 = (c0 + cp) & 1;  // the column's group holding r_0 (and r_2, r_4, ...)
+            float2* mom_k = p.mom32 + (size_t)k.vec * kVec * M;  // [j][n] of this vector
             if (tid < kVec) {
                 const int g = s_loc[tid], gz = g / (L * L), gy = (g / L) % L, gx = g % L;
                 const int zl = gz - z0, yl = gy - k.ry * PY;
-                s_lpos[tid] = (zl >= 0 && zl < 2 * NP && yl >= 0 && yl < PY)
-                                  ? 2 * (((zl >> 1) * PY + yl) * 32 + gx) + (zl & 1) : -1;
+                s_lpos[tid] = (zl >= 0 && zl < PY && yl >= 0 && yl < PY)
+                                  ? 2 * vc_slot(zl & 1, zl >> 2, yl, gx) + ((zl >> 1) & 1) : -1;
+                s_lpar[tid] = (gx + gy + gz) & 1;
             }
-            float2* mom_k = p.mom32 + (size_t)k.vec * kVec * M;  // [j][n] of this vector
 #pragma unroll
-            for (int pp = 0; pp < PP; ++pp) {
-                const int pr = k.p0 + pp;
-                float r1re[2], r1im[2], r0re[2];
+            for (int g = 0; g < 2; ++g)
 #pragma unroll
-                for (int hf = 0; hf < 2; ++hf) {
-                    const int zl = 2 * pr + hf, zz = z0 + zl, zp = (zz + 1) % L, zm = (zz + L - 1) % L;
-                    const int gi = k.x + L * (y + L * zz);
-                    float2 hh[6], f;
-                    f = __ldcg(p.hop32 + gi);
-                    hh[0] = f;
-                    f = __ldcg(p.hop32 + (xm + L * (y + L * zz)));
-                    hh[1] = make_float2(f.x, -f.y);
-                    f = __ldcg(p.hop32 + (size_t)N + gi);
-                    hh[2] = f;
-                    f = __ldcg(p.hop32 + (size_t)N + (k.x + L * (ym + L * zz)));
-                    hh[3] = make_float2(f.x, -f.y);
-                    f = __ldcg(p.hop32 + 2 * (size_t)N + gi);
-                    hh[4] = f;
-                    f = __ldcg(p.hop32 + 2 * (size_t)N + (k.x + L * (y + L * zm)));
-                    hh[5] = make_float2(f.x, -f.y);
-                    const int nbg[6] = {xp + L * (y + L * zz), xm + L * (y + L * zz), k.x + L * (yp + L * zz),
-                                        k.x + L * (ym + L * zz), k.x + L * (y + L * zp), k.x + L * (y + L * zm)};
-                    r0re[hf] = gi == src ? 1.f : 0.f;
-                    float a = 0.f, c = 0.f;
+                for (int qq = 0; qq < 2; ++qq) {
+                    float r0re[2], r1re[2], r1im[2];
 #pragma unroll
-                    for (int d = 0; d < 6; ++d)
-                        if (nbg[d] == src) {
-                            a += hh[d].x;
-                            c += hh[d].y;
-                        }
-                    r1re[hf] = a;
-                    r1im[hf] = c;
+                    for (int hf = 0; hf < 2; ++hf) {
+                        const int zl = g + 2 * hf + 4 * qq, zz = z0 + zl, zp = (zz + 1) % L, zm = (zz + L - 1) % L;
+                        const int gi = k.x + L * (y + L * zz);
+                        float2 hh[6], f;
+                        f = __ldcg(p.hop32 + gi);
+                        hh[0] = f;
+                        f = __ldcg(p.hop32 + (xm + L * (y + L * zz)));
+                        hh[1] = make_float2(f.x, -f.y);
+                        f = __ldcg(p.hop32 + (size_t)N + gi);
+                        hh[2] = f;
+                        f = __ldcg(p.hop32 + (size_t)N + (k.x + L * (ym + L * zz)));
+                        hh[3] = make_float2(f.x, -f.y);
+                        f = __ldcg(p.hop32 + 2 * (size_t)N + gi);
+                        hh[4] = f;
+                        f = __ldcg(p.hop32 + 2 * (size_t)N + (k.x + L * (y + L * zm)));
+                        hh[5] = make_float2(f.x, -f.y);
+                        const int nbg[6] = {xp + L * (y + L * zz), xm + L * (y + L * zz), k.x + L * (yp + L * zz),
+                                            k.x + L * (ym + L * zz), k.x + L * (y + L * zp), k.x + L * (y + L * zm)};
+                        r0re[hf] = gi == src ? 1.f : 0.f;
+                        float a = 0.f, cc = 0.f;
 #pragma unroll
-                    for (int j = 0; j < kVec; ++j)
-                        if (gi == s_loc[j]) {
-                            mom_k[(size_t)j * M + 0] = make_float2(r0re[hf], 0.f);
-                            mom_k[(size_t)j * M + 1] = make_float2(a, c);
-                        }
+                        for (int d = 0; d < 6; ++d)
+                            if (nbg[d] == src) {
+                                a += hh[d].x;
+                                cc += hh[d].y;
+                            }
+                        r1re[hf] = a;
+                        r1im[hf] = cc;
 #pragma unroll
-                    for (int d = 0; d < 6; ++d) {
-                        if (hf == 0) {
-                            st.hr[pp][d].x = 2.f * hh[d].x;
-                            st.hi[pp][d].x = 2.f * hh[d].y;
-                        } else {
-                            st.hr[pp][d].y = 2.f * hh[d].x;
-                            st.hi[pp][d].y = 2.f * hh[d].y;
+                        for (int j = 0; j < kVec; ++j)
+                            if (gi == s_loc[j]) {
+                                mom_k[(size_t)j * M + 0] = make_float2(r0re[hf], 0.f);
+                                mom_k[(size_t)j * M + 1] = make_float2(a, cc);
+                            }
+#pragma unroll
+                        for (int d = 0; d < 6; ++d) {
+                            if (hf == 0) {
+                                col.hr[g][qq][d].x = 2.f * hh[d].x;
+                                col.hi[g][qq][d].x = 2.f * hh[d].y;
+                            } else {
+                                col.hr[g][qq][d].y = 2.f * hh[d].x;
+                                col.hi[g][qq][d].y = 2.f * hh[d].y;
+                            }
                         }
                     }
+                    // group g0 holds r_0, the other group r_1 (zero on the wrong parity)
+                    if (g == g0) {
+                        col.V[g][qq].re = make_float2(r0re[0], r0re[1]);
+                        col.V[g][qq].im = make_float2(0.f, 0.f);
+                    } else {
+                        col.V[g][qq].re = make_float2(r1re[0], r1re[1]);
+                        col.V[g][qq].im = make_float2(r1im[0], r1im[1]);
+                        k.rb[vc_slot(g, qq, k.yl, k.x)] = col.V[g][qq];
+                    }
                 }
-                st.A[pp].re = make_float2(r0re[0], r0re[1]);
-                st.A[pp].im = make_float2(0.f, 0.f);
-                st.B[pp].re = make_float2(r1re[0], r1re[1]);
-                st.B[pp].im = make_float2(r1im[0], r1im[1]);
-                // r_1 into buffer 1 and its faces into the neighbours' halos of buffer 1
-                const int pi = (pr * PY + k.yl) * 32 + k.x;
-                k.rb[kVcPT + pi] = st.B[pp];
-                const bool stall = p.stall && k.vec == 0 && k.rank == 0;
-                if (!stall) {
-                    if (k.yl == 0) vc_push4(k.ra[0] + 16u * (unsigned)(((1 * 2 + 1) * NP + pr) * 32 + k.x), st.B[pp], k.ra[4] + 8);
-                    if (k.yl == PY - 1)
-                        vc_push4(k.ra[1] + 16u * (unsigned)(((1 * 2 + 0) * NP + pr) * 32 + k.x), st.B[pp], k.ra[5] + 8);
-                    if (pr == 0)
-                        vc_push2(k.ra[2] + 8u * (unsigned)(((1 * 2 + 1) * PY + k.yl) * 32 + k.x), st.B[pp].re.x,
-                                 st.B[pp].im.x, k.ra[6] + 8);
-                    if (pr == NP - 1)
-                        vc_push2(k.ra[3] + 8u * (unsigned)(((1 * 2 + 0) * PY + k.yl) * 32 + k.x), st.B[pp].re.y,
-                                 st.B[pp].im.y, k.ra[7] + 8);
-                }
+            // the faces of r_1 (group 1 - g0) into the neighbours' halos of step 1
+            if (!(p.stall && k.vec == 0 && k.rank == 0)) {
+                if (g0 == 1) vc_push_faces<0>(k, col.V[0], 1);
+                else vc_push_faces<1>(k, col.V[1], 1);
             }
             __syncthreads();
-            // mu_n^{j, vec} = r_n[l_j] for the local sites in this CTA, read from the buffer
-            // that holds r_n (complete after the step's CTA barrier)
-            auto emit = [&](int buf, int n) {
-                if (tid < kVec && s_lpos[tid] >= 0) {
-                    const int at = s_lpos[tid];
-                    const VcPair v = k.rb[buf * kVcPT + (at >> 1)];
-                    mom_k[(size_t)tid * M + n] = (at & 1) ? make_float2(v.re.y, v.im.y) : make_float2(v.re.x, v.im.x);
+            // mu_n^{j, vec} = r_n[l_j] for the local sites in this CTA, read from the
+            // buffer after the step's CTA barrier (zero on the parity r_n does not live on)
+            // (warps 1 and 2, whose rows have no y face, arm the barriers and emit)
+            auto emit = [&](int n) {
+                const int j = tid - kVcEmitTid;
+                if (j >= 0 && j < kVec && s_lpos[j] >= 0) {
+                    const int at = s_lpos[j];
+                    float2 v = make_float2(0.f, 0.f);
+                    if (s_lpar[j] == ((c0 + n) & 1)) {
+                        const VcPair w = k.rb[at >> 1];
+                        v = (at & 1) ? make_float2(w.re.y, w.im.y) : make_float2(w.re.x, w.im.x);
+                    }
+                    mom_k[(size_t)j * M + n] = v;
                 }
             };
-            // steps m = 1 .. S (S = M - 2, even): odd m overwrites A with r_{m+1} (buffer 0),
-            // even m overwrites B (buffer 1)
+            // a thread whose wait ran out sends nothing more; the CTA then stops, and
+            // lingers before the final cluster barrier so that the faces its other
+            // threads sent before have landed
+            auto stop = [&](int m) {
+                if (tid == 0) set_error(p, ERR_TIMEOUT, 300 + k.vec, m);
+                dead = true;
+                const long long t0 = clock64();
+                while (clock64() - t0 < (1ll << 21)) __nanosleep(256);
+            };
+            // steps m = 1 .. S (S = M - 2, even): odd m advances group g0, even m the other
             for (int m = 1; m <= S; m += 2) {
-                if (!vc_step<PP>(k, st, st.B, st.A, 1, ph1, true, p.budget)) {
-                    if (tid == 0) set_error(p, ERR_TIMEOUT, 300 + k.vec, m);
-                    dead = true;
+                bool ok = g0 == 0 ? vc_step<0>(k, col, 1, ph1, true, p.budget) : vc_step<1>(k, col, 1, ph1, true, p.budget);
+                ph1 ^= 1u;
+                if (__syncthreads_or(!ok)) {
+                    stop(m);
                     break;
                 }
-                __syncthreads();
-                if (tid == 0) vc_mbar_arm(k.mb + 8);
-                emit(0, m + 1);
-                if (!vc_step<PP>(k, st, st.A, st.B, 0, ph0, m + 1 < S, p.budget)) {
-                    if (tid == 0) set_error(p, ERR_TIMEOUT, 300 + k.vec, m + 1);
-                    dead = true;
+                if (tid == kVcArmTid) vc_mbar_arm(k.mb + 8);
+                emit(m + 1);
+                ok = g0 == 0 ? vc_step<1>(k, col, 0, ph0, m + 1 < S, p.budget)
+                             : vc_step<0>(k, col, 0, ph0, m + 1 < S, p.budget);
+                ph0 ^= 1u;
+                if (__syncthreads_or(!ok)) {
+                    stop(m + 1);
                     break;
                 }
-                __syncthreads();
-                if (tid == 0) vc_mbar_arm(k.mb);
-                emit(1, m + 2);
+                if (tid == kVcArmTid) vc_mbar_arm(k.mb);
+                emit(m + 2);
             }
         }
         // ---- all recursions done: the tail on cluster 0 ----
