@@ -161,9 +161,11 @@ struct VcCtx {
     VcPair* hy;        // [kVcHY]
     float2* hz;        // [kVcHZ]
     unsigned mb;       // this CTA's two mbarriers (shared::cta)
-    // shared memory, the neighbours' shared::cluster addresses: halo buffers
-    // of -y, +y, -z, +z, then their mbarriers in the same order
-    const unsigned* ra;
+    // shared::cluster addresses this thread writes faces to: the y halo slot of
+    // its row's face (pair 0 of group 0; 0 if the row has no y face) and that
+    // CTA's mbarrier 0, the z halo slot of its column below and above and
+    // those CTAs' mbarrier 0
+    unsigned y_slot, y_mb, zdn_slot, zdn_mb, zup_slot, zup_mb;
 };
 
 // The faces of a column after its group G was advanced: the y-face rows send
@@ -172,18 +174,13 @@ struct VcCtx {
 template <int G>
 __device__ __forceinline__ void vc_push_faces(const VcCtx& k, const VcPair (&nx)[2], int b)
 {
-    const int x = k.x, yl = k.yl;
-    if (yl == 0) {
-        vc_push4(k.ra[0] + 16u * (unsigned)vc_hy_slot(1, G, 0, x), nx[0], k.ra[4] + 8 * b);
-        vc_push4(k.ra[0] + 16u * (unsigned)vc_hy_slot(1, G, 1, x), nx[1], k.ra[4] + 8 * b);
-    } else if (yl == kVcPY - 1) {
-        vc_push4(k.ra[1] + 16u * (unsigned)vc_hy_slot(0, G, 0, x), nx[0], k.ra[5] + 8 * b);
-        vc_push4(k.ra[1] + 16u * (unsigned)vc_hy_slot(0, G, 1, x), nx[1], k.ra[5] + 8 * b);
+    // slot (G, q) of a y halo is vc_hy_slot(side, 0, 0, x) + (2 G + q) * 32
+    if (k.y_slot) {
+        vc_push4(k.y_slot + 16u * (unsigned)(2 * G * 32), nx[0], k.y_mb + 8 * b);
+        vc_push4(k.y_slot + 16u * (unsigned)((2 * G + 1) * 32), nx[1], k.y_mb + 8 * b);
     }
-    if (G == 0)
-        vc_push2(k.ra[2] + 8u * (unsigned)vc_hz_slot(1, yl, x), nx[0].re.x, nx[0].im.x, k.ra[6] + 8 * b);
-    else
-        vc_push2(k.ra[3] + 8u * (unsigned)vc_hz_slot(0, yl, x), nx[1].re.y, nx[1].im.y, k.ra[7] + 8 * b);
+    if (G == 0) vc_push2(k.zdn_slot, nx[0].re.x, nx[0].im.x, k.zdn_mb + 8 * b);
+    else vc_push2(k.zup_slot, nx[1].re.y, nx[1].im.y, k.zup_mb + 8 * b);
 }
 
 // One step on group G of the thread's column: r_{m+1} = 2 Htilde r_m - r_{m-1}
@@ -311,7 +308,6 @@ __global__ void __launch_bounds__(kVcNT, 1) gfmc_vc_engine(const Params p)
     __shared__ double s_draw[3];
     __shared__ double2 s_mu[NW][kPairs];
     __shared__ int s_acc, s_dead;
-    __shared__ unsigned s_ra[8];
     __shared__ int s_lpos[kVec];  // l_j in this CTA: 2 (pair slot) + half, or -1
     __shared__ int s_lpar[kVec];  // parity of l_j
 
@@ -337,17 +333,20 @@ __global__ void __launch_bounds__(kVcNT, 1) gfmc_vc_engine(const Params p)
     {
         const int r_ym = (k.ry + CY - 1) % CY + k.rz * CY, r_yp = (k.ry + 1) % CY + k.rz * CY;
         const int r_zm = k.ry + ((k.rz + CZ - 1) % CZ) * CY, r_zp = k.ry + ((k.rz + 1) % CZ) * CY;
-        if (tid == 0) {
-            s_ra[0] = vc_mapa(hy_s, r_ym);
-            s_ra[1] = vc_mapa(hy_s, r_yp);
-            s_ra[2] = vc_mapa(hz_s, r_zm);
-            s_ra[3] = vc_mapa(hz_s, r_zp);
-            s_ra[4] = vc_mapa(k.mb, r_ym);
-            s_ra[5] = vc_mapa(k.mb, r_yp);
-            s_ra[6] = vc_mapa(k.mb, r_zm);
-            s_ra[7] = vc_mapa(k.mb, r_zp);
+        // a face row y = y0 feeds the +y side of the CTA below, y = y0 + 7 the -y side above
+        k.y_slot = 0;
+        k.y_mb = 0;
+        if (k.yl == 0) {
+            k.y_slot = vc_mapa(hy_s + 16u * (unsigned)vc_hy_slot(1, 0, 0, k.x), r_ym);
+            k.y_mb = vc_mapa(k.mb, r_ym);
+        } else if (k.yl == PY - 1) {
+            k.y_slot = vc_mapa(hy_s + 16u * (unsigned)vc_hy_slot(0, 0, 0, k.x), r_yp);
+            k.y_mb = vc_mapa(k.mb, r_yp);
         }
-        k.ra = s_ra;
+        k.zdn_slot = vc_mapa(hz_s + 8u * (unsigned)vc_hz_slot(1, k.yl, k.x), r_zm);
+        k.zdn_mb = vc_mapa(k.mb, r_zm);
+        k.zup_slot = vc_mapa(hz_s + 8u * (unsigned)vc_hz_slot(0, k.yl, k.x), r_zp);
+        k.zup_mb = vc_mapa(k.mb, r_zp);
     }
     if (tid == 0) {
         vc_mbar_init(k.mb);
