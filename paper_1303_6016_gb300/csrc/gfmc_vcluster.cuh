@@ -59,8 +59,8 @@ constexpr int kVcHY = 2 * 2 * 2 * 32;         // y halo: [side][g][q][x] pair sl
 constexpr int kVcHZ = 2 * kVcPY * 32;         // z halo: [side][yl][x] values
 constexpr int kVcHaloBytes = 4096;            // faces a CTA receives per step (half of each face)
 constexpr int kVcFixedSmem = (kVcSlots + kVcHY) * 16 + kVcHZ * 8;
-constexpr int kVcArmTid = 32;   // warp 1: rows yl = 2, 3 (no y face)
-constexpr int kVcEmitTid = 64;  // warp 2: rows yl = 4, 5
+constexpr int kVcArmTid = 128;   // warp 4: rows yl = 4, 5 (no y face), sub-partition 0
+constexpr int kVcEmitTid = 224;  // warp 7: rows yl = 2, 3, sub-partition 3
 
 struct __align__(16) VcPair {
     float2 re, im;
@@ -320,9 +320,11 @@ __global__ void __launch_bounds__(kVcNT, 1) gfmc_vc_engine(const Params p)
     k.ry = k.rank % CY;
     k.rz = k.rank / CY;
     // warps 0-3: columns of even parity cp = (x + y + z0) mod 2, warps 4-7: odd; a
-    // half-warp is one y row (y0 and z0 are even)
+    // half-warp is one y row (y0 and z0 are even).  The odd warps take their rows
+    // two warps further on, so that each SM sub-partition (warp mod 4) holds one
+    // of the four warps with a y-face row (rows 0 and 7: warps 0, 3, 5, 6).
     const int cp = warp >> 2;
-    k.yl = 2 * (warp & 3) + (lane >> 4);
+    k.yl = 2 * ((warp + 2 * cp) & 3) + (lane >> 4);
     k.x = 2 * (lane & 15) + ((cp + k.yl) & 1);
     k.rb = (VcPair*)vc_dyn;
     k.hy = k.rb + kVcSlots;
@@ -470,7 +472,7 @@ __global__ void __launch_bounds__(kVcNT, 1) gfmc_vc_engine(const Params p)
             __syncthreads();
             // mu_n^{j, vec} = r_n[l_j] for the local sites in this CTA, read from the
             // buffer after the step's CTA barrier (zero on the parity r_n does not live on)
-            // (warps 1 and 2, whose rows have no y face, arm the barriers and emit)
+            // (warps 4 and 7, whose rows have no y face, arm the barriers and emit)
             auto emit = [&](int n) {
                 const int j = tid - kVcEmitTid;
                 if (j >= 0 && j < kVec && s_lpos[j] >= 0) {
