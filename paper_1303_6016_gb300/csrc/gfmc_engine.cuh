@@ -1530,6 +1530,139 @@ __device__ __forceinline__ void magnetisation_partial(const Params& p, int s0, i
     if (tid == 0) p.magpart[3 * cta + 2] = a0;
 }
 
+// ---------------------------------------------------------------------------
+// FP64 single-chain engine on a bipartite lattice (L even)
+// ---------------------------------------------------------------------------
+// With L even, T_n(Htilde) e_v is zero on every site whose parity
+// (x + y + z) mod 2 differs from parity(l_v) + n; o and its 6 neighbours have
+// opposite parities.  So at step m a site holds either r_m of vector 0 or
+// r_m of vectors 1..6, and <r_m^j|r_m^k> vanishes unless j, k are both 0 or
+// both >= 1, <r_m^j|r_{m+1}^k> (j <= k) unless j = 0 < k.
+
+// Site of thread tid of a tile [s0, s1): tid < 128 the tid-th even-parity site
+// of the tile, tid in [128, 256) the (tid - 128)-th odd one; -1 if none (and
+// for the threads beyond 256).  n[c] receives the count of parity c.  Every
+// thread of the block calls it.
+__device__ __forceinline__ int bip_site_map(int s0, int s1, int L, int (&n)[2])
+{
+    __shared__ int s_map[256];
+    __shared__ int s_cnt[2][8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < 256) s_map[tid] = -1;
+    const int s = s0 + tid;
+    const bool valid = tid < 256 && s < s1;
+    const int par = valid ? (s % L + (s / L) % L + s / (L * L)) & 1 : 0;
+    unsigned me = 0, mo = 0;
+    if (tid < 256) {
+        me = __ballot_sync(0xffffffffu, valid && par == 0);
+        mo = __ballot_sync(0xffffffffu, valid && par == 1);
+        if (lane == 0) {
+            s_cnt[0][warp] = __popc(me);
+            s_cnt[1][warp] = __popc(mo);
+        }
+    }
+    __syncthreads();
+    if (valid) {
+        int r = __popc((par ? mo : me) & ((1u << lane) - 1u));
+        for (int w = 0; w < warp; ++w) r += s_cnt[par][w];
+        s_map[par * 128 + r] = s;  // r < 128: the host admits tiles whose classes have at most 128 sites
+    }
+    n[0] = n[1] = 0;
+    for (int w = 0; w < 8; ++w) {
+        n[0] += s_cnt[0][w];
+        n[1] += s_cnt[1][w];
+    }
+    __syncthreads();
+    return tid < 256 ? s_map[tid] : -1;
+}
+
+constexpr int kBipUnits = 28;
+constexpr int kBipGroups = 8;
+
+// The 28 Gram units that are not zero by parity, each over 8 site groups of
+// its staging range: [a0, a1) holds the sites with r_m of vector 0, [b0, b1)
+// those with r_m of vectors 1..6.  Rows of the staging area: v = r_m^v,
+// 7+v = r_{m+1}^v, 14+v = -i r_m^v, 21+v = -i r_{m+1}^v.  Units 0-5:
+// <r_m^0|r_{m+1}^k> (block 2, over a); 6-20: <r_m^j|r_m^k>, 1 <= j < k (over
+// b); 21: |r_m^0|^2 (over a); 22-27: |r_m^j|^2, j >= 1 (over b).
+__device__ __forceinline__ void gram_units_bip(const double2* sr, int a0, int a1, int b0, int b1, double* gsum)
+{
+    const int tid = threadIdx.x;
+    if (tid >= kBipUnits * kBipGroups) return;
+    const int u = tid % kBipUnits, g = tid / kBipUnits;
+    int rx = 0, ry = 0, rz = 0, ere, lo, hi;
+    bool offd = true;
+    if (u < 6) {
+        const int k = u + 1;
+        ry = kVec + k;
+        rz = 3 * kVec + k;
+        ere = 56 + 2 * pair_of(0, k);
+        lo = a0;
+        hi = a1;
+    } else if (u < 21) {
+        int q = u - 6, j = 1;
+        while (q >= 6 - j) {
+            q -= 6 - j;
+            ++j;
+        }
+        const int k = j + 1 + q;
+        rx = j;
+        ry = k;
+        rz = 2 * kVec + k;
+        ere = 2 * pair_of(j, k);
+        lo = b0;
+        hi = b1;
+    } else {
+        const int j = u - 21;
+        rx = j;
+        offd = false;
+        ere = 2 * pair_of(j, j);
+        lo = j == 0 ? a0 : b0;
+        hi = j == 0 ? a1 : b1;
+    }
+    const double2* xs = sr + rx * kStage;
+    double re = 0.0, im = 0.0;
+    if (offd) {
+        const double2* ys = sr + ry * kStage;
+        const double2* zs = sr + rz * kStage;
+        for (int s = lo + g; s < hi; s += kBipGroups) {
+            const double2 x = xs[s], y = ys[s], z = zs[s];
+            re = fma(x.x, y.x, re);
+            re = fma(x.y, y.y, re);
+            im = fma(x.x, z.x, im);
+            im = fma(x.y, z.y, im);
+        }
+    } else {
+        for (int s = lo + g; s < hi; s += kBipGroups) {
+            const double2 x = xs[s];
+            re = fma(x.x, x.x, re);
+            re = fma(x.y, x.y, re);
+        }
+    }
+    double* gs = gsum + g * kEntries;
+    gs[ere] = re;
+    gs[ere + 1] = im;
+}
+
+// out[e] = the 8 groups of gram_units_bip added in order, or 0 for the
+// entries that vanish by parity (threads e < kEntries).
+__device__ __forceinline__ void gram_groups_bip(const double* gsum, double* out)
+{
+    const int e = threadIdx.x;
+    if (e < kEntries) {
+        const int pp = (e % 56) >> 1;
+        const int j = pair_j(pp), k = pair_k(pp);
+        const bool live = e < 56 ? !(j == 0 && k > 0) && !(j == k && (e & 1)) : (j == 0 && k > 0);
+        double s = 0.0;
+        if (live) {
+            s = gsum[e];
+#pragma unroll
+            for (int g = 1; g < kBipGroups; ++g) s += gsum[g * kEntries + e];
+        }
+        out[e] = s;
+    }
+}
+
 // Barrier of all CTAs of a chain: the grid barrier of a cooperative team, or
 // the hardware barrier of the chain's cluster (VARIANT 2; no wait can time out,
 // so every CTA of a cluster always runs the same sequence of barriers).
@@ -1589,8 +1722,15 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
     const int N = p.N, L = p.L, M = p.M;
     const int s0 = VARIANT == 2 ? cta * (p.N / p.ncta) : p.tile_start[cta];
     const int s1 = VARIANT == 2 ? s0 + p.N / p.ncta : p.tile_start[cta + 1];
-    const int i = s0 + tid;
-    const bool active = VARIANT == 0 && i < s1;
+    int i = s0 + tid;
+    bool active = VARIANT == 0 && i < s1;
+    [[maybe_unused]] int bip_n[2] = {0, 0};
+    if constexpr (VARIANT == 0 && sizeof(R) == 8 && NT > kThreads) {
+        if (p.bip) {
+            i = bip_site_map(s0, s1, p.L, bip_n);
+            active = i >= 0;
+        }
+    }
     const R2* hop = nullptr;
     if constexpr (sizeof(R) == 8) hop = (const R2*)p.hop64; else hop = (const R2*)p.hop32;
 
@@ -1875,6 +2015,78 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                         }
                     }
                     if (!ok) return;
+                } else if (p.bip) {
+                    // bipartite lattice: this thread's site holds r_m of vector 0 when its
+                    // parity is parity(o) + m (then it advances vectors 1..6), else r_m of
+                    // vectors 1..6 (then it advances vector 0); warps 0-3 hold the even
+                    // sites and warps 4-7 the odd ones, so the choice is warp-uniform
+                    const int o0 = s_loc[0];
+                    const int par_o = (o0 % L + (o0 / L) % L + o0 / (L * L)) & 1;
+                    const int cls = tid >= 128 ? 1 : 0;
+                    const double2* wsm = dyn + 4 * kVec * kStage;
+                    const int W = p.win_max;
+                    for (int m = 1; m <= p.nsteps; ++m) {
+                        // barrier 3 also ends every compute warp's Gram units of step m-1
+                        nbar_sync(3, NT);
+                        if (!s_go) return;
+                        if (m >= 2)
+                            gram_groups_bip(&red[0][0], p.partial + ((size_t)(m - 2) * p.ncta + cta) * kEntries);
+                        const R2* rd = (m & 1) ? buf1 : buf0;  // r_m of every site
+                        R2* wr = (m & 1) ? buf0 : buf1;        // receives r_{m+1}; held r_{m-1}
+                        const int pa = (par_o + m) & 1;        // parity of the sites holding r_m^0
+                        const bool holds0 = cls == pa;
+                        R2 nxt[kVec];
+    #pragma unroll
+                        for (int v = 0; v < kVec; ++v) nxt[v] = c_make<R2>(0, 0);
+                        if (active) {
+                            // h holds 2 Htilde: r_{m+1} = -r_{m-1} + sum_d (2 h_d) r_m(nb_d), FMAs only
+                            auto adv = [&](int v) {
+                                R2 acc = c_make<R2>(-prv[v].x, -prv[v].y);
+                                if (p.prefetch) {
+    #pragma unroll
+                                    for (int d = 0; d < 6; ++d) c_fma(acc, h[d], wsm[v * W + nbo[d]]);
+                                } else {
+                                    const R2* cv = rd + (size_t)v * N;
+    #pragma unroll
+                                    for (int d = 0; d < 6; ++d) c_fma(acc, h[d], ldcg2(cv + nb[d]));
+                                }
+                                nxt[v] = acc;
+                                if (m < p.nsteps) stcg2(wr + (size_t)v * N + i, acc);
+                            };
+                            if (holds0) {
+    #pragma unroll
+                                for (int v = 1; v < kVec; ++v) adv(v);
+                            } else {
+                                adv(0);
+                            }
+                        }
+                        // stage the rows the units of this thread's class read
+                        if (holds0) {
+                            dyn[tid] = cur[0];
+    #pragma unroll
+                            for (int v = 1; v < kVec; ++v) {
+                                dyn[(kVec + v) * kStage + tid] = nxt[v];
+                                dyn[(3 * kVec + v) * kStage + tid] = minus_i(nxt[v]);
+                            }
+                        } else {
+    #pragma unroll
+                            for (int v = 1; v < kVec; ++v) {
+                                dyn[v * kStage + tid] = cur[v];
+                                dyn[(2 * kVec + v) * kStage + tid] = minus_i(cur[v]);
+                            }
+                        }
+                        nbar_arrive(2, NT);
+                        nbar_sync(1, kThreads);
+                        const int a0 = pa * 128, b0 = (1 - pa) * 128;
+                        gram_units_bip(dyn, a0, a0 + bip_n[pa], b0, b0 + bip_n[1 - pa], &red[0][0]);
+    #pragma unroll
+                        for (int v = 0; v < kVec; ++v) {
+                            prv[v] = cur[v];
+                            cur[v] = nxt[v];
+                        }
+                    }
+                    nbar_sync(1, kThreads);
+                    gram_groups_bip(&red[0][0], p.partial + ((size_t)(p.nsteps - 1) * p.ncta + cta) * kEntries);
                 } else {
                     for (int m = 1; m <= p.nsteps; ++m) {
                         // barrier 3 also ends every compute warp's Gram units of step m-1
@@ -2217,7 +2429,7 @@ template <class R, int NV> constexpr int engine_threads()
 
 // A single chain spread over the whole GPU.
 template <class R, int NV = kVec>
-__global__ void __launch_bounds__(engine_threads<R, NV>()) gfmc_engine(const Params p)
+__global__ void __launch_bounds__(engine_threads<R, NV>(), 1) gfmc_engine(const Params p)
 {
     extern __shared__ double2 dyn[];
     run_chain<R, 0, NV, engine_threads<R, NV>()>(p, blockIdx.x, dyn, nullptr);

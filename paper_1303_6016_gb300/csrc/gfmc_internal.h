@@ -66,6 +66,12 @@ struct Params {
     const int2* win;        // [win_ptr[ncta]]
     int win_max;
     int prefetch;
+    // FP64 single-chain engine, L even (the periodic cubic lattice is then
+    // bipartite): warps 0-3 take the tile's even-parity sites, warps 4-7 the
+    // odd ones, and each step advances only the vectors that are nonzero at a
+    // site (vector o on one parity, its 6 neighbours' on the other) and forms
+    // only the Gram sums that are not zero by parity
+    int bip;
     // single-chain engines on 256 threads (FP32 unit vectors, proposal vectors):
     // every tile fits 7 warps, so warp 7 publishes and polls the flags while
     // the other warps form the Gram sums
