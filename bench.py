@@ -36,8 +36,8 @@ if ROOT not in sys.path:
 METRIC = "spin updates/s at L=32,M=1024 (FP64 vs FP32-mixed); stencil GB/s; p99 sweep latency"
 UNIT = "spin updates/s"
 
-# Algorithmic work of one site in one fused stencil step, recursion on the 7
-# unit vectors:
+# Algorithmic work of one site in one fused stencil step of the doubling
+# (M/2 - 1 steps), recursion on the 7 unit vectors:
 #   stencil  7 x (6 complex MACs + 2r - r_prev)      = 7 x (6 x 8 + 4)   = 364 flop
 #   Gram     28 <r_m|r_m> (7 real diagonal) + 28 <r_m|r_m+1>
 #            = 7 x 3 + 21 x 6 + 28 x 6                                     = 315 flop
@@ -46,12 +46,25 @@ UNIT = "spin updates/s"
 # 3 flop + 8 sums = 136 flop.
 FLOP_PER_SITE_STEP = 364 + 315 + 112
 FLOP_PER_SITE_STEP_PROPOSAL = 2 * 52 + 8 * 3 + 8
+# With L even the periodic cubic lattice is bipartite: r_m of vector o lives on
+# one parity and r_m of its 6 neighbours on the other, so half of the stencil
+# terms and most Gram products above are zero by construction.  What is left,
+# per pair of sites (one of each parity) and step:
+#   stencil  7 vector-site updates x 52                                     = 364 flop
+#   Gram     7 real diagonals x 3 + 15 pairs among the neighbours x 6
+#            + 6 products <r_m^o|r_m+1^k> x 6                              = 147 flop
+#   sums     49 nonzero real entries                                          = 49 flop
+# i.e. 280 flop per site and step: the work the FP64 engine does on even L.
+FLOP_PER_SITE_STEP_BIPARTITE = (364 + 147 + 49) / 2
 
 
-# Bytes of one site in one step: read r_m and r_{m-1}, write r_{m+1} for each
-# of the nv vectors (3 nv complex values) plus the site's bond row (3 complex).
+# Bytes of one site in one step of the doubling: read r_m and r_{m-1}, write
+# r_{m+1} for each of the nv vectors (3 nv complex values) plus the site's
+# spinor (3 reals), B_upd = (M/2) N (21 s_c + s_chi): 180 B FP32, 360 B FP64
+# for the 7 unit vectors.  The checkerboard recursion of the FP32 engine
+# (M - 2 steps over half the sites each) moves exactly these values.
 def bytes_per_site_step(real_bytes: int, nv: int = 7) -> int:
-    return 3 * nv * 2 * real_bytes + 3 * 2 * real_bytes
+    return 3 * nv * 2 * real_bytes + 3 * real_bytes
 
 
 def update_work(L: int, M: int, real_bytes: int, nv: int = 7):
@@ -61,10 +74,17 @@ def update_work(L: int, M: int, real_bytes: int, nv: int = 7):
     return steps * N * flop, steps * N * bytes_per_site_step(real_bytes, nv)
 
 
-# DRAM bytes per update of the engine kernels from one ncu capture each
-# (profiles/gfmc_engine_L32_M1024.md), valid only for the engine sources they
-# were taken from: bench.py reports them as roofline.traffic while the hash of
-# those sources is unchanged, and null otherwise.
+def update_flop_nonzero(L: int, M: int) -> float:
+    """Flop of one update of the FP64 engine without the terms that vanish by
+    parity (L even; the full count for odd L)."""
+    per = FLOP_PER_SITE_STEP_BIPARTITE if L % 2 == 0 else FLOP_PER_SITE_STEP
+    return (M // 2 - 1) * L ** 3 * per
+
+
+# DRAM bytes per update of the engine kernels from one ncu capture each, valid
+# only for the engine sources they were taken from: bench.py reports them as
+# roofline.traffic while the hash of those sources is unchanged, and null
+# otherwise.
 TRAFFIC_SOURCES = ("gfmc_engine.cuh", "gfmc_k64.cu", "gfmc_k32.cu", "gfmc_internal.h")
 TRAFFIC_HASH = "83228e9edc9f11b6"
 TRAFFIC_PER_UPDATE = {"fp64": 40.983552e6, "fp32_mixed": 40.681472e6}
@@ -427,13 +447,17 @@ def time_e2e(ch, stream, U, steps, spins0):
     return per, h2d, d2h
 
 
-def cpu_baseline(L, M, spins, n_updates):
+def cpu_baseline(L, M, spins, n_updates, threads):
+    """The oracle on `threads` host threads (its site and node loops; results
+    are bitwise the same for any count)."""
     from oracle import oracle as O
     O.build()
+    O.set_threads(threads)
     t0 = time.perf_counter()
     O.updates(L, spins, n_updates, M, beta=20.0, chem=-2.0, seed=1)
     dt = time.perf_counter() - t0
-    return n_updates / dt, dt
+    used = O.max_threads()
+    return n_updates / dt, dt, used
 
 
 def run_reference(args, rank, world, dist):
@@ -445,6 +469,8 @@ def run_reference(args, rank, world, dist):
     spins = inputs.uniform_sphere(L, 0)
     from oracle import oracle as O
     O.build()
+    O.set_threads(os.cpu_count() or 1)
+    cores = O.max_threads()
     U = 1
     per = []
     s = spins.copy()
@@ -462,8 +488,9 @@ def run_reference(args, rank, world, dist):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": dict(workload_config(L, M, U, "fp64"), l2="not applicable: the CPU oracle"),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{U} update per step from the start of sweep 0 at L={L}, M={M}"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{U} update per step from the start of sweep 0 at L={L}, M={M}, "
+                                   f"OpenMP over the oracle's site and node loops on {cores} threads"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -489,7 +516,10 @@ def main():
     ap.add_argument("--M", type=int, default=1024)
     ap.add_argument("--updates-per-step", type=int, default=0)
     ap.add_argument("--mixed-updates-per-step", type=int, default=0)
-    ap.add_argument("--cpu-updates", type=int, default=2)
+    ap.add_argument("--cpu-updates", type=int, default=6)
+    ap.add_argument("--cpu-updates-all", type=int, default=40)
+    ap.add_argument("--sweeps-l32", type=int, default=0,
+                    help="also time this many full FP32-mixed sweeps of the L=32 chain (each ~30 s)")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-latency", action="store_true")
@@ -529,9 +559,11 @@ def main():
     value = aggregate(world, args.steps, U, total_ms)
     ms_step = total_ms / args.steps
     flop_u, bytes_u = update_work(L, M, 8)
+    flop_nz = update_flop_nonzero(L, M)
     launch_s = statistics.mean(per) / 1000.0
-    achieved_tf = U * flop_u / launch_s / 1e12
-    peak_tf = alu_peak_tflops("fp64", clocks.get("sm_max_mhz") or 2070.0) if clocks else alu_peak_tflops("fp64")
+    achieved_tf = U * flop_nz / launch_s / 1e12
+    derived_tf = alu_peak_tflops("fp64", clocks.get("sm_max_mhz") or 2070.0) if clocks else alu_peak_tflops("fp64")
+    peak_tf = gfmc.fma_peak_tflops("fp64", repeats=3, stream=stream.cuda_stream)
     e2e_per, h2d, d2h = time_e2e(ch, stream, U, max(3, args.steps // 2), ch.get_spins())
     e2e_value = U / (statistics.mean(e2e_per) / 1000.0) * world
     ch.close()
@@ -546,8 +578,15 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s",
                      "frac": achieved_tf / peak_tf, "traffic": traffic_per_launch("fp64", U),
                      "traffic_unit": "bytes per launch (DRAM read + write, ncu)",
-                     "peak_source": "FP64 vector peak derived from 152 SMs x max SM clock x 2 FMA lanes "
-                                    "(1.25 TFLOP/s class); not in MEASURED_PEAKS.json"},
+                     "flop_per_update": flop_nz,
+                     "flop_note": "flop of the update without the terms that vanish by parity on the bipartite "
+                                  "lattice (280 per site and step of the M/2-1 doubling steps at even L; the "
+                                  "count with them, 791, gives flop_full_per_update)",
+                     "flop_full_per_update": flop_u,
+                     "peak_source": "measured in this run: gfmc_measure_fma_peak (own kernel, 16 independent "
+                                    "double fma chains per thread, 2 CTAs of 256 per SM, best of 3, CUDA events)",
+                     "peak_derived": derived_tf,
+                     "peak_derived_source": "152 SMs x max SM clock x 2 FP64 FMA lanes per SM x 2 flop"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
         "clocks": clocks,
@@ -618,19 +657,28 @@ def main():
 
     if not args.no_serving:
         from paper_1303_6016_gb300 import serving
-        line["serving"] = serving.sweep(rates=(10, 100), seconds=3.0, K=2, drain_s=8.0)
+        line["serving"] = serving.sweep(rates=(10, 100, 1000), seconds=3.0, K=2, drain_s=8.0)
 
     if not args.no_latency:
         line["sweep_latency"] = [sweep_latency(gfmc, inputs, stream, 8, M, prec, args.latency_sweeps)
                                  for prec in ("fp64", "fp32_mixed")]
         line["sweep_latency_note"] = ("full sequential sweeps of an 8^3 chain; at L=32 a sweep is "
                                       "32768 updates, i.e. 32768 x latency_ms_per_update")
+        if args.sweeps_l32 > 0:
+            line["sweep_latency_L32"] = sweep_latency(gfmc, inputs, stream, L, M, "fp32_mixed", args.sweeps_l32,
+                                                      warmup=0)
 
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, dt = cpu_baseline(L, M, spins, args.cpu_updates)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"first {args.cpu_updates} updates of sweep 0 at L={L}, M={M} "
-                                          f"({dt:.1f} s, single-threaded C, FP64)"}
+        ncores = os.cpu_count() or 1
+        v, dt, used = cpu_baseline(L, M, spins, args.cpu_updates_all, ncores)
+        v1, dt1, _ = cpu_baseline(L, M, spins, args.cpu_updates, 1)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": used, "kind": "oracle",
+                                "sample": f"first {args.cpu_updates_all} updates of sweep 0 at L={L}, M={M} "
+                                          f"({dt:.1f} s; plain C, FP64, OpenMP over the site and node loops "
+                                          f"on {used} of {ncores} host threads)",
+                                "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                                                  "sample": f"first {args.cpu_updates} updates of sweep 0 "
+                                                            f"({dt1:.1f} s, one thread)"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -19,9 +19,9 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgfmc.so")
 SOURCES = ["gfmc_api.cu", "gfmc_setup.cu", "gfmc_k64.cu", "gfmc_k32.cu", "gfmc_kvc.cu", "gfmc_static.cu",
-           "gfmc_server.cu"]
+           "gfmc_server.cu", "gfmc_peaks.cu"]
 HEADERS = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))] + [
-    os.path.join(ROOT, "include", "gfmc.h")]
+    os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

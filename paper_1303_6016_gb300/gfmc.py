@@ -35,7 +35,8 @@ EXPORTS = ("gfmc_default_options", "gfmc_create", "gfmc_moments", "gfmc_delta_om
            "gfmc_plan_create", "gfmc_plan_launch", "gfmc_plan_sync", "gfmc_plan_destroy",
            "gfmc_server_create",
            "gfmc_server_submit",
-           "gfmc_server_poll", "gfmc_server_last_error", "gfmc_server_destroy")
+           "gfmc_server_poll", "gfmc_server_last_error", "gfmc_server_destroy",
+           "gfmc_measure_fma_peak")
 
 
 class GfmcError(RuntimeError):
@@ -118,6 +119,8 @@ def load(path: str = LIB_PATH):
     L.gfmc_server_last_error.restype = ctypes.c_char_p
     L.gfmc_server_destroy.argtypes = [vp]
     L.gfmc_server_destroy.restype = None
+    L.gfmc_measure_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, d, vp]
+    L.gfmc_measure_fma_peak.restype = ctypes.c_int
     for name in ("gfmc_create", "gfmc_moments", "gfmc_delta_omega", "gfmc_updates", "gfmc_sweep",
                  "gfmc_get_spins", "gfmc_set_state", "gfmc_get_counter", "gfmc_set_wait_budget",
                  "gfmc_inject_stall"):
@@ -265,6 +268,16 @@ class Chain:
         c = ctypes.c_uint64(0)
         self._check(self._lib.gfmc_get_counter(self._h, ctypes.byref(c)))
         return int(c.value)
+
+
+def fma_peak_tflops(precision: str = "fp64", repeats: int = 3, stream=None) -> float:
+    """Fused multiply-add throughput of the current GPU (gfmc_measure_fma_peak)."""
+    lib = load()
+    out = np.zeros(1)
+    st = lib.gfmc_measure_fma_peak(PRECISIONS[precision], int(repeats), _dp(out), stream)
+    if st != GFMC_OK:
+        raise GfmcError(st, "gfmc_measure_fma_peak failed")
+    return float(out[0])
 
 
 def run_clusters(chains, n_updates, cluster_ctas, trace=True, stream=None) -> list:
