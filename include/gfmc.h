@@ -357,10 +357,14 @@ gfmc_status gfmc_inject_stall(gfmc_t h, int enable);
  *   err_msg   optional host buffer of err_len bytes for a message on failure.
  * The first call on a device looks up the device address of the scratch
  * array (with that device current); make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents
- * (the call clears what must start at zero), so calls that overlap on the GPU
- * -- from two threads, or on two streams -- race and must be serialised by
- * the caller. */
+ * capture.  That first call may also be the one that loads the library's
+ * device code on the device, which is when the array comes into being: make
+ * it at set-up time; from the second call on nothing is allocated.  Calls
+ * after cudaDeviceReset on that device are not supported (the address found
+ * by the first call belongs to the reset context).  All calls share the array
+ * and it keeps the last call's contents (the call clears what must start at
+ * zero), so calls that overlap on the GPU -- from two threads, or on two
+ * streams -- race and must be serialised by the caller. */
 gfmc_status gfmc_delta_omega_noalloc(int L, const double* d_spins, double t, double mu, double beta, int M,
                                      int kernel, double lorentz_lambda, double spectral_scale, int64_t site,
                                      double theta_new, double phi_new, double* d_omega, void* stream,

@@ -9,8 +9,12 @@
 // the process exits).
 //
 // The computation is the FP64 engine of gfmc_engine.cuh in its Delta Omega
-// mode, launched exactly as gfmc_delta_omega launches it, with its scratch
-// carved out of that array instead of cudaMalloc'd memory.
+// mode, with its scratch carved out of that array instead of cudaMalloc'd
+// memory.  It differs from a handle's gfmc_delta_omega launch in the plan
+// only: it runs on the fewest CTAs that hold the lattice (ceil(N / 256)),
+// one site per thread in index order, without the prefetch plan, on the
+// K = M nodes of the paper's FFT; so its sums run in another order and the
+// result agrees with gfmc_delta_omega to rounding, not bit for bit.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -34,7 +38,9 @@ __device__ __align__(256) unsigned char g_gfmc_static_scratch[kStaticScratchByte
 
 // Device address of the array on each device, found once per device (with
 // that device current) by cudaGetSymbolAddress; the host-side name of the
-// array is only a stand-in and must never be passed to a kernel.
+// array is only a stand-in and must never be passed to a kernel.  The address
+// belongs to the device's primary context: after cudaDeviceReset it would be
+// stale, and calls on that device are not supported any more.
 void* g_scratch_addr[kMaxDevices];
 bool g_scratch_ready[kMaxDevices];
 std::mutex g_scratch_mutex;

@@ -4,15 +4,19 @@ Some callers cannot allocate device memory while they run -- a plugin's
 enqueue step inside a framework that owns the device memory pool, code under a
 fixed memory budget, code that must not let cudaMalloc synchronise the device.
 They own their input and output buffers and call this entry point, whose
-scratch is a fixed device array inside the library.  This test calls it
-through the C ABI twice in a row and checks each result against the handle
-based gfmc_delta_omega within the Delta Omega tolerance of the parity tests.
-It lives in its own file so that pytest collects it last.
+scratch is a fixed device array inside the library.  These tests call it
+through the C ABI: twice in a row against the handle based gfmc_delta_omega,
+against the oracle (at the largest accepted size and with the Lorentz kernel),
+and with the device's free memory read around a call that is not the first,
+all within the Delta Omega tolerance of the parity tests.  They live in their
+own file so that pytest collects them last.
 """
 import ctypes
 
+import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_1303_6016_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -62,3 +66,45 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(lib):
                                       d_out.data_ptr(), None, msg, len(msg))
     assert st == 1  # GFMC_EINVAL
     assert "needs" in msg.value.decode() and "static scratch holds" in msg.value.decode()
+
+
+def _call(lib, L, d_spins, M, o, th, ph, d_out, kernel=0, lam=0.0):
+    msg = ctypes.create_string_buffer(256)
+    st = lib.gfmc_delta_omega_noalloc(L, d_spins.data_ptr(), 1.0, -2.0, 20.0, M, kernel, lam, 0.0, o, th, ph,
+                                      d_out.data_ptr(), None, msg, len(msg))
+    assert st == 0, msg.value.decode()
+    return float(d_out.item())
+
+
+@pytest.mark.parametrize("L,M,kernel", [(8, 256, 0), (12, 1024, 0), (6, 128, 1)])
+def test_noalloc_matches_the_oracle(lib, L, M, kernel):
+    """Against the oracle directly, at the largest accepted size (L = 12 with
+    M = 1024 fills most of the scratch) and with the Lorentz kernel."""
+    torch = pytest.importorskip("torch")
+    sp = inputs.uniform_sphere(L, 7)
+    d_spins = torch.tensor(sp, dtype=torch.float64, device="cuda")
+    d_out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    rng = np.random.default_rng(3)
+    for o in (0, L ** 3 // 2 + 1):
+        th, ph = float(np.arccos(1 - 2 * rng.random())), float(2 * np.pi * rng.random())
+        got = _call(lib, L, d_spins, M, o, th, ph, d_out, kernel=kernel, lam=4.0 if kernel else 0.0)
+        ref = O.delta_omega(L, sp, o, th, ph, M, beta=20.0, chem=-2.0, kernel_kind=kernel, lam=4.0)
+        assert abs(got - ref) <= tol(ref), (L, M, o, got, ref)
+
+
+def test_noalloc_second_call_allocates_nothing(lib):
+    """Free device memory is the same before and after a call that is not the
+    first one on the device."""
+    torch = pytest.importorskip("torch")
+    L, M = 12, 1024
+    sp = inputs.uniform_sphere(L, 8)
+    d_spins = torch.tensor(sp, dtype=torch.float64, device="cuda")
+    d_out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    first = _call(lib, L, d_spins, M, 100, 1.0, 1.0, d_out)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    second = _call(lib, L, d_spins, M, 100, 1.0, 1.0, d_out)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert second == first
