@@ -263,16 +263,16 @@ def sweep_latency(gfmc, inputs, stream, L, M, precision, sweeps, warmup=2):
             "p99_ms": p99}
 
 
-def run_batching(stream, steps, warmup, updates, flush, recursion="unit_vectors", graphs=True):
+def run_batching(stream, steps, warmup, updates, flush, recursion="unit_vectors", graphs=True, compensated=False):
     """64 independent FP32-mixed chains, L from {8,12,16,24,32}, T ~ U[0.02, 0.2],
     M = 1024, in team-engine launches planned by the autotuner; a step runs
-    `updates` updates of every chain."""
+    `updates` updates of every chain (`compensated`: Dot2 Gram sums)."""
     import torch
     from paper_1303_6016_gb300 import batch
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    chains, Ls, Ts = batch.c4_chains(M=1024, recursion=recursion)
-    tuner = batch.Autotuner(M=1024, precision="fp32_mixed", recursion=recursion)
+    chains, Ls, Ts = batch.c4_chains(M=1024, recursion=recursion, compensated=compensated)
+    tuner = batch.Autotuner(M=1024, precision="fp32_mixed", recursion=recursion, compensated=compensated)
     runner = batch.BatchRunner(chains, tuner)
     plan = runner.plan([updates] * len(chains))
     tune_s = time.perf_counter() - t0
@@ -326,7 +326,7 @@ def run_batching(stream, steps, warmup, updates, flush, recursion="unit_vectors"
                                and tc[k + 1] == 0),
             "lattice_counts": {str(int(L)): int((Ls == L).sum()) for L in sorted(set(Ls.tolist()))},
             "stencil_gbs": sum(bytes_u) * updates / (total / steps / 1000.0) / 1e9,
-            "autotune_s": tune_s, "recursion": recursion,
+            "autotune_s": tune_s, "recursion": recursion, "compensated": compensated,
             "config": "64 chains, L uniform from {8,12,16,24,32} (seed 4), T uniform in [0.02, 0.2] t, "
                       "mu = -2t, M = 1024, FP32-mixed, spins uniform (seed = chain index)"}
 
@@ -646,6 +646,13 @@ def main():
                                                                args.batch_updates, flush, "proposal", graphs)
             line["batching_clusters"] = run_batching_clusters(stream, max(3, args.steps // 2), 3,
                                                               args.batch_updates, flush, graphs)
+            comp = run_batching(stream, max(3, args.steps // 2), 3, args.batch_updates, flush,
+                                graphs=graphs, compensated=True)
+            line["batching_compensated"] = {k: comp[k] for k in ("value", "unit", "ms_per_step", "graph",
+                                                                 "launches_per_step", "compensated")}
+            line["batching_compensated"]["note"] = ("the batching workload with Dot2 compensated Gram sums "
+                                                    "(gfmc_options.compensated); the cost of the extra "
+                                                    "accuracy against batching.value")
 
     if not args.no_mixed:
         # FP32-mixed against the FP64 path on the same chain: Delta Omega error per
@@ -653,7 +660,12 @@ def main():
         from paper_1303_6016_gb300 import precision_report
         prec = precision_report.run(L=L, Ms=(M,), n_sites=4)
         line["fp32_mixed"]["error_vs_fp64"] = [
-            {k: r[k] for k in ("spins", "M", "domega_err_max", "domega_rel_err_max", "moment_err_by_n")} for r in prec]
+            {"spins": r["spins"], "M": r["M"],
+             **{name: {k: v[k] for k in ("domega_err_max", "domega_rel_err_max", "moment_err_by_n")}
+                for name, v in r["variants"].items()}} for r in prec]
+        line["fp32_mixed"]["error_vs_fp64_note"] = (
+            "default: the vector-cluster engine (moments read off the recursion); grid_plain: the doubling's "
+            "Gram products in FP32 warp sums; grid_compensated: the same with Dot2 products and sums")
 
     if not args.no_serving:
         from paper_1303_6016_gb300 import serving

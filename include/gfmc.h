@@ -108,11 +108,20 @@ typedef struct {
      * Any other value is GFMC_EINVAL. */
     int nodes;
     int engine; /* GFMC_ENGINE_* */
+    /* FP32-mixed chains only (0 otherwise): 1 forms the Gram dot products of
+     * the doubling (Eq. mu2) in compensated FP32 -- every product split
+     * exactly by a fused multiply-add, every sum by TwoSum, the error terms
+     * carried as (hi, lo) pairs through the warp sums (Dot2 of Ogita, Rump and
+     * Oishi, SIAM J. Sci. Comput. 26, 2005) -- and adds the pairs in FP64
+     * above the warp; 0 (default) sums in plain FP32 within a warp.  The
+     * VECTOR_CLUSTERS engine forms no dot products; gfmc_server_submit
+     * refuses compensated chains; a batch or plan takes chains of one kind. */
+    int compensated;
 } gfmc_options;
 
 /* Fill *opt with the defaults (FP64, Jackson, a = 6.05|t|, seed 1, chain 0,
  * default stream, automatic CTA count, unit-vector recursion, K = M nodes,
- * automatic engine). */
+ * automatic engine, plain FP32 sums). */
 void gfmc_default_options(gfmc_options* opt);
 
 /* Create a chain (Sec. 2.1: the spin configuration and H({S}); Sec. 3.3.2:

@@ -44,8 +44,9 @@ class Autotuner:
     """Per-lattice-size update times of the team engine at candidate team sizes."""
 
     def __init__(self, M: int, precision: str = "fp32_mixed", candidates=CANDIDATES, probe_updates: int = 2,
-                 beta: float = 20.0, mu: float = -2.0, recursion: str = "unit_vectors"):
+                 beta: float = 20.0, mu: float = -2.0, recursion: str = "unit_vectors", compensated: bool = False):
         self.M, self.precision, self.recursion = M, precision, recursion
+        self.compensated = compensated
         self.candidates = tuple(candidates)
         self.probe_updates = probe_updates
         self.beta, self.mu = beta, mu
@@ -58,7 +59,7 @@ class Autotuner:
         sp = inputs.uniform_sphere(L, 0)
         res = {}
         with gfmc.Chain(L, sp, M=self.M, precision=self.precision, beta=self.beta, mu=self.mu,
-                        recursion=self.recursion) as ch:
+                        recursion=self.recursion, compensated=self.compensated) as ch:
             for tc in self.candidates:
                 if tc > min(L ** 3, 1024) or tc > device_ctas():
                     continue
@@ -202,7 +203,7 @@ class BatchRunner:
         t = self.tuner
         probes = [gfmc.Chain(self.chains[i].L, inputs.uniform_sphere(self.chains[i].L, 0), M=t.M,
                              precision=t.precision, beta=t.beta, mu=t.mu, recursion=self.chains[i].recursion,
-                             chain_id=k) for k, i in enumerate(w)]
+                             compensated=self.chains[i].compensated, chain_id=k) for k, i in enumerate(w)]
         best = None
         try:
             for order, tc in cands:
@@ -408,13 +409,15 @@ class ClusterRunner:
 
 def c4_chains(n_chains: int = 64, M: int = 1024, precision: str = "fp32_mixed", seed: int = 4,
               sizes=(8, 12, 16, 24, 32), tmin: float = 0.02, tmax: float = 0.2, mu: float = -2.0,
-              recursion: str = "unit_vectors"):
+              recursion: str = "unit_vectors", compensated: bool = False):
     """The batching workload: n_chains independent chains with L drawn from
     `sizes` and temperatures uniform in [tmin, tmax] (seeded), spins uniform on
-    the sphere (seed = chain index), M moments, FP32-mixed by default."""
+    the sphere (seed = chain index), M moments, FP32-mixed by default
+    (`compensated`: Dot2 sums of the Gram products)."""
     rng = np.random.default_rng(seed)
     Ls = rng.choice(sizes, size=n_chains)
     Ts = rng.uniform(tmin, tmax, size=n_chains)
     chains = [gfmc.Chain(int(L), inputs.uniform_sphere(int(L), c), M=M, precision=precision, beta=1.0 / T,
-                         mu=mu, seed=1, chain_id=c, recursion=recursion) for c, (L, T) in enumerate(zip(Ls, Ts))]
+                         mu=mu, seed=1, chain_id=c, recursion=recursion, compensated=compensated)
+              for c, (L, T) in enumerate(zip(Ls, Ts))]
     return chains, Ls, Ts

@@ -219,7 +219,7 @@ gfmc_status run_engine(gfmc_ctx* h, Params& P)
             return cuda_fail(h, e, "uploading the job");
         const int smem = gfmc::engine_smem_bytes(P.K);
         e = h->precision == GFMC_PREC_FP64 ? gfmc::launch_team_f64(h->d_job, 1, P.ncta, 0, smem, h->stream)
-                                            : gfmc::launch_team_f32(h->d_job, 1, P.ncta, 0, smem, h->stream);
+                                            : gfmc::launch_team_f32(h->d_job, 1, P.ncta, 0, smem, h->stream, P.comp != 0);
     } else {
         const int nv = (h->recursion == GFMC_RECURSION_PROPOSAL && P.mode != gfmc::MODE_MOMENTS) ? 2 : gfmc::kVec;
         if (h->vcl && nv == gfmc::kVec)
@@ -353,6 +353,7 @@ void gfmc_default_options(gfmc_options* opt)
     opt->recursion = GFMC_RECURSION_UNIT_VECTORS;
     opt->nodes = 0;
     opt->engine = GFMC_ENGINE_AUTO;
+    opt->compensated = 0;
 }
 
 gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double beta, int M,
@@ -385,6 +386,10 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
         return fail(nullptr, GFMC_EINVAL, "nodes = %d must be 0, M = %d or 2M = %d", opt.nodes, M, 2 * M);
     if (opt.engine != GFMC_ENGINE_AUTO && opt.engine != GFMC_ENGINE_GRID && opt.engine != GFMC_ENGINE_VECTOR_CLUSTERS)
         return fail(nullptr, GFMC_EINVAL, "unknown engine %d", opt.engine);
+    if (opt.compensated != 0 && opt.compensated != 1)
+        return fail(nullptr, GFMC_EINVAL, "compensated = %d must be 0 or 1", opt.compensated);
+    if (opt.compensated && opt.precision != GFMC_PREC_FP32_MIXED)
+        return fail(nullptr, GFMC_EINVAL, "compensated dot products apply to FP32-mixed chains");
     if (opt.engine == GFMC_ENGINE_VECTOR_CLUSTERS && (opt.precision != GFMC_PREC_FP32_MIXED || L != gfmc::kVcLattice))
         return fail(nullptr, GFMC_EINVAL, "the vector-cluster engine runs FP32-mixed chains with L = %d",
                     gfmc::kVcLattice);
@@ -476,6 +481,7 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
     P.divL = (unsigned)(((1ull << 32) + (unsigned long long)L - 1) / (unsigned long long)L);
     P.divLL = (unsigned)(((1ull << 32) + (unsigned long long)L * L - 1) / ((unsigned long long)L * L));
     P.nv = gfmc::kVec;
+    P.comp = opt.compensated;
     P.t = t;
     P.chem = mu;
     P.beta = beta;
@@ -724,6 +730,8 @@ gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_update
         for (int d = 0; d < c; ++d)
             if (chains[d] == h) return fail(nullptr, GFMC_EINVAL, "chain %d appears twice", c);
         if (h->precision != prec) return fail(nullptr, GFMC_EINVAL, "chain %d has another precision", c);
+        if (h->P.comp != chains[0]->P.comp)
+            return fail(nullptr, GFMC_EINVAL, "chain %d sums its dot products otherwise than chain 0", c);
         if (h->device != dev) return fail(nullptr, GFMC_EINVAL, "chain %d lives on another device", c);
         if (n_updates[c] < 0) return fail(nullptr, GFMC_EINVAL, "n_updates[%d] < 0", c);
         gfmc_status st = check_team_size(chains, team_ctas, c);
@@ -812,7 +820,8 @@ gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_update
         cudaSuccess)
         return cuda_fail(nullptr, e, "uploading the job table");
     e = prec == GFMC_PREC_FP64 ? gfmc::launch_team_f64(d_jobs, n_chains, grid, (int)vec_bytes, smem, s)
-                               : gfmc::launch_team_f32(d_jobs, n_chains, grid, (int)vec_bytes, smem, s);
+                               : gfmc::launch_team_f32(d_jobs, n_chains, grid, (int)vec_bytes, smem, s,
+                                                       chains[0]->P.comp != 0);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "launching the batch");
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(nullptr, e, "batch execution");
     gfmc_status result = GFMC_OK;
@@ -947,11 +956,13 @@ gfmc_status gfmc_run_clusters(gfmc_t* chains, int n_chains, const int64_t* n_upd
         if (!cluster_fits(h->L, h->K, C, h->precision, dev_smem, st_smem))
             return fail(nullptr, GFMC_EINVAL, "chain %d: %zu B of lattice per CTA (and %d B of the engine's own) exceed "
                         "the %d B of shared memory; use a larger cluster", c, vb, st_smem, dev_smem);
+        // launch key: the precision, and the compensated sums in bit 4
+        const int key = h->precision | (h->P.comp << 4);
         Group* g = nullptr;
         for (auto& x : groups)
-            if (x.prec == h->precision && x.C == C) g = &x;
+            if (x.prec == key && x.C == C) g = &x;
         if (!g) {
-            groups.push_back({h->precision, C, 0, 0, {}});
+            groups.push_back({key, C, 0, 0, {}});
             g = &groups.back();
         }
         g->vec_bytes = std::max(g->vec_bytes, vb);
@@ -988,7 +999,7 @@ gfmc_status gfmc_run_clusters(gfmc_t* chains, int n_chains, const int64_t* n_upd
     for (const auto& g : groups) {
         int active = 0;
         const int smem = (int)g.vec_bytes + g.work;
-        if ((e = gfmc::cluster_max_active(g.prec, g.C, smem, &active)) != cudaSuccess)
+        if ((e = gfmc::cluster_max_active(g.prec & 15, g.C, smem, &active)) != cudaSuccess)
             return cuda_fail(nullptr, e, "cluster occupancy");
         if (active < 1)
             return fail(nullptr, GFMC_EINVAL, "a cluster of %d CTAs with %d B of shared memory each cannot be scheduled",
@@ -1033,9 +1044,10 @@ gfmc_status gfmc_run_clusters(gfmc_t* chains, int n_chains, const int64_t* n_upd
         if ((e = cudaStreamCreateWithFlags(&gs[k], cudaStreamNonBlocking)) != cudaSuccess ||
             (e = cudaStreamWaitEvent(gs[k], ev[0], 0)) != cudaSuccess)
             return cuda_fail(nullptr, e, "ordering the cluster launches");
-        e = g.prec == GFMC_PREC_FP64
+        e = (g.prec & 15) == GFMC_PREC_FP64
                 ? gfmc::launch_cluster_f64(d_jobs + goff[k], (int)g.members.size(), g.C, (int)g.vec_bytes, smem, gs[k])
-                : gfmc::launch_cluster_f32(d_jobs + goff[k], (int)g.members.size(), g.C, (int)g.vec_bytes, smem, gs[k]);
+                : gfmc::launch_cluster_f32(d_jobs + goff[k], (int)g.members.size(), g.C, (int)g.vec_bytes, smem, gs[k],
+                                           (g.prec >> 4) != 0);
         if (e != cudaSuccess) return cuda_fail(nullptr, e, "launching clusters");
         if ((e = cudaEventCreateWithFlags(&ev[k + 1], cudaEventDisableTiming)) != cudaSuccess ||
             (e = cudaEventRecord(ev[k + 1], gs[k])) != cudaSuccess || (e = cudaStreamWaitEvent(s, ev[k + 1], 0)) != cudaSuccess)
@@ -1171,6 +1183,8 @@ gfmc_status gfmc_plan_create(gfmc_t* chains, int n_chains, const int64_t* n_upda
                 return fail(nullptr, GFMC_EINVAL, "chain %d: %d z-planes do not split over %d CTAs", c, h->L, C);
         } else {
             if (h->precision != prec) return fail(nullptr, GFMC_EINVAL, "chain %d has another precision", c);
+            if (h->P.comp != chains[0]->P.comp)
+                return fail(nullptr, GFMC_EINVAL, "chain %d sums its dot products otherwise than chain 0", c);
             gfmc_status st = check_team_size(chains, ctas, c);
             if (st != GFMC_OK) return st;
         }
@@ -1221,7 +1235,7 @@ gfmc_status gfmc_plan_create(gfmc_t* chains, int n_chains, const int64_t* n_upda
             return bail(cuda_fail(nullptr, e, "querying shared memory"));
         std::vector<std::pair<int, int>> keys;  // (precision, C) in order of first appearance
         for (int c = 0; c < n_chains; ++c) {
-            const std::pair<int, int> k(chains[c]->precision, ctas[c]);
+            const std::pair<int, int> k(chains[c]->precision | (chains[c]->P.comp << 4), ctas[c]);
             if (std::find(keys.begin(), keys.end(), k) == keys.end()) keys.push_back(k);
         }
         // groups launch in the order of their first chain in `chains` (the caller's priority)
@@ -1229,7 +1243,7 @@ gfmc_status gfmc_plan_create(gfmc_t* chains, int n_chains, const int64_t* n_upda
             Group g{k.first, k.second, (int)jobs.size(), 0, 0};
             for (int c = 0; c < n_chains; ++c) {
                 gfmc_ctx* h = chains[c];
-                if (h->precision != k.first || ctas[c] != k.second) continue;
+                if ((h->precision | (h->P.comp << 4)) != k.first || ctas[c] != k.second) continue;
                 const int C = ctas[c], T = h->N / C;
                 if ((unsigned long long)h->N * (unsigned long long)T >= (1ull << 32))
                     return bail(fail(nullptr, GFMC_EINVAL, "chain %d: %d sites per CTA are too many", c, T));
@@ -1254,7 +1268,7 @@ gfmc_status gfmc_plan_create(gfmc_t* chains, int n_chains, const int64_t* n_upda
                 ++g.count;
             }
             int active = 0;
-            if ((e = gfmc::cluster_max_active(g.prec, g.C, (int)g.vec_bytes, &active)) != cudaSuccess)
+            if ((e = gfmc::cluster_max_active(g.prec & 15, g.C, (int)g.vec_bytes, &active)) != cudaSuccess)
                 return bail(cuda_fail(nullptr, e, "cluster occupancy"));
             if (active < 1)
                 return bail(fail(nullptr, GFMC_EINVAL, "a cluster of %d CTAs with %zu B each cannot be scheduled", g.C,
@@ -1346,7 +1360,8 @@ gfmc_status gfmc_plan_create(gfmc_t* chains, int n_chains, const int64_t* n_upda
     ce = cudaGetLastError();
     if (ce == cudaSuccess && !clusters) {
         ce = prec == GFMC_PREC_FP64 ? gfmc::launch_team_ex_f64(p->d_jobs, nj, team_grid, team_vec, team_smem, cs)
-                                    : gfmc::launch_team_ex_f32(p->d_jobs, nj, team_grid, team_vec, team_smem, cs);
+                                    : gfmc::launch_team_ex_f32(p->d_jobs, nj, team_grid, team_vec, team_smem, cs,
+                                                               chains[0]->P.comp != 0);
     } else if (ce == cudaSuccess) {
         cudaEvent_t fork = nullptr;
         ce = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
@@ -1361,9 +1376,10 @@ gfmc_status gfmc_plan_create(gfmc_t* chains, int n_chains, const int64_t* n_upda
             if ((ce = cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking)) != cudaSuccess) break;
             p->streams.push_back(gs);
             if ((ce = cudaStreamWaitEvent(gs, fork, 0)) != cudaSuccess) break;
-            ce = g.prec == GFMC_PREC_FP64
+            ce = (g.prec & 15) == GFMC_PREC_FP64
                      ? gfmc::launch_cluster_f64(p->d_jobs + g.first, g.count, g.C, (int)g.vec_bytes, (int)g.vec_bytes, gs)
-                     : gfmc::launch_cluster_f32(p->d_jobs + g.first, g.count, g.C, (int)g.vec_bytes, (int)g.vec_bytes, gs);
+                     : gfmc::launch_cluster_f32(p->d_jobs + g.first, g.count, g.C, (int)g.vec_bytes, (int)g.vec_bytes, gs,
+                                                (g.prec >> 4) != 0);
             if (ce != cudaSuccess) break;
             if ((ce = cudaEventCreateWithFlags(&join, cudaEventDisableTiming)) != cudaSuccess) break;
             p->events.push_back(join);
@@ -1582,6 +1598,8 @@ gfmc_status gfmc_server_submit(gfmc_server_t s, int slot, gfmc_t h, int64_t n_up
     if (h->in_server) return sfail(s, GFMC_EINVAL, "the chain already has a job in a server");
     if (h->in_plan) return sfail(s, GFMC_EINVAL, "the chain belongs to a batch plan");
     if (h->device != s->device) return sfail(s, GFMC_EINVAL, "the chain lives on another device");
+    if (h->P.comp)
+        return sfail(s, GFMC_EINVAL, "the serving loop forms plain FP32 dot products; the chain asks for compensated ones");
     if (h->K > s->maxM)
         return sfail(s, GFMC_EINVAL, "chain with M = %d on %d nodes above the server's %d", h->M, h->K, s->maxM);
     if (n_updates < 1) return sfail(s, GFMC_EINVAL, "n_updates = %lld < 1", (long long)n_updates);

@@ -33,6 +33,8 @@
 // records GFMC_ETIMEOUT in p.err and all CTAs leave at their next wait.
 #pragma once
 
+#include <type_traits>
+
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math_constants.h>
@@ -353,6 +355,76 @@ template <class R> __device__ __forceinline__ R warp_reduce_scatter8(R (&v)[8], 
     return v[0];
 }
 
+// ---------------------------------------------------------------------------
+// compensated FP32 sums (Dot2 of Ogita, Rump and Oishi, "Accurate sum and dot
+// product", SIAM J. Sci. Comput. 26 (2005)): a product is split exactly into
+// p + e with p = fl(a b) and e = fma(a, b, -p) (TwoProduct), a sum exactly
+// into s + t with Knuth's TwoSum; the pair (hi, lo) carries the rounding
+// errors, so a dot product comes out as if formed in twice the working
+// precision.  The round-to-nearest intrinsics keep the compiler from
+// contracting or reassociating the error terms.
+// ---------------------------------------------------------------------------
+struct F32c {
+    float hi, lo;
+};
+__device__ __forceinline__ F32c two_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ F32c c_add(F32c x, F32c y)
+{
+    const float s = __fadd_rn(x.hi, y.hi);
+    const float bb = __fsub_rn(s, x.hi);
+    const float t = __fadd_rn(__fsub_rn(x.hi, __fsub_rn(s, bb)), __fsub_rn(y.hi, bb));
+    return {s, __fadd_rn(__fadd_rn(t, x.lo), y.lo)};
+}
+// re = a.x b.x + a.y b.y, im = a.x b.y - a.y b.x (conj(a) b) as compensated pairs
+__device__ __forceinline__ F32c c_dot_re(float2 a, float2 b) { return c_add(two_prod(a.x, b.x), two_prod(a.y, b.y)); }
+__device__ __forceinline__ F32c c_dot_im(float2 a, float2 b) { return c_add(two_prod(a.x, b.y), two_prod(-a.y, b.x)); }
+__device__ __forceinline__ double c_val(F32c x) { return (double)x.hi + (double)x.lo; }  // exact in FP64
+// a warp sum kept in shared memory as a float, a double, or a compensated (hi, lo) pair
+__device__ __forceinline__ double to_d(float x) { return (double)x; }
+__device__ __forceinline__ double to_d(double x) { return x; }
+__device__ __forceinline__ double to_d(float2 x) { return (double)x.x + (double)x.y; }
+
+__device__ __forceinline__ F32c c_shfl_xor(F32c v, int m)
+{
+    return {__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
+}
+
+// warp_reduce_scatter32 / 8 with compensated pairs
+__device__ __forceinline__ F32c warp_reduce_scatter32c(F32c (&v)[32], int lane)
+{
+#pragma unroll
+    for (int w = 16, n = 16; w >= 1; w >>= 1, n >>= 1) {
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            const bool up = lane & w;
+            const F32c send = up ? v[i] : v[i + n];
+            const F32c keep = up ? v[i + n] : v[i];
+            v[i] = c_add(keep, c_shfl_xor(send, w));
+        }
+    }
+    return v[0];
+}
+__device__ __forceinline__ F32c warp_reduce_scatter8c(F32c (&v)[8], int lane)
+{
+#pragma unroll
+    for (int w = 16, n = 4; w >= 4; w >>= 1, n >>= 1) {
+#pragma unroll
+        for (int i = 0; i < n; ++i) {
+            const bool up = lane & w;
+            const F32c send = up ? v[i] : v[i + n];
+            const F32c keep = up ? v[i + n] : v[i];
+            v[i] = c_add(keep, c_shfl_xor(send, w));
+        }
+    }
+    v[0] = c_add(v[0], c_shfl_xor(v[0], 2));
+    v[0] = c_add(v[0], c_shfl_xor(v[0], 1));
+    return v[0];
+}
+
 // Deterministic CTA-wide sum (and max) of one double per thread.
 template <int NT = kThreads>
 __device__ __forceinline__ void block_sum_max(double s, double mx, double* out_s, double* out_m)
@@ -583,6 +655,62 @@ __device__ __forceinline__ void gram_chunk_accumulate2(const R2 (&ca)[kVec], con
 }
 
 
+// gram_fill with compensated products
+template <int C, int Q>
+__device__ __forceinline__ void gram_fill_c(const float2 (&rc)[kVec], const float2 (&rn)[kVec], F32c (&vals)[32])
+{
+    constexpr int e = 14 * C + Q;
+    constexpr int g = e / kPairs, pp = e % kPairs;
+    constexpr int j = pair_j(pp), k = pair_k(pp);
+    const float2 x = rc[j];
+    const float2 y = (g == 0) ? rc[k] : rn[k];
+    vals[2 * Q] = c_dot_re(x, y);
+    vals[2 * Q + 1] = (g == 0 && j == k) ? F32c{0.f, 0.f} : c_dot_im(x, y);
+    if constexpr (Q + 1 < 14) gram_fill_c<C, Q + 1>(rc, rn, vals);
+}
+
+// gram_chunk_accumulate with compensated products and warp sums
+template <int C>
+__device__ __forceinline__ void gram_chunk_accumulate_c(const float2 (&rc)[kVec], const float2 (&rn)[kVec], int lane,
+                                                        double* dst)
+{
+    F32c vals[32];
+    gram_fill_c<C, 0>(rc, rn, vals);
+#pragma unroll
+    for (int qq = 28; qq < 32; ++qq) vals[qq] = F32c{0.f, 0.f};
+    const F32c s = warp_reduce_scatter32c(vals, lane);
+    if (lane < 28) dst[28 * C + lane] += c_val(s);
+}
+
+// gram_chunk_reduce_raw with compensated products and warp sums, (hi, lo) left
+// in dst[28 C + lane]
+template <int C>
+__device__ __forceinline__ void gram_chunk_reduce_c(const float2 (&rc)[kVec], const float2 (&rn)[kVec], int lane,
+                                                    float2* dst)
+{
+    F32c vals[32];
+    gram_fill_c<C, 0>(rc, rn, vals);
+#pragma unroll
+    for (int qq = 28; qq < 32; ++qq) vals[qq] = F32c{0.f, 0.f};
+    const F32c s = warp_reduce_scatter32c(vals, lane);
+    if (lane < 28) dst[28 * C + lane] = make_float2(s.hi, s.lo);
+}
+
+// The 8 products of the proposal-vector recursion at one site (a = r_m^o,
+// b = r_m^v; na, nb at m+1), added to compensated accumulators:
+// |a|^2, |b|^2, Re a*b, Im a*b, Re a*na, Re b*nb, Re a*nb, Im a*nb.
+__device__ __forceinline__ void gram8_c(F32c (&acc)[8], float2 a, float2 b, float2 na, float2 nb)
+{
+    acc[0] = c_add(acc[0], c_dot_re(a, a));
+    acc[1] = c_add(acc[1], c_dot_re(b, b));
+    acc[2] = c_add(acc[2], c_dot_re(a, b));
+    acc[3] = c_add(acc[3], c_dot_im(a, b));
+    acc[4] = c_add(acc[4], c_dot_re(a, na));
+    acc[5] = c_add(acc[5], c_dot_re(b, nb));
+    acc[6] = c_add(acc[6], c_dot_re(a, nb));
+    acc[7] = c_add(acc[7], c_dot_im(a, nb));
+}
+
 // FP64 Gram sums of one CTA from shared memory in kGramUnits = 49 work units
 // of four fused multiply-adds per site: units 0..20 are the off-diagonal pairs
 // j < k of <r_m|r_m>, 21..41 those of <r_m|r_{m+1}>, 42..48 the diagonal j = k
@@ -737,7 +865,7 @@ __device__ __forceinline__ void site_nbrs(int i, int L, unsigned mL, unsigned mL
 // Phase 0 and the stencil steps of one update for a team CTA whose tile may
 // hold any number of sites: every vector value lives in memory (vm), the
 // thread walks its sites s0 + tid, s0 + tid + kThreads, ...
-template <class R, class V, bool WIDE = true>
+template <class R, class V, bool WIDE = true, bool COMP = false>
 __device__ bool team_steps(const Params& p, int cta, unsigned phase, typename Cx<R>::T* buf0,
                            typename Cx<R>::T* buf1, const int* s_loc, double (*red)[kEntries], double2* dyn,
                            V vm)
@@ -810,7 +938,17 @@ __device__ bool team_steps(const Params& p, int cta, unsigned phase, typename Cx
                     }
                 }
             };
-            if constexpr (WIDE) {
+            if constexpr (COMP) {
+                // compensated FP32 products and warp sums (Dot2), one site per thread per pass
+                for (int c = 0; c < nch; ++c) {
+                    R2 ca[kVec], na[kVec];
+                    site(s0 + c * kThreads + tid, ca, na);
+                    gram_chunk_accumulate_c<0>(ca, na, lane, red[warp]);
+                    gram_chunk_accumulate_c<1>(ca, na, lane, red[warp]);
+                    gram_chunk_accumulate_c<2>(ca, na, lane, red[warp]);
+                    gram_chunk_accumulate_c<3>(ca, na, lane, red[warp]);
+                }
+            } else if constexpr (WIDE) {
                 for (int c = 0; c < nch; c += 2) {
                     R2 ca[kVec], na[kVec], cb[kVec], nb2[kVec];
                     site(s0 + c * kThreads + tid, ca, na);
@@ -887,7 +1025,7 @@ __device__ bool team_steps(const Params& p, int cta, unsigned phase, typename Cx
 
 // Phase 0 and the steps of one update of a team CTA for the recursion on the
 // proposal's vectors o and v (any number of sites per thread, vectors in vm).
-template <class R, class V, bool WIDE = true>
+template <class R, class V, bool WIDE = true, bool COMP = false>
 __device__ bool team_steps2(const Params& p, int cta, unsigned phase, typename Cx<R>::T* buf0,
                             typename Cx<R>::T* buf1, const int* s_loc, const double2* s_c,
                             double (*red)[kEntries], V vm)
@@ -946,6 +1084,11 @@ __device__ bool team_steps2(const Params& p, int cta, unsigned phase, typename C
         R acc[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) acc[e] = (R)0;
+        [[maybe_unused]] F32c cacc[8];
+        if constexpr (COMP) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) cacc[e] = F32c{0.f, 0.f};
+        }
         // one site's operands: its bonds, the neighbours' r_m of o and v, its r_m and r_{m-1}
         struct Ops {
             R2 h[6], nv[2][6], cur[2], pv[2];
@@ -972,6 +1115,10 @@ __device__ bool team_steps2(const Params& p, int cta, unsigned phase, typename C
                 if (m < p.nsteps) vm.st(wr + (size_t)v * N + i, nxt[v]);
             }
             const R2 a = q.cur[0], b = q.cur[1], na = nxt[0], nbv = nxt[1];
+            if constexpr (COMP) {
+                gram8_c(cacc, a, b, na, nbv);
+                return;
+            }
             acc[0] = fma(a.x, a.x, fma(a.y, a.y, acc[0]));
             acc[1] = fma(b.x, b.x, fma(b.y, b.y, acc[1]));
             acc[2] = fma(a.x, b.x, fma(a.y, b.y, acc[2]));
@@ -981,7 +1128,7 @@ __device__ bool team_steps2(const Params& p, int cta, unsigned phase, typename C
             acc[6] = fma(a.x, nbv.x, fma(a.y, nbv.y, acc[6]));
             acc[7] = fma(a.x, nbv.y, fma(-a.y, nbv.x, acc[7]));
         };
-        if constexpr (WIDE && sizeof(R) == 4) {
+        if constexpr (WIDE && sizeof(R) == 4 && !COMP) {
             // two sites per pass, both sites' loads issued before the first use
             // (the sites are still summed in the order i, i + kThreads, ...)
             for (int i = s0 + tid; i < s1; i += 2 * kThreads) {
@@ -1000,8 +1147,13 @@ __device__ bool team_steps2(const Params& p, int cta, unsigned phase, typename C
             }
         }
         publish(p, cta, phase + (unsigned)m + 1u);
-        const R s8 = warp_reduce_scatter8(acc, lane);
-        if ((lane & 3) == 0) red[warp][lane >> 2] = (double)s8;
+        if constexpr (COMP) {
+            const F32c s8 = warp_reduce_scatter8c(cacc, lane);
+            if ((lane & 3) == 0) red[warp][lane >> 2] = c_val(s8);
+        } else {
+            const R s8 = warp_reduce_scatter8(acc, lane);
+            if ((lane & 3) == 0) red[warp][lane >> 2] = (double)s8;
+        }
         __syncthreads();
         if (tid < 8) {
             double sum = 0.0;
@@ -1166,6 +1318,16 @@ template <> struct GramAcc<double> {
     }
 };
 
+// GramAcc<float> with compensated products and sums (the same 8 entries)
+struct GramAccC {
+    F32c v[8] = {};
+    __device__ __forceinline__ void add(const SOV<float>& c, const SOV<float>& n)
+    {
+        gram8_c(v, make_float2(c.re.x, c.im.x), make_float2(c.re.y, c.im.y), make_float2(n.re.x, n.im.x),
+                make_float2(n.re.y, n.im.y));
+    }
+};
+
 // Phase 0 and the steps of one update for a chain held by one thread-block
 // cluster of C CTAs: the recursion on the proposal's vectors o and v with
 // every vector value and forward bond of the lattice in the cluster's shared
@@ -1185,7 +1347,7 @@ template <> struct GramAcc<double> {
 // then waits.  U sites per thread have all their loads issued before any
 // arithmetic; U = 1 (the 16 warps of an FP32 CTA hide the shared-memory
 // latency, and two sites per thread spilled registers and measured slower).
-template <class R, int NT>
+template <class R, int NT, bool COMP = false>
 __device__ bool cluster_steps2(const Params& p, int rank, typename Cx<R>::T* vs, const int* s_loc,
                                const double2* s_c)
 {
@@ -1277,7 +1439,7 @@ __device__ bool cluster_steps2(const Params& p, int rank, typename Cx<R>::T* vs,
         const Q* __restrict__ rd = vq + (size_t)b * T;
         Q* __restrict__ wr = vq + (size_t)(b ^ 1) * T;
         const unsigned rd_off = (unsigned)b * (unsigned)T * (unsigned)sizeof(Q);
-        GramAcc<R> g;
+        std::conditional_t<COMP, GramAccC, GramAcc<R>> g;
         if (colmode) {
             // columns along z: a thread walks the S sites of each of its column
             // segments with a window of r_m below / at / above the site in
@@ -1380,11 +1542,18 @@ __device__ bool cluster_steps2(const Params& p, int rank, typename Cx<R>::T* vs,
             }
         }
         asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-        R acc[8];
-        g.out(acc);
-        const R s8 = warp_reduce_scatter8(acc, lane);
-        if ((lane & 3) == 0)
-            ((R*)(p.partial + ((size_t)(m - 1) * C + rank) * kEntries))[warp * 8 + (lane >> 2)] = s8;
+        if constexpr (COMP) {
+            // compensated: each warp's 8 sums as doubles (NT / 32 x 8 <= kEntries)
+            static_assert(NT / 32 * 8 <= kEntries, "compensated cluster sums: at most 14 warps");
+            const F32c s8 = warp_reduce_scatter8c(g.v, lane);
+            if ((lane & 3) == 0) (p.partial + ((size_t)(m - 1) * C + rank) * kEntries)[warp * 8 + (lane >> 2)] = c_val(s8);
+        } else {
+            R acc[8];
+            g.out(acc);
+            const R s8 = warp_reduce_scatter8(acc, lane);
+            if ((lane & 3) == 0)
+                ((R*)(p.partial + ((size_t)(m - 1) * C + rank) * kEntries))[warp * 8 + (lane >> 2)] = s8;
+        }
         asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
     }
     return true;
@@ -1694,7 +1863,7 @@ template <int VARIANT> __device__ __forceinline__ bool chain_barrier(const Param
 // WIDE: the team variant's FP32 paths take two sites per thread per pass (more
 // registers); the server kernel, which holds every instantiation in one kernel,
 // takes one.
-template <class R, int VARIANT, int NV = kVec, int NT = kThreads, bool WIDE = true>
+template <class R, int VARIANT, int NV = kVec, int NT = kThreads, bool WIDE = true, bool COMP = false>
 __device__ __forceinline__ void run_chain(const Params& p, const int cta, double2* dyn,
                                           typename Cx<R>::T* vec_smem)
 {
@@ -1846,12 +2015,13 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
             // Each warp leaves its 8 sums of step m (type R) in w8[m & 1]; they are added
             // over the warps in FP64 during step m+1, while its neighbour loads are in
             // flight (the wait at the top of each step orders the two).
-            __shared__ R w8[2][NW][8];
+            using W8T = std::conditional_t<COMP, float2, R>;  // compensated: (hi, lo)
+            __shared__ W8T w8[2][NW][8];
             auto flush8 = [&](int m) {
                 if (tid < 8) {
                     double sum = 0.0;
 #pragma unroll
-                    for (int w = 0; w < NW; ++w) sum += (double)w8[m & 1][w][tid];
+                    for (int w = 0; w < NW; ++w) sum += to_d(w8[m & 1][w][tid]);
                     p.partial[((size_t)(m - 1) * p.ncta + cta) * kEntries + tid] = sum;
                 }
             };
@@ -1861,7 +2031,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
             const bool helper = p.helper7 != 0;
             __shared__ int s_go2;
             if (helper && warp == kWarps - 1) {
-                for (int e = lane; e < 16; e += 32) w8[e >> 3][kWarps - 1][e & 7] = (R)0;
+                for (int e = lane; e < 16; e += 32) w8[e >> 3][kWarps - 1][e & 7] = W8T{};
                 bool ok = true;
                 for (int m = 1; m <= p.nsteps + 1 && ok; ++m) {
                     if (m > 1) {
@@ -1918,6 +2088,12 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 else publish(p, cta, phase + (unsigned)m + 1u);
                 // |r_m^o|^2, |r_m^v|^2, <r_m^o|r_m^v>, Re<r_m^o|r_m+1^o>, Re<r_m^v|r_m+1^v>, <r_m^o|r_m+1^v>
                 const R2 a = cur[0], b = cur[1], na = nxt[0], nbv = nxt[1];
+                if constexpr (COMP) {
+                    F32c c8[8] = {};
+                    gram8_c(c8, a, b, na, nbv);
+                    const F32c s8 = warp_reduce_scatter8c(c8, lane);
+                    if ((lane & 3) == 0) w8[m & 1][warp][lane >> 2] = make_float2(s8.hi, s8.lo);
+                } else {
                 R v8[8];
                 v8[0] = fma(a.x, a.x, a.y * a.y);
                 v8[1] = fma(b.x, b.x, b.y * b.y);
@@ -1929,6 +2105,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 v8[7] = fma(a.x, nbv.y, -(a.y * nbv.x));
                 const R s8 = warp_reduce_scatter8(v8, lane);
                 if ((lane & 3) == 0) w8[m & 1][warp][lane >> 2] = s8;
+                }
 #pragma unroll
                 for (int v = 0; v < 2; ++v) {
                     prv[v] = cur[v];
@@ -1965,12 +2142,13 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
             // ---- steps m = 1 .. M/2-1: r_{m+1} = 2 Htilde r_m - r_{m-1} and the Gram sums ----
             // FP32: each warp leaves its 112 Gram sums of step m in g32[m & 1]; they are added
             // over the warps in FP64 during step m+1 while its neighbour loads are in flight.
-            __shared__ float g32[sizeof(R) == 4 ? 2 : 1][sizeof(R) == 4 ? NW : 1][kEntries];
+            using G32T = std::conditional_t<COMP, float2, float>;  // compensated: (hi, lo)
+            __shared__ G32T g32[sizeof(R) == 4 ? 2 : 1][sizeof(R) == 4 ? NW : 1][kEntries];
             auto flush112 = [&](int m) {
                 if (tid < kEntries) {
                     double sum = 0.0;
     #pragma unroll
-                    for (int w = 0; w < NW; ++w) sum += (double)g32[m & 1][w][tid];
+                    for (int w = 0; w < NW; ++w) sum += to_d(g32[m & 1][w][tid]);
                     p.partial[((size_t)(m - 1) * p.ncta + cta) * kEntries + tid] = sum;
                 }
             };
@@ -2157,7 +2335,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 __shared__ int s_go32;
                 if (helper && warp == kWarps - 1) {
                     for (int w = 0; w < 2; ++w)
-                        for (int e = lane; e < kEntries; e += 32) g32[w][kWarps - 1][e] = 0.0f;
+                        for (int e = lane; e < kEntries; e += 32) g32[w][kWarps - 1][e] = G32T{};
                     bool ok = true;
                     for (int m = 1; m <= p.nsteps + 1 && ok; ++m) {
                         if (m > 1) {
@@ -2207,10 +2385,17 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                         else publish(p, cta, phase + (unsigned)m + 1u);
                         // Gram entries e = 0..55: e < 28 -> conj(r_m^j) r_m^k, else conj(r_m^j) r_{m+1}^k,
                         // (j, k) the upper pair e mod 28; 4 chunks of 14 complex values, warp butterfly.
-                        gram_chunk_reduce_raw<R, R2, 0>(cur, nxt, lane, g32[m & 1][warp]);
-                        gram_chunk_reduce_raw<R, R2, 1>(cur, nxt, lane, g32[m & 1][warp]);
-                        gram_chunk_reduce_raw<R, R2, 2>(cur, nxt, lane, g32[m & 1][warp]);
-                        gram_chunk_reduce_raw<R, R2, 3>(cur, nxt, lane, g32[m & 1][warp]);
+                        if constexpr (COMP) {
+                            gram_chunk_reduce_c<0>(cur, nxt, lane, g32[m & 1][warp]);
+                            gram_chunk_reduce_c<1>(cur, nxt, lane, g32[m & 1][warp]);
+                            gram_chunk_reduce_c<2>(cur, nxt, lane, g32[m & 1][warp]);
+                            gram_chunk_reduce_c<3>(cur, nxt, lane, g32[m & 1][warp]);
+                        } else {
+                            gram_chunk_reduce_raw<R, R2, 0>(cur, nxt, lane, g32[m & 1][warp]);
+                            gram_chunk_reduce_raw<R, R2, 1>(cur, nxt, lane, g32[m & 1][warp]);
+                            gram_chunk_reduce_raw<R, R2, 2>(cur, nxt, lane, g32[m & 1][warp]);
+                            gram_chunk_reduce_raw<R, R2, 3>(cur, nxt, lane, g32[m & 1][warp]);
+                        }
     #pragma unroll
                         for (int v = 0; v < kVec; ++v) {
                             prv[v] = cur[v];
@@ -2222,19 +2407,19 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 flush112(p.nsteps);
             }
         } else if constexpr (VARIANT == 2) {
-            cluster_steps2<R, NT>(p, cta, vec_smem, s_loc, s_c);
+            cluster_steps2<R, NT, COMP>(p, cta, vec_smem, s_loc, s_c);
         } else if constexpr (NV == 2) {
             if (vec_smem) {
-                if (!team_steps2<R, SmemVec, WIDE>(p, cta, phase, buf0, buf1, s_loc, s_c, red, SmemVec{})) return;
+                if (!team_steps2<R, SmemVec, WIDE, COMP>(p, cta, phase, buf0, buf1, s_loc, s_c, red, SmemVec{})) return;
             } else {
-                if (!team_steps2<R, GlobalVec, WIDE>(p, cta, phase, buf0, buf1, s_loc, s_c, red, GlobalVec{}))
+                if (!team_steps2<R, GlobalVec, WIDE, COMP>(p, cta, phase, buf0, buf1, s_loc, s_c, red, GlobalVec{}))
                     return;
             }
         } else {
             if (vec_smem) {
-                if (!team_steps<R, SmemVec, WIDE>(p, cta, phase, buf0, buf1, s_loc, red, dyn, SmemVec{})) return;
+                if (!team_steps<R, SmemVec, WIDE, COMP>(p, cta, phase, buf0, buf1, s_loc, red, dyn, SmemVec{})) return;
             } else {
-                if (!team_steps<R, GlobalVec, WIDE>(p, cta, phase, buf0, buf1, s_loc, red, dyn, GlobalVec{}))
+                if (!team_steps<R, GlobalVec, WIDE, COMP>(p, cta, phase, buf0, buf1, s_loc, red, dyn, GlobalVec{}))
                     return;
             }
         }
@@ -2285,7 +2470,8 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                         // fourth (CTA, warp) slot from lane >> 3
                         double sum = 0.0;
                         for (int cw = lane >> 3; cw < p.ncta * NW; cw += 4) {
-                            const R* row = (const R*)(src + (size_t)(cw / NW) * kEntries);
+                            using CS = std::conditional_t<COMP, double, R>;  // compensated: doubles
+                            const CS* row = (const CS*)(src + (size_t)(cw / NW) * kEntries);
                             sum += (double)__ldcg(row + (cw % NW) * 8 + (lane & 7));
                         }
                         sum += __shfl_xor_sync(0xffffffffu, sum, 8);
@@ -2427,17 +2613,18 @@ template <class R, int NV> constexpr int engine_threads()
     return (sizeof(R) == 8 && NV == kVec) ? kThreads + 32 : kThreads;
 }
 
-// A single chain spread over the whole GPU.
-template <class R, int NV = kVec>
+// A single chain spread over the whole GPU.  COMP (FP32 only): compensated
+// Gram dot products.
+template <class R, int NV = kVec, bool COMP = false>
 __global__ void __launch_bounds__(engine_threads<R, NV>(), 1) gfmc_engine(const Params p)
 {
     extern __shared__ double2 dyn[];
-    run_chain<R, 0, NV, engine_threads<R, NV>()>(p, blockIdx.x, dyn, nullptr);
+    run_chain<R, 0, NV, engine_threads<R, NV>(), true, COMP>(p, blockIdx.x, dyn, nullptr);
 }
 
 // A batch of chains, each on its own team of CTAs (jobs sorted by cta0).
 // The dynamic shared memory holds [vector area of vec_bytes][work area].
-template <class R>
+template <class R, bool COMP = false>
 __global__ void __launch_bounds__(kThreads, 1) gfmc_team_engine(const TeamJob* __restrict__ jobs, int njobs,
                                                                  int vec_bytes)
 {
@@ -2476,13 +2663,15 @@ __global__ void __launch_bounds__(kThreads, 1) gfmc_team_engine(const TeamJob* _
     load();
     if (sp.nv == 2) {
         do {
-            run_chain<R, 1, 2>(sp, s_cta, dyn_all + vec_bytes / (int)sizeof(double2), s_vs ? (R2*)dyn_all : nullptr);
+            run_chain<R, 1, 2, kThreads, true, COMP>(sp, s_cta, dyn_all + vec_bytes / (int)sizeof(double2),
+                                                     s_vs ? (R2*)dyn_all : nullptr);
             if (!next()) break;
             load();
         } while (true);
     } else {
         do {
-            run_chain<R, 1>(sp, s_cta, dyn_all + vec_bytes / (int)sizeof(double2), s_vs ? (R2*)dyn_all : nullptr);
+            run_chain<R, 1, kVec, kThreads, true, COMP>(sp, s_cta, dyn_all + vec_bytes / (int)sizeof(double2),
+                                                        s_vs ? (R2*)dyn_all : nullptr);
             if (!next()) break;
             load();
         } while (true);
@@ -2498,11 +2687,16 @@ __global__ void __launch_bounds__(kThreads, 1) gfmc_team_engine(const TeamJob* _
 // Threads per CTA of the cluster engine: FP32 512 (one site per thread per
 // pass, twice the warps of the other engines to hide shared-memory latency),
 // FP64 256.
-template <class R> constexpr int cluster_threads() { return sizeof(R) == 4 ? 2 * kThreads : kThreads; }
+// The compensated FP32 variant keeps 256 threads: its warps' 8 sums go to the
+// partial row as doubles.
+template <class R, bool COMP = false> constexpr int cluster_threads()
+{
+    return sizeof(R) == 4 && !COMP ? 2 * kThreads : kThreads;
+}
 
-template <class R>
-__global__ void __launch_bounds__(cluster_threads<R>(), 1) gfmc_cluster_engine(const TeamJob* __restrict__ jobs,
-                                                                                int vec_bytes)
+template <class R, bool COMP = false>
+__global__ void __launch_bounds__(cluster_threads<R, COMP>(), 1) gfmc_cluster_engine(const TeamJob* __restrict__ jobs,
+                                                                                      int vec_bytes)
 {
     extern __shared__ double2 dyn_all[];
     __shared__ Params sp;
@@ -2513,7 +2707,7 @@ __global__ void __launch_bounds__(cluster_threads<R>(), 1) gfmc_cluster_engine(c
     if (threadIdx.x == 0) sp = jobs[job].p;
     __syncthreads();
     using R2 = typename Cx<R>::T;
-    run_chain<R, 2, 2, cluster_threads<R>()>(sp, rank, dyn_all, (R2*)dyn_all);
+    run_chain<R, 2, 2, cluster_threads<R, COMP>(), true, COMP>(sp, rank, dyn_all, (R2*)dyn_all);
 }
 
 }  // namespace gfmc

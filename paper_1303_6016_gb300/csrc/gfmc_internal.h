@@ -72,6 +72,9 @@ struct Params {
     // site (vector o on one parity, its 6 neighbours' on the other) and forms
     // only the Gram sums that are not zero by parity
     int bip;
+    // FP32-mixed: the Gram dot products of the doubling (Eq. mu2) with
+    // compensated FP32 products and warp sums (Dot2) before FP64
+    int comp;
     // single-chain engines on 256 threads (FP32 unit vectors, proposal vectors):
     // every tile fits 7 warps, so warp 7 publishes and polls the flags while
     // the other warps form the Gram sums
@@ -138,15 +141,18 @@ cudaError_t launch_engine_f32(const Params& p, cudaStream_t s);
 cudaError_t launch_engine_f64(const Params& p, int nv, cudaStream_t s);
 cudaError_t launch_engine_f32(const Params& p, int nv, cudaStream_t s);
 cudaError_t launch_team_f64(const TeamJob* d_jobs, int njobs, int grid, int vec_bytes, int smem, cudaStream_t s);
-cudaError_t launch_team_f32(const TeamJob* d_jobs, int njobs, int grid, int vec_bytes, int smem, cudaStream_t s);
+cudaError_t launch_team_f32(const TeamJob* d_jobs, int njobs, int grid, int vec_bytes, int smem, cudaStream_t s,
+                            bool comp);
 cudaError_t team_max_ctas(int precision, int smem, int* out);
 // launch_team_* through cudaLaunchKernelEx with the cooperative attribute (capturable in a CUDA graph)
 cudaError_t launch_team_ex_f64(const TeamJob* d_jobs, int njobs, int grid, int vec_bytes, int smem, cudaStream_t s);
-cudaError_t launch_team_ex_f32(const TeamJob* d_jobs, int njobs, int grid, int vec_bytes, int smem, cudaStream_t s);
+cudaError_t launch_team_ex_f32(const TeamJob* d_jobs, int njobs, int grid, int vec_bytes, int smem, cudaStream_t s,
+                               bool comp);
 cudaError_t launch_server(const ServerArgs& a, int grid, int smem, cudaStream_t s);
 // one cluster of C CTAs per job (recursion on the proposal's vectors)
 cudaError_t launch_cluster_f64(const TeamJob* d_jobs, int njobs, int C, int vec_bytes, int smem, cudaStream_t s);
-cudaError_t launch_cluster_f32(const TeamJob* d_jobs, int njobs, int C, int vec_bytes, int smem, cudaStream_t s);
+cudaError_t launch_cluster_f32(const TeamJob* d_jobs, int njobs, int C, int vec_bytes, int smem, cudaStream_t s,
+                               bool comp);
 cudaError_t cluster_max_active(int precision, int C, int smem, int* out);
 // static shared memory of the cluster engine of a precision (bytes)
 cudaError_t cluster_static_smem(int precision, int* out);

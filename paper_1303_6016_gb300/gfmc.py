@@ -50,7 +50,7 @@ class Options(ctypes.Structure):
                 ("lorentz_lambda", ctypes.c_double), ("spectral_scale", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("chain_id", ctypes.c_uint32),
                 ("stream", ctypes.c_void_p), ("num_ctas", ctypes.c_int), ("recursion", ctypes.c_int),
-                ("nodes", ctypes.c_int), ("engine", ctypes.c_int)]
+                ("nodes", ctypes.c_int), ("engine", ctypes.c_int), ("compensated", ctypes.c_int)]
 
 
 _lib = None
@@ -151,7 +151,7 @@ class Chain:
                  M: int = 256, precision: str = "fp64", kernel: str = "jackson",
                  lorentz_lambda: float = 4.0, spectral_scale: float = 0.0, seed: int = 1,
                  chain_id: int = 0, stream=None, num_ctas: int = 0, recursion: str = "unit_vectors",
-                 nodes: int = 0, engine: str = "auto"):
+                 nodes: int = 0, engine: str = "auto", compensated: bool = False):
         lib = load()
         self.L, self.N, self.M = int(L), int(L) ** 3, int(M)
         self.K = int(nodes) if nodes else self.M  # Chebyshev nodes of G and of the quadrature
@@ -172,7 +172,9 @@ class Chain:
         opt.recursion = RECURSIONS[recursion]
         opt.nodes = int(nodes)
         opt.engine = ENGINES[engine]
+        opt.compensated = 1 if compensated else 0
         self.engine = engine
+        self.compensated = bool(compensated)
         sp = np.ascontiguousarray(spins, dtype=np.float64).reshape(-1, 2)
         if sp.shape[0] != self.N:
             raise ValueError(f"spins has {sp.shape[0]} rows, expected N = {self.N}")

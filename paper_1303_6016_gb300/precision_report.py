@@ -1,4 +1,4 @@
-"""Error of the FP32-mixed path against the FP64 path on the L = 32 workloads.
+"""Error of the FP32-mixed paths against the FP64 path on the L = 32 workloads.
 
     python -m paper_1303_6016_gb300.precision_report [--L 32] [--M 1024 2048] [--sites 6]
                                                      [--json out.json]
@@ -8,8 +8,12 @@ about +z with kappa = 5, seed 2) and each M, on a sample of sites it reports
   * the moment error |mu_mixed - mu_fp64| as a function of n (maximum over the
     49 entries and the sampled sites, in bands of n),
   * the Delta Omega error |dO_mixed - dO_fp64| for a seeded proposal at each
-    sampled site.
-The FP64 path itself is checked against the oracle by the parity tests.
+    sampled site,
+for three FP32-mixed arithmetics: the default engine (at L = 32 the vector
+clusters, moments read off the recursion with no dot products), the grid
+engine's doubling with plain FP32 warp sums of the Gram products, and the
+same with compensated (Dot2) products and sums.  The FP64 path itself is
+checked against the oracle by the parity tests.
 """
 from __future__ import annotations
 
@@ -37,26 +41,28 @@ def run(L=32, Ms=(1024, 2048), n_sites=6, kinds=("uniform", "vmf")):
         sp = inputs.make(kind, L, seed=0 if kind == "uniform" else 2)
         for M in Ms:
             bands = [(0, 64), (64, 256), (256, M // 2), (M // 2, M)]
-            band_err = np.zeros(len(bands))
-            dom_err = []
-            dom_rel = []
-            with gfmc.Chain(L, sp, M=M, precision="fp64") as c64, \
-                    gfmc.Chain(L, sp, M=M, precision="fp32_mixed") as c32:
-                for q, o in enumerate(sites):
-                    m64 = c64.moments(o)
-                    m32 = c32.moments(o)
-                    err = np.abs(m32 - m64).max(axis=(0, 1))
-                    for b, (lo, hi) in enumerate(bands):
-                        band_err[b] = max(band_err[b], float(err[lo:hi].max()))
-                    th, ph = proposal(q)
-                    d64 = c64.delta_omega(o, th, ph)
-                    d32 = c32.delta_omega(o, th, ph)
-                    dom_err.append(abs(d32 - d64))
-                    dom_rel.append(abs(d32 - d64) / max(abs(d64), 1e-300))
-            out.append({"spins": kind, "L": L, "M": M, "sites": sites,
-                        "moment_err_by_n": {f"[{lo},{hi})": float(e) for (lo, hi), e in zip(bands, band_err)},
-                        "domega_err_max": float(max(dom_err)), "domega_err_mean": float(np.mean(dom_err)),
-                        "domega_rel_err_max": float(max(dom_rel))})
+            variants = {"default": {}, "grid_plain": {"engine": "grid"},
+                        "grid_compensated": {"engine": "grid", "compensated": True}}
+            with gfmc.Chain(L, sp, M=M, precision="fp64") as c64:
+                ref = {o: c64.moments(o) for o in sites}
+                dref = {q: c64.delta_omega(o, *proposal(q)) for q, o in enumerate(sites)}
+            rows = {}
+            for name, kw in variants.items():
+                band_err = np.zeros(len(bands))
+                dom_err, dom_rel = [], []
+                with gfmc.Chain(L, sp, M=M, precision="fp32_mixed", **kw) as c32:
+                    for q, o in enumerate(sites):
+                        err = np.abs(c32.moments(o) - ref[o]).max(axis=(0, 1))
+                        for b, (lo, hi) in enumerate(bands):
+                            band_err[b] = max(band_err[b], float(err[lo:hi].max()))
+                        d32 = c32.delta_omega(o, *proposal(q))
+                        dom_err.append(abs(d32 - dref[q]))
+                        dom_rel.append(abs(d32 - dref[q]) / max(abs(dref[q]), 1e-300))
+                rows[name] = {"moment_err_by_n": {f"[{lo},{hi})": float(e) for (lo, hi), e in zip(bands, band_err)},
+                              "domega_err_max": float(max(dom_err)), "domega_err_mean": float(np.mean(dom_err)),
+                              "domega_rel_err_max": float(max(dom_rel))}
+            out.append(dict({"spins": kind, "L": L, "M": M, "sites": sites}, **rows["default"],
+                            variants=rows))
     return out
 
 
