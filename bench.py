@@ -566,6 +566,11 @@ def main():
     peak_tf = gfmc.fma_peak_tflops("fp64", repeats=3, stream=stream.cuda_stream)
     e2e_per, h2d, d2h = time_e2e(ch, stream, U, max(3, args.steps // 2), ch.get_spins())
     e2e_value = U / (statistics.mean(e2e_per) / 1000.0) * world
+    vec_bytes = 2 * 7 * L ** 3 * 16
+    footprint = {"device_bytes": ch.device_bytes, "vector_bytes": vec_bytes,
+                 "beyond_vectors": ch.device_bytes - vec_bytes,
+                 "note": "device memory of the FP64 chain's handle (gfmc_device_bytes); the Gram sums of the "
+                         "doubling are one [M/2-1][112] fixed-point array whatever the number of CTAs"}
     ch.close()
 
     line = {
@@ -590,6 +595,7 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
         "clocks": clocks,
+        "footprint": footprint,
     }
 
     # ---- FP32-mixed ----
@@ -670,6 +676,9 @@ def main():
     if not args.no_serving:
         from paper_1303_6016_gb300 import serving
         line["serving"] = serving.sweep(rates=(10, 100, 1000), seconds=3.0, K=2, drain_s=8.0)
+        if not args.no_variant:
+            line["serving_unit_vectors"] = serving.sweep(rates=(10, 100, 1000), seconds=3.0, K=2, drain_s=8.0,
+                                                         recursion="unit_vectors")
 
     if not args.no_latency:
         line["sweep_latency"] = [sweep_latency(gfmc, inputs, stream, 8, M, prec, args.latency_sweeps)

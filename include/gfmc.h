@@ -189,6 +189,13 @@ gfmc_status gfmc_set_state(gfmc_t h, const double* spins, uint64_t update_counte
 /* Read the update counter. */
 gfmc_status gfmc_get_counter(gfmc_t h, uint64_t* update_counter);
 
+/* Bytes of device memory the handle holds (every buffer it has allocated,
+ * including those a batch made it grow; freed by gfmc_destroy).  Most of it
+ * is the two recursion buffers, 2 x 7 x N complex values of the chain's
+ * precision; the Gram sums of the doubling take (M/2 - 1) x 112 x 8 bytes
+ * whatever the number of CTAs. */
+gfmc_status gfmc_device_bytes(gfmc_t h, uint64_t* bytes);
+
 /* Run a batch of independent chains in one launch, each on its own team of
  * CTAs (the multi-chain form of Algorithm 1's Monte Carlo sampling, Sec. 3.2:
  * independent chains share nothing).  Chain c runs n_updates[c] sequential
@@ -354,9 +361,9 @@ gfmc_status gfmc_inject_stall(gfmc_t h, int enable);
  * that every GPU which loads the library holds until the process exits.
  *   L, t, mu, beta, M      as for gfmc_create; the scratch limits them to
  *                          (L, M) whose buffers fit in 8 MiB with at most 32
- *                          CTAs (for example L <= 16 with M <= 512, or L <= 12
- *                          with M <= 1024); larger sizes return GFMC_EINVAL
- *                          with the bytes they would need.
+ *                          CTAs of 256 sites: every M with L <= 20; larger
+ *                          lattices return GFMC_EINVAL with the bytes and
+ *                          CTAs they would need.
  *   kernel, lorentz_lambda, spectral_scale   as in gfmc_options (<= 0: defaults).
  *   d_spins   DEVICE pointer, double[N][2] (theta, phi), owned by the caller, read only.
  *   site, theta_new, phi_new   as for gfmc_delta_omega.

@@ -33,6 +33,7 @@ struct gfmc_ctx {
     bool vcl = false;
     Params P{};
     std::vector<void*> allocs;
+    uint64_t alloc_bytes = 0;
     // growable output buffers of the sweep mode
     long long trace_cap = 0;
     unsigned char* d_dec = nullptr;
@@ -41,7 +42,7 @@ struct gfmc_ctx {
     double* d_mag = nullptr;
     unsigned long long* d_nacc = nullptr;
     long long* d_nmag = nullptr;
-    // CTAs the per-CTA buffers (partials, flags, phase sums) are sized for
+    // CTAs the per-CTA buffers (flags, phase sums) are sized for
     int cap_ncta = 0;
     // more sites than threads of the chain's CTAs: single-chain calls run the
     // team variant of the engine (several sites per thread) as a one-job launch
@@ -90,11 +91,22 @@ template <class T> cudaError_t dalloc(gfmc_ctx* h, T** p, size_t n)
     cudaError_t e = cudaMalloc(&q, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
     if (e != cudaSuccess) return e;
     h->allocs.push_back(q);
+    h->alloc_bytes += n * sizeof(T) > 0 ? n * sizeof(T) : 16;
     *p = (T*)q;
     return cudaSuccess;
 }
 
 bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// The engine clears the chain's Gram sums as it reads them; a launch that
+// ended early (a device error) can leave a step partly added, so the host
+// clears them before the chain runs again.
+void clear_gram(gfmc_ctx* h, cudaStream_t s)
+{
+    const Params& P = h->P;
+    if (cudaMemsetAsync(P.gram, 0, sizeof(unsigned long long) * (size_t)P.nsteps * gfmc::kEntries, s) == cudaSuccess)
+        cudaStreamSynchronize(s);
+}
 
 gfmc_status check_spins(gfmc_ctx* h, const double* spins, int N)
 {
@@ -233,9 +245,12 @@ gfmc_status run_engine(gfmc_ctx* h, Params& P)
     if ((e = cudaMemcpyAsync(err, P.err, sizeof(err), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
         return cuda_fail(h, e, "reading the engine status");
     if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return cuda_fail(h, e, "engine execution");
+    if (err[0] != 0) clear_gram(h, h->stream);
     if (err[0] == gfmc::ERR_TIMEOUT)
         return fail(h, GFMC_ETIMEOUT, "a device wait ran out of its budget (stage %d, CTA %d, aux %d)", err[1],
                     err[2], err[3]);
+    if (err[0] == gfmc::ERR_NUMERIC && err[1] == 90)
+        return fail(h, GFMC_ENUMERIC, "a Gram sum of step %d is out of range or not finite (CTA %d)", err[3], err[2]);
     if (err[0] == gfmc::ERR_NUMERIC)
         return fail(h, GFMC_ENUMERIC, "non-finite d(z) at node %d (CTA %d)", err[3], err[2]);
     if (err[0] != 0) return fail(h, GFMC_ECUDA, "engine error word %d", err[0]);
@@ -270,23 +285,19 @@ gfmc_status ensure_team_capacity(gfmc_ctx* h, int tc)
 {
     if (tc <= h->cap_ncta) return GFMC_OK;
     Params& P = h->P;
-    double *part = nullptr, *qp = nullptr, *mp = nullptr;
+    double *qp = nullptr, *mp = nullptr;
     unsigned* fl = nullptr;
     cudaError_t e;
-    if ((e = dalloc(h, &part, (size_t)P.nsteps * tc * gfmc::kEntries)) != cudaSuccess ||
-        (e = dalloc(h, &qp, 2 * (size_t)tc)) != cudaSuccess || (e = dalloc(h, &mp, 3 * (size_t)tc)) != cudaSuccess ||
+    if ((e = dalloc(h, &qp, 2 * (size_t)tc)) != cudaSuccess || (e = dalloc(h, &mp, 3 * (size_t)tc)) != cudaSuccess ||
         (e = dalloc(h, &fl, (size_t)tc)) != cudaSuccess) {
-        release(h, part);
         release(h, qp);
         release(h, mp);
         release(h, fl);
         return cuda_fail(h, e, "growing per-CTA buffers");
     }
-    release(h, P.partial);
     release(h, P.qpart);
     release(h, P.magpart);
     release(h, P.flags);
-    P.partial = part;
     P.qpart = qp;
     P.magpart = mp;
     P.flags = fl;
@@ -498,7 +509,7 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
         (e = dalloc(h, &P.gker, (size_t)M)) != cudaSuccess || (e = dalloc(h, &P.twc, (size_t)M)) != cudaSuccess ||
         (e = dalloc(h, &P.fftw, (size_t)K / 2)) != cudaSuccess ||
         (e = dalloc(h, &P.sinth, (size_t)K)) != cudaSuccess || (e = dalloc(h, &P.cumw, (size_t)K)) != cudaSuccess ||
-        (e = dalloc(h, &P.partial, (size_t)P.nsteps * ncta * gfmc::kEntries)) != cudaSuccess ||
+        (e = dalloc(h, &P.gram, (size_t)P.nsteps * gfmc::kEntries)) != cudaSuccess ||
         (e = dalloc(h, &P.fftin, 4 * (size_t)M)) != cudaSuccess ||
         (e = dalloc(h, &P.gnode, 4 * (size_t)K)) != cudaSuccess ||
         (e = dalloc(h, &P.qpart, 2 * (size_t)std::max(ncta, 16))) != cudaSuccess ||
@@ -544,6 +555,8 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
     P.nbr_ptr = d_np;
     P.nbr_idx = d_ni;
     if ((e = cudaMemcpyAsync(P.spins, spins, sizeof(double) * 2 * N, cudaMemcpyHostToDevice, h->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(P.gram, 0, sizeof(unsigned long long) * (size_t)P.nsteps * gfmc::kEntries, h->stream)) !=
+            cudaSuccess ||
         (e = cudaMemcpyAsync(d_ts, tstart.data(), sizeof(int) * tstart.size(), cudaMemcpyHostToDevice, h->stream)) !=
             cudaSuccess ||
         (e = cudaMemcpyAsync(d_np, nptr.data(), sizeof(int) * nptr.size(), cudaMemcpyHostToDevice, h->stream)) !=
@@ -694,6 +707,14 @@ gfmc_status gfmc_set_state(gfmc_t h, const double* spins, uint64_t update_counte
     return GFMC_OK;
 }
 
+gfmc_status gfmc_device_bytes(gfmc_t h, uint64_t* bytes)
+{
+    if (!h) return fail(nullptr, GFMC_EINVAL, "invalid handle");
+    if (!bytes) return fail(h, GFMC_EINVAL, "bytes is NULL");
+    *bytes = h->alloc_bytes;
+    return GFMC_OK;
+}
+
 gfmc_status gfmc_get_counter(gfmc_t h, uint64_t* update_counter)
 {
     if (!h) return fail(nullptr, GFMC_EINVAL, "invalid handle");
@@ -832,6 +853,7 @@ gfmc_status gfmc_run_batch(gfmc_t* chains, int n_chains, const int64_t* n_update
         if ((e = cudaMemcpy(err, h->P.err, sizeof(err), cudaMemcpyDeviceToHost)) != cudaSuccess ||
             (e = cudaMemcpy(&nacc, h->d_nacc, sizeof(nacc), cudaMemcpyDeviceToHost)) != cudaSuccess)
             return cuda_fail(nullptr, e, "reading batch status");
+        if (err[0] != 0) clear_gram(h, s);
         if (err[0] != 0 && result == GFMC_OK) {
             result = err[0] == gfmc::ERR_TIMEOUT ? GFMC_ETIMEOUT : err[0] == gfmc::ERR_NUMERIC ? GFMC_ENUMERIC : GFMC_ECUDA;
             fail(nullptr, result, "chain %d: device error %d at stage %d", c, err[0], err[1]);
@@ -1065,6 +1087,7 @@ gfmc_status gfmc_run_clusters(gfmc_t* chains, int n_chains, const int64_t* n_upd
             (e = cudaMemcpy(&nm, h->d_nmag, sizeof(nm), cudaMemcpyDeviceToHost)) != cudaSuccess)
             return cuda_fail(nullptr, e, "reading cluster status");
         if (err[0] != 0) {
+            clear_gram(h, s);
             if (result == GFMC_OK) {
                 result = err[0] == gfmc::ERR_NUMERIC ? GFMC_ENUMERIC : GFMC_ECUDA;
                 fail(nullptr, result, "chain %d: device error %d at stage %d", c, err[0], err[1]);
@@ -1435,6 +1458,7 @@ gfmc_status gfmc_plan_sync(gfmc_plan_t p, uint64_t* n_accepted, uint8_t** decisi
             (e = cudaMemcpy(&nm, h->d_nmag, sizeof(nm), cudaMemcpyDeviceToHost)) != cudaSuccess)
             return cuda_fail(nullptr, e, "reading plan status");
         if (err[0] != 0) {
+            clear_gram(h, p->last);
             if (result == GFMC_OK) {
                 result = err[0] == gfmc::ERR_TIMEOUT ? GFMC_ETIMEOUT
                          : err[0] == gfmc::ERR_NUMERIC ? GFMC_ENUMERIC : GFMC_ECUDA;
@@ -1688,6 +1712,7 @@ gfmc_status gfmc_server_poll(gfmc_server_t s, int slot, int* done, uint64_t* n_a
     s->chain[slot] = nullptr;
     h->in_server = false;
     *done = 1;
+    if (err[0] != 0) clear_gram(h, s->post_stream);
     if (err[0] != 0)
         return sfail(s, err[0] == gfmc::ERR_TIMEOUT ? GFMC_ETIMEOUT : err[0] == gfmc::ERR_NUMERIC ? GFMC_ENUMERIC : GFMC_ECUDA,
                      "job in slot %d: device error %d at stage %d", slot, err[0], err[1]);

@@ -11,7 +11,8 @@
 //                 fused with the 2 x 28 Gram dot products <r_m^j|r_m^k>,
 //                 <r_m^j|r_{m+1}^k> (Eq. mu2); a CTA only waits for the CTAs
 //                 whose sites its stencil reads (release/acquire flags)
-//     reduce      per-CTA Gram partials -> 7x7 moments mu_n (doubling) ->
+//     reduce      Gram sums (each CTA adds its partials into a fixed-point
+//                 [nsteps][112] array) -> 7x7 moments mu_n (doubling) ->
 //                 the four real sequences <V|T_n|V>, V = o, v, o+v, o+iv,
 //                 damped by g_n and twisted by e^{-i n pi/2M} (Eq. mu_to_mu_tilde)
 //     FFT         M-point FFT of each sequence (Eq. green_fft), node mapping
@@ -26,8 +27,8 @@
 // R is the arithmetic type of the recursion vectors and the stencil (double
 // for the FP64 path, float for the mixed path).  Products for the dot
 // products are formed in R and summed in R across a warp; everything above
-// the warp (CTA sums, cross-CTA sums, moments, FFT, determinant, quadrature)
-// is FP64 for both paths.
+// the warp (CTA sums, moments, FFT, determinant, quadrature) is FP64 for both
+// paths, and the sums over CTAs are exact 64-bit fixed-point additions.
 //
 // Every spin-wait is bounded by p.budget clock cycles; on expiry the kernel
 // records GFMC_ETIMEOUT in p.err and all CTAs leave at their next wait.
@@ -156,6 +157,43 @@ __device__ __forceinline__ void set_error(const Params& p, int code, int where, 
         p.err[3] = aux;
         __threadfence();
     }
+}
+
+// ---------------------------------------------------------------------------
+// Gram sums over the CTAs of a chain (the dot products of Eq. mu2)
+// ---------------------------------------------------------------------------
+// Each CTA adds its partial sum of entry e at step m into p.gram[m - 1][e], a
+// signed 64-bit fixed-point number with kGramFrac fraction bits.  Integer
+// addition is exact and associative, so the folded sum does not depend on the
+// order in which the CTAs' additions reach memory (reruns agree bit for bit)
+// and the array is [nsteps][kEntries] whatever the number of CTAs.  Every
+// entry is an inner product <x|y> of Chebyshev vectors with |x|, |y| <= 2
+// (|T_n(Htilde) e| <= 1 for a spectrum inside [-1, 1]; the proposal's vector
+// v = Delta~ o has |v| <= |Delta~| <= 2), so the sums and every CTA's partial
+// lie inside [-4, 4], well within the range 2^(63 - kGramFrac) = 32; placing a
+// partial on the grid moves it by at most 2^-59 ~ 1.7e-18.  A partial outside
+// [-16, 16] (a non-finite value, or a spectral scale below the spectrum's
+// half width) records ERR_NUMERIC.  The reader of an entry clears it, so the
+// array is zero again when the update's sums have been read; after a launch
+// that ended early the host clears it.
+constexpr int kGramFrac = 58;
+
+__device__ __forceinline__ void gram_add(const Params& p, int m, int e, double x)
+{
+    if (!(fabs(x) <= 16.0)) {
+        set_error(p, ERR_NUMERIC, 90, m);
+        x = 0.0;
+    }
+    const long long q = __double2ll_rn(x * 0x1p58);
+    atomicAdd(p.gram + (size_t)(m - 1) * kEntries + e, (unsigned long long)q);
+}
+
+__device__ __forceinline__ double gram_take(const Params& p, int m, int e)
+{
+    unsigned long long* a = p.gram + (size_t)(m - 1) * kEntries + e;
+    const long long v = (long long)__ldcg(a);
+    __stcg(a, 0ull);
+    return (double)v * 0x1p-58;
 }
 
 // All CTAs of the launch meet here.  Returns false (in every thread) when an
@@ -721,8 +759,8 @@ __device__ __forceinline__ void gram8_c(F32c (&acc)[8], float2 a, float2 b, floa
 // instruction stream.  kGramGroups groups of 49 threads split the sites
 // (s = g, g + kGramGroups, ...) and the groups are added in order.  sr rows
 // (stride kStage): v -> r_m^v, 7+v -> r_{m+1}^v, 14+v -> -i r_m^v,
-// 21+v -> -i r_{m+1}^v.  out[kEntries] as the per-CTA partial row: entry e <
-// 28 at 2e, 2e+1 = conj(r_m^j) r_m^k summed; e >= 28 the same for r_{m+1}^k.
+// 21+v -> -i r_{m+1}^v.  The CTA's sums by entry (kEntries): entry e < 28 at
+// 2e, 2e+1 = conj(r_m^j) r_m^k summed; e >= 28 the same for r_{m+1}^k.
 constexpr int kGramUnits = 49;
 constexpr int kGramGroups = 5;
 
@@ -785,15 +823,16 @@ __device__ __forceinline__ void gram_units_f64(const double2* sr, int T, double*
     }
 }
 
-// out[e] = sum over the kGramGroups groups of gsum, in order (threads e < kEntries).
-__device__ __forceinline__ void gram_groups_f64(const double* gsum, double* out)
+// Entry e of the CTA's Gram sums of step m = the kGramGroups groups of gsum
+// added in order, into the chain's sums (threads e < kEntries).
+__device__ __forceinline__ void gram_groups_f64(const double* gsum, const Params& p, int m)
 {
     const int tid = threadIdx.x;
     if (tid < kEntries) {
         double s = gsum[tid];
 #pragma unroll
         for (int g = 1; g < kGramGroups; ++g) s += gsum[g * kEntries + tid];
-        out[tid] = s;
+        gram_add(p, m, tid, s);
     }
 }
 
@@ -821,8 +860,8 @@ __device__ __forceinline__ void gram_smem_acc(const double2* sr, int T, double& 
     }
 }
 
-// The four groups of gram_smem_acc added in order into out[kEntries].
-__device__ __forceinline__ void gram_smem_finish(double re, double im, double* gsum, double* out)
+// The four groups of gram_smem_acc added in order: the CTA's Gram sums of step m.
+__device__ __forceinline__ void gram_smem_finish(double re, double im, double* gsum, const Params& p, int m)
 {
     const int tid = threadIdx.x;
     if (tid < 4 * 56) {
@@ -833,7 +872,8 @@ __device__ __forceinline__ void gram_smem_finish(double re, double im, double* g
         gsum[g * kEntries + 2 * e + 1] = im;
     }
     __syncthreads();
-    if (tid < kEntries) out[tid] = ((gsum[tid] + gsum[kEntries + tid]) + gsum[2 * kEntries + tid]) + gsum[3 * kEntries + tid];
+    if (tid < kEntries)
+        gram_add(p, m, tid, ((gsum[tid] + gsum[kEntries + tid]) + gsum[2 * kEntries + tid]) + gsum[3 * kEntries + tid]);
 }
 
 // Vector storage of a team: L2-resident global memory or the CTA's shared memory.
@@ -902,7 +942,6 @@ __device__ bool team_steps(const Params& p, int cta, unsigned phase, typename Cx
         if (!wait_neighbours(p, cta, phase + (unsigned)m, 100 + m)) return false;
         const R2* rd = (m & 1) ? buf1 : buf0;  // r_m of every site
         R2* wr = (m & 1) ? buf0 : buf1;        // r_{m-1}, overwritten by r_{m+1}
-        double* prow = p.partial + ((size_t)(m - 1) * p.ncta + cta) * kEntries;
         if constexpr (sizeof(R) == 4) {
             // chunks of kThreads sites, one per thread: all loads issued before the first use;
             // the Gram products of two chunks summed in the thread, then by warp butterfly
@@ -973,7 +1012,7 @@ __device__ bool team_steps(const Params& p, int cta, unsigned phase, typename Cx
                 double sum = 0.0;
 #pragma unroll
                 for (int w = 0; w < kWarps; ++w) sum += red[w][tid];
-                prow[tid] = sum;
+                gram_add(p, m, tid, sum);
             }
         } else {
             double re = 0.0, im = 0.0;
@@ -1017,7 +1056,7 @@ __device__ bool team_steps(const Params& p, int cta, unsigned phase, typename Cx
                 __syncthreads();
             }
             publish(p, cta, phase + (unsigned)m + 1u);
-            gram_smem_finish(re, im, &red[0][0], prow);
+            gram_smem_finish(re, im, &red[0][0], p, m);
         }
     }
     return true;
@@ -1080,7 +1119,6 @@ __device__ bool team_steps2(const Params& p, int cta, unsigned phase, typename C
         if (!wait_neighbours(p, cta, phase + (unsigned)m, 100 + m)) return false;
         const R2* rd = (m & 1) ? buf1 : buf0;
         R2* wr = (m & 1) ? buf0 : buf1;
-        double* prow = p.partial + ((size_t)(m - 1) * p.ncta + cta) * kEntries;
         R acc[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) acc[e] = (R)0;
@@ -1159,7 +1197,7 @@ __device__ bool team_steps2(const Params& p, int cta, unsigned phase, typename C
             double sum = 0.0;
 #pragma unroll
             for (int w = 0; w < kWarps; ++w) sum += red[w][tid];
-            prow[tid] = sum;
+            gram_add(p, m, tid, sum);
         }
     }
     return true;
@@ -1339,12 +1377,11 @@ struct GramAccC {
 // step separates the steps (reads of step m are done before step m+1
 // overwrites, writes of step m visible before step m+1 reads).
 // vs: [buffer][T] of SOV, then [3][T] stored forward bonds.
-// Per step each warp writes its 8 Gram sums (type R) to its own slot of the
-// step's partial row, [C][NT / 32][8] in the rows of kEntries doubles; the
-// reduce phase adds them over warps and CTAs in FP64, so a step has no CTA
-// barrier and no FP64 arithmetic.  The cluster barrier is split: a CTA
-// arrives once its stores of r_{m+1} are issued, reduces its warps' sums,
-// then waits.  U sites per thread have all their loads issued before any
+// Per step each warp adds its 8 Gram sums into the chain's fixed-point sums
+// (8 reductions to global memory that the warp does not wait for), so a step
+// has no CTA barrier and no shared memory of its own.  The cluster barrier is
+// split: a CTA arrives once its stores of r_{m+1} are issued, reduces its
+// warps' sums, then waits.  U sites per thread have all their loads issued before any
 // arithmetic; U = 1 (the 16 warps of an FP32 CTA hide the shared-memory
 // latency, and two sites per thread spilled registers and measured slower).
 template <class R, int NT, bool COMP = false>
@@ -1543,16 +1580,14 @@ __device__ bool cluster_steps2(const Params& p, int rank, typename Cx<R>::T* vs,
         }
         asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
         if constexpr (COMP) {
-            // compensated: each warp's 8 sums as doubles (NT / 32 x 8 <= kEntries)
-            static_assert(NT / 32 * 8 <= kEntries, "compensated cluster sums: at most 14 warps");
+            // compensated: the (hi, lo) pair's value, exact in FP64
             const F32c s8 = warp_reduce_scatter8c(g.v, lane);
-            if ((lane & 3) == 0) (p.partial + ((size_t)(m - 1) * C + rank) * kEntries)[warp * 8 + (lane >> 2)] = c_val(s8);
+            if ((lane & 3) == 0) gram_add(p, m, lane >> 2, c_val(s8));
         } else {
             R acc[8];
             g.out(acc);
             const R s8 = warp_reduce_scatter8(acc, lane);
-            if ((lane & 3) == 0)
-                ((R*)(p.partial + ((size_t)(m - 1) * C + rank) * kEntries))[warp * 8 + (lane >> 2)] = s8;
+            if ((lane & 3) == 0) gram_add(p, m, lane >> 2, (double)s8);
         }
         asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
     }
@@ -1813,22 +1848,22 @@ __device__ __forceinline__ void gram_units_bip(const double2* sr, int a0, int a1
     gs[ere + 1] = im;
 }
 
-// out[e] = the 8 groups of gram_units_bip added in order, or 0 for the
-// entries that vanish by parity (threads e < kEntries).
-__device__ __forceinline__ void gram_groups_bip(const double* gsum, double* out)
+// Entry e of the CTA's Gram sums of step m = the 8 groups of gram_units_bip
+// added in order, into the chain's sums; the entries that vanish by parity
+// add nothing (threads e < kEntries).
+__device__ __forceinline__ void gram_groups_bip(const double* gsum, const Params& p, int m)
 {
     const int e = threadIdx.x;
     if (e < kEntries) {
         const int pp = (e % 56) >> 1;
         const int j = pair_j(pp), k = pair_k(pp);
         const bool live = e < 56 ? !(j == 0 && k > 0) && !(j == k && (e & 1)) : (j == 0 && k > 0);
-        double s = 0.0;
         if (live) {
-            s = gsum[e];
+            double s = gsum[e];
 #pragma unroll
             for (int g = 1; g < kBipGroups; ++g) s += gsum[g * kEntries + e];
+            gram_add(p, m, e, s);
         }
-        out[e] = s;
     }
 }
 
@@ -2022,7 +2057,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                     double sum = 0.0;
 #pragma unroll
                     for (int w = 0; w < NW; ++w) sum += to_d(w8[m & 1][w][tid]);
-                    p.partial[((size_t)(m - 1) * p.ncta + cta) * kEntries + tid] = sum;
+                    gram_add(p, m, tid, sum);
                 }
             };
             // With every tile within 7 warps (p.helper7), warp 7 has no site: it publishes
@@ -2149,7 +2184,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                     double sum = 0.0;
     #pragma unroll
                     for (int w = 0; w < NW; ++w) sum += to_d(g32[m & 1][w][tid]);
-                    p.partial[((size_t)(m - 1) * p.ncta + cta) * kEntries + tid] = sum;
+                    gram_add(p, m, tid, sum);
                 }
             };
             if constexpr (sizeof(R) == 8 && NT > kThreads) {
@@ -2208,7 +2243,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                         nbar_sync(3, NT);
                         if (!s_go) return;
                         if (m >= 2)
-                            gram_groups_bip(&red[0][0], p.partial + ((size_t)(m - 2) * p.ncta + cta) * kEntries);
+                            gram_groups_bip(&red[0][0], p, m - 1);
                         const R2* rd = (m & 1) ? buf1 : buf0;  // r_m of every site
                         R2* wr = (m & 1) ? buf0 : buf1;        // receives r_{m+1}; held r_{m-1}
                         const int pa = (par_o + m) & 1;        // parity of the sites holding r_m^0
@@ -2264,14 +2299,14 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                         }
                     }
                     nbar_sync(1, kThreads);
-                    gram_groups_bip(&red[0][0], p.partial + ((size_t)(p.nsteps - 1) * p.ncta + cta) * kEntries);
+                    gram_groups_bip(&red[0][0], p, p.nsteps);
                 } else {
                     for (int m = 1; m <= p.nsteps; ++m) {
                         // barrier 3 also ends every compute warp's Gram units of step m-1
                         nbar_sync(3, NT);
                         if (!s_go) return;
                         if (m >= 2)
-                            gram_groups_f64(&red[0][0], p.partial + ((size_t)(m - 2) * p.ncta + cta) * kEntries);
+                            gram_groups_f64(&red[0][0], p, m - 1);
                         const R2* rd = (m & 1) ? buf1 : buf0;  // r_m of every site
                         R2* wr = (m & 1) ? buf0 : buf1;        // receives r_{m+1}; held r_{m-1}
                         R2 nxt[kVec];
@@ -2322,7 +2357,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                         }
                     }
                     nbar_sync(1, kThreads);
-                    gram_groups_f64(&red[0][0], p.partial + ((size_t)(p.nsteps - 1) * p.ncta + cta) * kEntries);
+                    gram_groups_f64(&red[0][0], p, p.nsteps);
                 }
             } else {
                 // FP32: one site per thread, all 42 neighbour loads issued before the first use
@@ -2464,24 +2499,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                     vv[1] = s_vv1;
                     X[1] = s_ov1;
                 } else {
-                    const double* src = p.partial + (size_t)(item - 1) * p.ncta * kEntries;
-                    if constexpr (VARIANT == 2) {
-                        // per CTA and warp 8 sums of type R; lane: entry lane & 7, every
-                        // fourth (CTA, warp) slot from lane >> 3
-                        double sum = 0.0;
-                        for (int cw = lane >> 3; cw < p.ncta * NW; cw += 4) {
-                            using CS = std::conditional_t<COMP, double, R>;  // compensated: doubles
-                            const CS* row = (const CS*)(src + (size_t)(cw / NW) * kEntries);
-                            sum += (double)__ldcg(row + (cw % NW) * 8 + (lane & 7));
-                        }
-                        sum += __shfl_xor_sync(0xffffffffu, sum, 8);
-                        sum += __shfl_xor_sync(0xffffffffu, sum, 16);
-                        if (lane < 8) red[warp][lane] = sum;
-                    } else if (lane < 8) {
-                        double sum = 0.0;
-                        for (int c = 0; c < p.ncta; ++c) sum += __ldcg(src + (size_t)c * kEntries + lane);
-                        red[warp][lane] = sum;
-                    }
+                    if (lane < 8) red[warp][lane] = gram_take(p, item, lane);
                     __syncwarp();
                     const double* e = red[warp];
                     oo[0] = 2.0 * e[0] - 1.0;
@@ -2512,12 +2530,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                         s_mu2[warp][1][lane] = s_mu1[lane];
                     }
                 } else {
-                    const double* src = p.partial + (size_t)(item - 1) * p.ncta * kEntries;
-                    for (int e = lane; e < kEntries; e += 32) {
-                        double s = 0.0;
-                        for (int c = 0; c < p.ncta; ++c) s += __ldcg(src + (size_t)c * kEntries + e);
-                        red[warp][e] = s;
-                    }
+                    for (int e = lane; e < kEntries; e += 32) red[warp][e] = gram_take(p, item, e);
                     __syncwarp();
                     if (lane < kPairs) {
                         const bool diag = pair_j(lane) == pair_k(lane);
@@ -2687,8 +2700,8 @@ __global__ void __launch_bounds__(kThreads, 1) gfmc_team_engine(const TeamJob* _
 // Threads per CTA of the cluster engine: FP32 512 (one site per thread per
 // pass, twice the warps of the other engines to hide shared-memory latency),
 // FP64 256.
-// The compensated FP32 variant keeps 256 threads: its warps' 8 sums go to the
-// partial row as doubles.
+// The compensated FP32 variant keeps 256 threads (its (hi, lo) sums take more
+// registers).
 template <class R, bool COMP = false> constexpr int cluster_threads()
 {
     return sizeof(R) == 4 && !COMP ? 2 * kThreads : kThreads;

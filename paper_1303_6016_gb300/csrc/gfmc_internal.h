@@ -44,7 +44,7 @@ struct Params {
     double* cumw;     // [K]     C_k = sum_{j<=k} sin theta_j f(a cos theta_j)
 
     // per-update scratch
-    double* partial;  // [nsteps][ncta][kEntries]  per-CTA Gram partial sums
+    unsigned long long* gram;  // [nsteps][kEntries]  Gram sums over the CTAs, 64-bit fixed point
     double2* fftin;   // [4][M]  damped, twisted combined moments (zero beyond M)
     double2* gnode;   // [4][K]  G_V(w_k) for V = o, v, o+v, o+iv
     double* qpart;    // [ncta][2]  (phase-sum partial, max |increment|)

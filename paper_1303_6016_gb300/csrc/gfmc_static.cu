@@ -102,7 +102,7 @@ extern "C" gfmc_status gfmc_delta_omega_noalloc(int L, const double* d_spins, do
     const size_t o_fftw = take(sizeof(double2) * (M / 2));
     const size_t o_sinth = take(sizeof(double) * M);
     const size_t o_cumw = take(sizeof(double) * M);
-    const size_t o_partial = take(sizeof(double) * (size_t)nsteps * ncta * gfmc::kEntries);
+    const size_t o_gram = take(sizeof(unsigned long long) * (size_t)nsteps * gfmc::kEntries);
     const size_t o_fftin = take(sizeof(double2) * 4 * (size_t)M);
     const size_t o_gnode = take(sizeof(double2) * 4 * (size_t)M);
     const size_t o_qpart = take(sizeof(double) * 2 * ncta);
@@ -188,7 +188,7 @@ extern "C" gfmc_status gfmc_delta_omega_noalloc(int L, const double* d_spins, do
     P.fftw = (double2*)(b + o_fftw);
     P.sinth = (double*)(b + o_sinth);
     P.cumw = (double*)(b + o_cumw);
-    P.partial = (double*)(b + o_partial);
+    P.gram = (unsigned long long*)(b + o_gram);
     P.fftin = (double2*)(b + o_fftin);
     P.gnode = (double2*)(b + o_gnode);
     P.qpart = (double*)(b + o_qpart);
@@ -209,6 +209,8 @@ extern "C" gfmc_status gfmc_delta_omega_noalloc(int L, const double* d_spins, do
     if ((e = cudaMemcpyAsync(b + o_tiles, tiles, sizeof(int) * (ncta + 1), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(b + o_nptr, nptr, sizeof(int) * (ncta + 1), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (cnt > 0 && (e = cudaMemcpyAsync(b + o_nidx, nidx, sizeof(int) * cnt, cudaMemcpyHostToDevice, s)) != cudaSuccess) ||
+        (e = cudaMemsetAsync(P.gram, 0, sizeof(unsigned long long) * (size_t)nsteps * gfmc::kEntries, s)) !=
+            cudaSuccess ||
         (e = cudaMemsetAsync(P.flags, 0, sizeof(unsigned) * ncta, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(P.bar, 0, sizeof(unsigned) * 2, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(P.err, 0, sizeof(int) * 4, s)) != cudaSuccess)

@@ -29,7 +29,7 @@ ENGINES = {"auto": 0, "grid": 1, "vector_clusters": 2}
 
 # Names exported by libgfmc.so; include/gfmc.h declares exactly these.
 EXPORTS = ("gfmc_default_options", "gfmc_create", "gfmc_moments", "gfmc_delta_omega",
-           "gfmc_updates", "gfmc_sweep", "gfmc_get_spins", "gfmc_set_state", "gfmc_get_counter",
+           "gfmc_updates", "gfmc_sweep", "gfmc_get_spins", "gfmc_set_state", "gfmc_get_counter", "gfmc_device_bytes",
            "gfmc_set_wait_budget", "gfmc_inject_stall", "gfmc_last_error", "gfmc_destroy",
            "gfmc_delta_omega_noalloc", "gfmc_run_batch", "gfmc_run_clusters", "gfmc_cluster_min_ctas",
            "gfmc_plan_create", "gfmc_plan_launch", "gfmc_plan_sync", "gfmc_plan_destroy",
@@ -78,6 +78,7 @@ def load(path: str = LIB_PATH):
     L.gfmc_get_spins.argtypes = [vp, d]
     L.gfmc_set_state.argtypes = [vp, d, u64]
     L.gfmc_get_counter.argtypes = [vp, ctypes.POINTER(u64)]
+    L.gfmc_device_bytes.argtypes = [vp, ctypes.POINTER(u64)]
     L.gfmc_set_wait_budget.argtypes = [vp, i64]
     L.gfmc_inject_stall.argtypes = [vp, ctypes.c_int]
     L.gfmc_last_error.argtypes = [vp]
@@ -122,7 +123,7 @@ def load(path: str = LIB_PATH):
     L.gfmc_measure_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, d, vp]
     L.gfmc_measure_fma_peak.restype = ctypes.c_int
     for name in ("gfmc_create", "gfmc_moments", "gfmc_delta_omega", "gfmc_updates", "gfmc_sweep",
-                 "gfmc_get_spins", "gfmc_set_state", "gfmc_get_counter", "gfmc_set_wait_budget",
+                 "gfmc_get_spins", "gfmc_set_state", "gfmc_get_counter", "gfmc_device_bytes", "gfmc_set_wait_budget",
                  "gfmc_inject_stall"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -264,6 +265,13 @@ class Chain:
 
     def inject_stall(self, enable: bool = True):
         self._check(self._lib.gfmc_inject_stall(self._h, 1 if enable else 0))
+
+    @property
+    def device_bytes(self) -> int:
+        """Bytes of device memory the handle holds."""
+        b = ctypes.c_uint64(0)
+        self._check(self._lib.gfmc_device_bytes(self._h, ctypes.byref(b)))
+        return int(b.value)
 
     @property
     def counter(self) -> int:

@@ -55,13 +55,15 @@ def preferred_team(L: int, M: int = 1024, precision: str = "fp32_mixed") -> int:
     return 2
 
 
-def footprint(L: int, M: int, precision: str, ncta: int = 152) -> int:
-    """Device bytes of one chain (the allocations of gfmc_create)."""
+def footprint(L: int, M: int, precision: str) -> int:
+    """Device bytes of one chain before it is created (the allocations of
+    gfmc_create: spins and bonds, the two recursion buffers, the Gram sums
+    (M/2 - 1) x 112 x 8 bytes, moments and tables); once created, the chain's
+    own count (Chain.device_bytes) replaces the estimate."""
     N = L ** 3
     vec = 16 if precision == "fp64" else 8
-    ncta = max(1, min(ncta, N // 64))
-    return (16 * N + 36 * N + 14 * N * vec + (M // 2 - 1) * ncta * 112 * 8 + 49 * M * 16 + 200 * M
-            + 24 * 1024 + 3 * 1024 * 9)
+    return (16 * N + 36 * N + 14 * N * vec + (M // 2 - 1) * 112 * 8 + 49 * M * 16 + 200 * M
+            + 24 * 1024 + 3 * 1024 * 9 + 64 * 1024)
 
 
 def pool_specs(n: int = 24, seed: int = 5, Ls=range(8, 49), Ms=(512, 1024, 2048)):
@@ -111,7 +113,7 @@ class Scheduler:
         self.chains[c] = gfmc.Chain(sp["L"], inputs.uniform_sphere(sp["L"], 100 + c), M=sp["M"],
                                     precision=sp["precision"], beta=20.0, mu=-2.0, seed=1, chain_id=c,
                                     stream=0, recursion=self.recursion)
-        self.used += fb
+        self.used += self.chains[c].device_bytes
         return True
 
     def _slot_for(self, c):

@@ -56,9 +56,10 @@ def test_noalloc_matches_handle_entry_point_on_two_calls(lib):
         assert abs(got - ref) <= tol(ref), (o, got, ref)
 
 
-def test_noalloc_rejects_sizes_beyond_its_scratch(lib):
+@pytest.mark.parametrize("L,M", [(32, 1024), (22, 256)])
+def test_noalloc_rejects_sizes_beyond_its_scratch(lib, L, M):
+    """More CTAs of 256 sites than the scratch is laid out for (L = 22, 32)."""
     torch = pytest.importorskip("torch")
-    L, M = 32, 1024
     d_spins = torch.zeros((L ** 3, 2), dtype=torch.float64, device="cuda")
     d_out = torch.zeros(1, dtype=torch.float64, device="cuda")
     msg = ctypes.create_string_buffer(256)
@@ -76,10 +77,10 @@ def _call(lib, L, d_spins, M, o, th, ph, d_out, kernel=0, lam=0.0):
     return float(d_out.item())
 
 
-@pytest.mark.parametrize("L,M,kernel", [(8, 256, 0), (12, 1024, 0), (6, 128, 1)])
+@pytest.mark.parametrize("L,M,kernel", [(8, 256, 0), (12, 1024, 0), (20, 4096, 0), (6, 128, 1)])
 def test_noalloc_matches_the_oracle(lib, L, M, kernel):
-    """Against the oracle directly, at the largest accepted size (L = 12 with
-    M = 1024 fills most of the scratch) and with the Lorentz kernel."""
+    """Against the oracle directly, at the largest accepted size (L = 20 on
+    all 32 CTAs, with the largest M) and with the Lorentz kernel."""
     torch = pytest.importorskip("torch")
     sp = inputs.uniform_sphere(L, 7)
     d_spins = torch.tensor(sp, dtype=torch.float64, device="cuda")
