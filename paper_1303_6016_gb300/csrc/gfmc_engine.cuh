@@ -1394,7 +1394,7 @@ __device__ bool cluster_steps2(const Params& p, int rank, typename Cx<R>::T* vs,
     using B = BondSm<R>;
     constexpr int U = 1;
     cg::cluster_group cl = cg::this_cluster();
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int N = p.N, L = p.L, C = p.ncta, LL = L * L, T = N / C, P = L / C;
     // column walk when the threads share the columns evenly (whole columns when
     // LL is a multiple of NT, else NT / LL segments of P / nseg planes each) and

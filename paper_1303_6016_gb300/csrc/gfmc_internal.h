@@ -9,6 +9,28 @@
 
 namespace gfmc {
 
+// Let kernel fn take any dynamic shared memory the current device allows (its
+// opt-in maximum less fn's static shared memory).  The attribute is raised to
+// that bound and never set to a launch's own size, so its value does not
+// depend on the order of calls: a kernel node of a captured graph that is
+// launched again on its own (as a profiler replays graph nodes one by one) is
+// checked against the attribute as it stands then, and a per-launch setting
+// would have let a later, smaller launch or occupancy query lower it below
+// the node's size.
+inline cudaError_t allow_dynamic_smem(const void* fn)
+{
+    int dev = 0, optin = 0;
+    cudaFuncAttributes a;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess ||
+        (e = cudaFuncGetAttributes(&a, fn)) != cudaSuccess)
+        return e;
+    const int room = optin - (int)a.sharedSizeBytes;
+    if (a.maxDynamicSharedSizeBytes >= room) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, room);
+}
+
 constexpr int kThreads = 256;            // threads per CTA of the persistent engine
 constexpr int kWarps = kThreads / 32;
 constexpr int kVec = 7;                  // local vectors: o and its 6 neighbours

@@ -9,7 +9,7 @@ template <int NV, bool COMP>
 static cudaError_t launch_nv_f32(const Params& p, cudaStream_t s)
 {
     const int smem = engine_smem_bytes(p.K);
-    cudaError_t e = cudaFuncSetAttribute(gfmc_engine<float, NV, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_dynamic_smem((const void*)gfmc_engine<float, NV, COMP>);
     if (e != cudaSuccess) return e;
     Params q = p;
     void* args[] = {(void*)&q};
@@ -29,7 +29,7 @@ template <bool COMP>
 static cudaError_t max_ctas_f32(int K, int* out)
 {
     const int smem = engine_smem_bytes(K);
-    cudaError_t e = cudaFuncSetAttribute(gfmc_engine<float, kVec, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_dynamic_smem((const void*)gfmc_engine<float, kVec, COMP>);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gfmc_engine<float, kVec, COMP>, kThreads, smem);
@@ -51,7 +51,7 @@ template <bool COMP>
 static cudaError_t team_launch(const TeamJob* d_jobs, int njobs, int grid, int vec_bytes, int smem, cudaStream_t s,
                                bool ex)
 {
-    cudaError_t e = cudaFuncSetAttribute(gfmc_team_engine<float, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_dynamic_smem((const void*)gfmc_team_engine<float, COMP>);
     if (e != cudaSuccess) return e;
     if (!ex) {
         void* args[] = {(void*)&d_jobs, (void*)&njobs, (void*)&vec_bytes};
@@ -90,7 +90,7 @@ cudaError_t launch_team_ex_f32(const TeamJob* d_jobs, int njobs, int grid, int v
 template <bool COMP>
 static cudaError_t team_occupancy(int smem, int* out)
 {
-    cudaError_t e = cudaFuncSetAttribute(gfmc_team_engine<float, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_dynamic_smem((const void*)gfmc_team_engine<float, COMP>);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, gfmc_team_engine<float, COMP>, kThreads, smem);
 }
@@ -105,10 +105,9 @@ cudaError_t team_max_ctas_f32(int smem, int* out)
 }
 
 template <bool COMP>
-static cudaError_t cluster_config_f32(int C, int smem)
+static cudaError_t cluster_config_f32(int C)
 {
-    cudaError_t e = cudaFuncSetAttribute(gfmc_cluster_engine<float, COMP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         smem);
+    cudaError_t e = allow_dynamic_smem((const void*)gfmc_cluster_engine<float, COMP>);
     if (e == cudaSuccess && C > 8)
         e = cudaFuncSetAttribute(gfmc_cluster_engine<float, COMP>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     return e;
@@ -134,7 +133,7 @@ static cudaLaunchConfig_t cluster_cfg(int C, int njobs, int smem, cudaStream_t s
 template <bool COMP>
 static cudaError_t cluster_launch(const TeamJob* d_jobs, int njobs, int C, int vec_bytes, int smem, cudaStream_t s)
 {
-    cudaError_t e = cluster_config_f32<COMP>(C, smem);
+    cudaError_t e = cluster_config_f32<COMP>(C);
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = cluster_cfg<COMP>(C, njobs, smem, s, attr);
@@ -161,7 +160,7 @@ cudaError_t cluster_static_smem_f32(int* out)
 template <bool COMP>
 static cudaError_t cluster_active(int C, int smem, int* out)
 {
-    cudaError_t e = cluster_config_f32<COMP>(C, smem);
+    cudaError_t e = cluster_config_f32<COMP>(C);
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = cluster_cfg<COMP>(C, 1, smem, nullptr, attr);

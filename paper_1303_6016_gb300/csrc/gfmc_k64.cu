@@ -7,7 +7,7 @@ template <int NV>
 static cudaError_t launch_nv_f64(const Params& p, cudaStream_t s)
 {
     const int smem = single_smem_bytes(p.K, 0, p.prefetch ? p.win_max : 0);
-    cudaError_t e = cudaFuncSetAttribute(gfmc_engine<double, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_dynamic_smem((const void*)gfmc_engine<double, NV>);
     if (e != cudaSuccess) return e;
     Params q = p;
     void* args[] = {(void*)&q};
@@ -33,8 +33,7 @@ cudaError_t engine_static_smem_f64(int* out)
 cudaError_t engine_max_ctas_f64(int K, int* out)
 {
     const int smem = single_smem_bytes(K, 0);
-    cudaError_t e = cudaFuncSetAttribute(gfmc_engine<double>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_dynamic_smem((const void*)gfmc_engine<double>);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gfmc_engine<double>, engine_threads<double, kVec>(),
@@ -50,7 +49,7 @@ namespace gfmc {
 
 cudaError_t launch_team_f64(const TeamJob* d_jobs, int njobs, int grid, int vec_bytes, int smem, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(gfmc_team_engine<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_dynamic_smem((const void*)gfmc_team_engine<double>);
     if (e != cudaSuccess) return e;
     void* args[] = {(void*)&d_jobs, (void*)&njobs, (void*)&vec_bytes};
     return cudaLaunchCooperativeKernel((void*)gfmc_team_engine<double>, dim3(grid), dim3(kThreads), args, (size_t)smem, s);
@@ -60,7 +59,7 @@ cudaError_t launch_team_f64(const TeamJob* d_jobs, int njobs, int grid, int vec_
 // the form a CUDA graph captures as a cooperative kernel node.
 cudaError_t launch_team_ex_f64(const TeamJob* d_jobs, int njobs, int grid, int vec_bytes, int smem, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(gfmc_team_engine<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_dynamic_smem((const void*)gfmc_team_engine<double>);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
@@ -77,7 +76,7 @@ cudaError_t launch_team_ex_f64(const TeamJob* d_jobs, int njobs, int grid, int v
 
 cudaError_t team_max_ctas_f64(int smem, int* out)
 {
-    cudaError_t e = cudaFuncSetAttribute(gfmc_team_engine<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_dynamic_smem((const void*)gfmc_team_engine<double>);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, gfmc_team_engine<double>, kThreads, smem);
 }
@@ -86,9 +85,9 @@ cudaError_t team_max_ctas_f64(int smem, int* out)
 
 namespace gfmc {
 
-static cudaError_t cluster_config_f64(int C, int smem)
+static cudaError_t cluster_config_f64(int C)
 {
-    cudaError_t e = cudaFuncSetAttribute(gfmc_cluster_engine<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_dynamic_smem((const void*)gfmc_cluster_engine<double>);
     if (e == cudaSuccess && C > 8)
         e = cudaFuncSetAttribute(gfmc_cluster_engine<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     return e;
@@ -96,7 +95,7 @@ static cudaError_t cluster_config_f64(int C, int smem)
 
 cudaError_t launch_cluster_f64(const TeamJob* d_jobs, int njobs, int C, int vec_bytes, int smem, cudaStream_t s)
 {
-    cudaError_t e = cluster_config_f64(C, smem);
+    cudaError_t e = cluster_config_f64(C);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(C * njobs));
@@ -123,7 +122,7 @@ cudaError_t cluster_static_smem_f64(int* out)
 
 cudaError_t cluster_max_active_f64(int C, int smem, int* out)
 {
-    cudaError_t e = cluster_config_f64(C, smem);
+    cudaError_t e = cluster_config_f64(C);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)C);

@@ -7,9 +7,9 @@ namespace gfmc {
 namespace {
 int vc_smem(int K) { return kVcFixedSmem + K * (int)sizeof(double2); }
 
-cudaError_t vc_config(int K)
+cudaError_t vc_config()
 {
-    cudaError_t e = cudaFuncSetAttribute(gfmc_vc_engine, cudaFuncAttributeMaxDynamicSharedMemorySize, vc_smem(K));
+    cudaError_t e = allow_dynamic_smem((const void*)gfmc_vc_engine);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(gfmc_vc_engine, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     return e;
 }
@@ -34,7 +34,7 @@ cudaLaunchConfig_t vc_launch_config(int K, cudaStream_t s, cudaLaunchAttribute* 
 cudaError_t launch_vcluster_f32(const Params& p, cudaStream_t s)
 {
     if (p.L != kVcL) return cudaErrorInvalidValue;
-    cudaError_t e = vc_config(p.K);
+    cudaError_t e = vc_config();
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = vc_launch_config(p.K, s, attr);
@@ -43,7 +43,7 @@ cudaError_t launch_vcluster_f32(const Params& p, cudaStream_t s)
 
 cudaError_t vcluster_max_clusters(int K, int* out)
 {
-    cudaError_t e = vc_config(K);
+    cudaError_t e = vc_config();
     if (e != cudaSuccess) return e;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = vc_launch_config(K, nullptr, attr);

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kThreads, 1) gfmc_server_kernel(ServerArgs a)
 
 cudaError_t launch_server(const ServerArgs& a, int grid, int smem, cudaStream_t s)
 {
-    cudaError_t e = cudaFuncSetAttribute(gfmc_server_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_dynamic_smem((const void*)gfmc_server_kernel);
     if (e != cudaSuccess) return e;
     ServerArgs q = a;
     void* args[] = {(void*)&q};
@@ -132,7 +132,7 @@ cudaError_t launch_server(const ServerArgs& a, int grid, int smem, cudaStream_t 
 
 cudaError_t server_max_ctas(int smem, int* out)
 {
-    cudaError_t e = cudaFuncSetAttribute(gfmc_server_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_dynamic_smem((const void*)gfmc_server_kernel);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gfmc_server_kernel, kThreads, smem)) != cudaSuccess)
