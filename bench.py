@@ -85,7 +85,8 @@ def update_flop_nonzero(L: int, M: int) -> float:
 # only for the engine sources they were taken from: bench.py reports them as
 # roofline.traffic while the hash of those sources is unchanged, and null
 # otherwise.
-TRAFFIC_SOURCES = ("gfmc_engine.cuh", "gfmc_k64.cu", "gfmc_k32.cu", "gfmc_internal.h")
+TRAFFIC_SOURCES = ("gfmc_engine.cuh", "gfmc_k64.cu", "gfmc_k32.cu", "gfmc_internal.h", "gfmc_vcluster.cuh",
+                   "gfmc_kvc.cu")
 TRAFFIC_HASH = "83228e9edc9f11b6"
 TRAFFIC_PER_UPDATE = {"fp64": 40.983552e6, "fp32_mixed": 40.681472e6}
 

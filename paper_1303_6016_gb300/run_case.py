@@ -24,6 +24,8 @@ def main(argv=None):
     ap.add_argument("--mu", type=float, default=-2.0)
     ap.add_argument("--num-ctas", type=int, default=0)
     ap.add_argument("--recursion", default="unit_vectors", choices=sorted(gfmc.RECURSIONS))
+    ap.add_argument("--engine", default="auto", choices=sorted(gfmc.ENGINES))
+    ap.add_argument("--compensated", action="store_true")
     ap.add_argument("--team", type=int, default=0,
                     help="run the updates as a one-chain batch on a team of this many CTAs")
     ap.add_argument("--cluster", type=int, default=0,
@@ -32,7 +34,8 @@ def main(argv=None):
     build.build()
     sp = inputs.make(a.spins, a.L, seed=0 if a.spins != "vmf" else 2)
     with gfmc.Chain(a.L, sp, M=a.M, beta=a.beta, mu=a.mu, precision=a.precision,
-                    num_ctas=a.num_ctas, recursion=a.recursion) as ch:
+                    num_ctas=a.num_ctas, recursion=a.recursion, engine=a.engine,
+                    compensated=a.compensated) as ch:
         t0 = time.perf_counter()
         if a.cluster > 0:
             out = gfmc.run_clusters([ch], [a.updates], [a.cluster])[0]
