@@ -81,14 +81,17 @@ def update_flop_nonzero(L: int, M: int) -> float:
     return (M // 2 - 1) * L ** 3 * per
 
 
-# DRAM bytes per update of the engine kernels from one ncu capture each, valid
-# only for the engine sources they were taken from: bench.py reports them as
-# roofline.traffic while the hash of those sources is unchanged, and null
+# DRAM bytes (read + write) of one engine launch in the bench's launch
+# configuration (FP64: 16 updates; FP32-mixed: 64), each from one ncu capture
+# (`ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum` of run_case with
+# that many updates).  They hold only for the engine sources they were taken
+# from: bench.py reports them as roofline.traffic while the hash of those
+# sources is unchanged and the launch has that many updates, and null
 # otherwise.
 TRAFFIC_SOURCES = ("gfmc_engine.cuh", "gfmc_k64.cu", "gfmc_k32.cu", "gfmc_internal.h", "gfmc_vcluster.cuh",
                    "gfmc_kvc.cu")
-TRAFFIC_HASH = "83228e9edc9f11b6"
-TRAFFIC_PER_UPDATE = {"fp64": 40.983552e6, "fp32_mixed": 40.681472e6}
+TRAFFIC_HASH = "eec14ac4b8f6b648"
+TRAFFIC_PER_LAUNCH = {"fp64": (16, 7208704 + 4568320), "fp32_mixed": (64, 1158656 + 22272)}
 
 
 def engine_sources_hash() -> str:
@@ -105,7 +108,8 @@ def traffic_per_launch(precision: str, updates: int):
             return None
     except OSError:
         return None
-    return TRAFFIC_PER_UPDATE[precision] * updates
+    n, b = TRAFFIC_PER_LAUNCH[precision]
+    return float(b) if updates == n else None
 
 
 def load_peaks():
