@@ -596,7 +596,11 @@ def main():
                      "peak_source": "measured in this run: gfmc_measure_fma_peak (own kernel, 16 independent "
                                     "double fma chains per thread, 2 CTAs of 256 per SM, best of 3, CUDA events)",
                      "peak_derived": derived_tf,
-                     "peak_derived_source": "152 SMs x max SM clock x 2 FP64 FMA lanes per SM x 2 flop"},
+                     "peak_derived_source": "152 SMs x max SM clock x 2 FP64 FMA lanes per SM x 2 flop",
+                     "flop_s8d_per_update": (M // 2) * L ** 3 * 830,
+                     "frac_s8d": U * (M // 2) * L ** 3 * 830 / launch_s / 1e12 / peak_tf,
+                     "s8d_note": "the survey's per-update count (M/2) N 830 counts the products that vanish by "
+                                 "parity, which this engine does not execute; against it the fraction exceeds 1"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
         "clocks": clocks,
@@ -625,6 +629,20 @@ def main():
             "alu_tflops": Um * flop_m / launch_m / 1e12, "clocks": clocks_m,
             "gpu_launches": args.steps,
         }
+        if L == 32 and L % 2 == 0:
+            # the vector-cluster engine's bound: its per-step exchange between CTAs,
+            # measured alone (no arithmetic) in this run
+            floor = gfmc.cluster_exchange_cycles(steps=2000, repeats=3, stream=stream.cuda_stream)
+            mhz = (clocks_m or {}).get("sm_mhz") or 2070.0
+            step_cycles = launch_m / Um / (M - 1) * mhz * 1e6
+            line["fp32_mixed"]["exchange_floor"] = {
+                "cycles_per_step": floor, "engine_cycles_per_step": step_cycles,
+                "floor_over_step": floor / step_cycles,
+                "updates_per_s_at_floor": mhz * 1e6 / (floor * (M - 1)),
+                "note": "gfmc_measure_cluster_exchange: the engine's exchange pattern and volume (4 KB per CTA "
+                        "and step over st.async + mbarrier in 4x4 tori of 16 CTAs, 7 clusters) with no "
+                        "arithmetic; the engine takes M - 1 steps per update (moments read off the "
+                        "recursion), engine cycles per step include the update's tail"}
         chm.close()
 
     if not args.no_variant:

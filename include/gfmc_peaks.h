@@ -3,10 +3,11 @@
  * denominators of the GFMC engines (the paper has no counterpart: they time
  * the hardware, not the method).
  *
- * The FP64 single-chain engine is bound by the FP64 pipe and the FP32 stencil
- * engines by FP32 arithmetic and data movement, so a benchmark divides their
- * achieved rates by what the same GPU reaches on a plain stream of fused
- * multiply-adds.
+ * The FP64 single-chain engine is bound by the FP64 pipe, so a benchmark
+ * divides its achieved rate by what the same GPU reaches on a plain stream of
+ * fused multiply-adds.  The FP32 vector-cluster engine is bound by its
+ * per-step exchange between CTAs, whose cost without arithmetic is measured
+ * by the second call.
  */
 #ifndef GFMC_PEAKS_H
 #define GFMC_PEAKS_H
@@ -28,6 +29,26 @@ extern "C" {
  * milliseconds.  The call is synchronous.  GFMC_EINVAL for a bad precision or
  * repeats < 1, GFMC_ECUDA if a CUDA call fails. */
 gfmc_status gfmc_measure_fma_peak(int precision, int repeats, double* tflops, void* stream);
+
+/* The exchange of the FP32 vector-cluster engine alone, with no arithmetic:
+ * 7 clusters of 16 CTAs (256 threads each) in a 4 x 4 torus, where every step
+ * each CTA sends 1 KB to each of its 4 neighbours by st.async (complete_tx on
+ * the neighbour's mbarrier), waits for its own 4 KB (mbarrier try_wait,
+ * acquire, cluster scope) and re-arms the barrier between two CTA barriers --
+ * the pattern and volume of one step of that engine.  It is the floor of that
+ * engine's time per step.
+ *   steps            >= 2 steps per launch (the first is not timed).
+ *   cycles_per_step  host double, receives the SM clock cycles per step of the
+ *                    slowest CTA (clock64), the best of `repeats` launches.
+ *   repeats          >= 1.
+ *   stream           cudaStream_t (NULL: the legacy default stream).
+ * Every wait is bounded: a CTA whose wait runs out stops sending and the call
+ * returns GFMC_ETIMEOUT (no device fault); every CTA ends at a cluster barrier
+ * after a pause, so no CTA exits while a neighbour may still write into its
+ * shared memory.  The call is synchronous.  GFMC_EINVAL for steps < 2 or
+ * repeats < 1, GFMC_ECUDA if a CUDA call fails (for example a device that
+ * cannot hold 16-CTA clusters). */
+gfmc_status gfmc_measure_cluster_exchange(int steps, int repeats, double* cycles_per_step, void* stream);
 
 #ifdef __cplusplus
 }

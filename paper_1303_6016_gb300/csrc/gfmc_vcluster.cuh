@@ -199,35 +199,25 @@ __device__ __forceinline__ bool vc_step(const VcCtx& k, VcColumn& c, int b, unsi
     const VcPair* rb = k.rb;
     VcPair nx[2];
     // ---- every term that needs no halo ----
+    // The shared-memory loads of both pairs are issued first (a y-face row loads
+    // its own slot in place of the missing y-neighbour and does not use it), and
+    // each sum starts with the z-neighbours, which are in registers, so the FMAs
+    // run while the loads are in flight.
+    const int yup = fyp ? yl : yl + 1, ydn = fym ? yl : yl - 1;
+    VcPair vxp[2], vxm[2], vyp[2], vym[2];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-        const VcPair vxp = rb[vc_slot(G, q, yl, xp)], vxm = rb[vc_slot(G, q, yl, xm)];
+        vxp[q] = rb[vc_slot(G, q, yl, xp)];
+        vxm[q] = rb[vc_slot(G, q, yl, xm)];
+        vyp[q] = rb[vc_slot(G, q, yup, x)];
+        vym[q] = rb[vc_slot(G, q, ydn, x)];
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
         float2 P = make_float2(-c.V[G][q].re.x, -c.V[G][q].re.y), Q = make_float2(-c.V[G][q].im.x, -c.V[G][q].im.y);
         float2 S = make_float2(0.f, 0.f), W = make_float2(0.f, 0.f);
         const float2* hr = c.hr[G][q];
         const float2* hi = c.hi[G][q];
-        ff2(P, hr[0], vxp.re);
-        ff2(Q, hr[0], vxp.im);
-        ff2(S, hi[0], vxp.im);
-        ff2(W, hi[0], vxp.re);
-        ff2(P, hr[1], vxm.re);
-        ff2(Q, hr[1], vxm.im);
-        ff2(S, hi[1], vxm.im);
-        ff2(W, hi[1], vxm.re);
-        if (!fyp) {
-            const VcPair v = rb[vc_slot(G, q, yl + 1, x)];
-            ff2(P, hr[2], v.re);
-            ff2(Q, hr[2], v.im);
-            ff2(S, hi[2], v.im);
-            ff2(W, hi[2], v.re);
-        }
-        if (!fym) {
-            const VcPair v = rb[vc_slot(G, q, yl - 1, x)];
-            ff2(P, hr[3], v.re);
-            ff2(Q, hr[3], v.im);
-            ff2(S, hi[3], v.im);
-            ff2(W, hi[3], v.re);
-        }
         // z-neighbours on the other group of the column: planes zl +- 1 of the pair's
         // two sites (zl = G + 4q and G + 4q + 2); a plane outside the pencil is added
         // after the wait (zero here)
@@ -253,6 +243,26 @@ __device__ __forceinline__ bool vc_step(const VcCtx& k, VcColumn& c, int b, unsi
         ff2(Q, hr[5], zmi);
         ff2(S, hi[5], zmi);
         ff2(W, hi[5], zmr);
+        ff2(P, hr[0], vxp[q].re);
+        ff2(Q, hr[0], vxp[q].im);
+        ff2(S, hi[0], vxp[q].im);
+        ff2(W, hi[0], vxp[q].re);
+        ff2(P, hr[1], vxm[q].re);
+        ff2(Q, hr[1], vxm[q].im);
+        ff2(S, hi[1], vxm[q].im);
+        ff2(W, hi[1], vxm[q].re);
+        if (!fyp) {
+            ff2(P, hr[2], vyp[q].re);
+            ff2(Q, hr[2], vyp[q].im);
+            ff2(S, hi[2], vyp[q].im);
+            ff2(W, hi[2], vyp[q].re);
+        }
+        if (!fym) {
+            ff2(P, hr[3], vym[q].re);
+            ff2(Q, hr[3], vym[q].im);
+            ff2(S, hi[3], vym[q].im);
+            ff2(W, hi[3], vym[q].re);
+        }
         nx[q].re = __ffma2_rn(S, make_float2(-1.f, -1.f), P);
         nx[q].im = __fadd2_rn(Q, W);
     }

@@ -36,7 +36,7 @@ EXPORTS = ("gfmc_default_options", "gfmc_create", "gfmc_moments", "gfmc_delta_om
            "gfmc_server_create",
            "gfmc_server_submit",
            "gfmc_server_poll", "gfmc_server_last_error", "gfmc_server_destroy",
-           "gfmc_measure_fma_peak")
+           "gfmc_measure_fma_peak", "gfmc_measure_cluster_exchange")
 
 
 class GfmcError(RuntimeError):
@@ -122,6 +122,8 @@ def load(path: str = LIB_PATH):
     L.gfmc_server_destroy.restype = None
     L.gfmc_measure_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, d, vp]
     L.gfmc_measure_fma_peak.restype = ctypes.c_int
+    L.gfmc_measure_cluster_exchange.argtypes = [ctypes.c_int, ctypes.c_int, d, vp]
+    L.gfmc_measure_cluster_exchange.restype = ctypes.c_int
     for name in ("gfmc_create", "gfmc_moments", "gfmc_delta_omega", "gfmc_updates", "gfmc_sweep",
                  "gfmc_get_spins", "gfmc_set_state", "gfmc_get_counter", "gfmc_device_bytes", "gfmc_set_wait_budget",
                  "gfmc_inject_stall"):
@@ -287,6 +289,17 @@ def fma_peak_tflops(precision: str = "fp64", repeats: int = 3, stream=None) -> f
     st = lib.gfmc_measure_fma_peak(PRECISIONS[precision], int(repeats), _dp(out), stream)
     if st != GFMC_OK:
         raise GfmcError(st, "gfmc_measure_fma_peak failed")
+    return float(out[0])
+
+
+def cluster_exchange_cycles(steps: int = 2000, repeats: int = 3, stream=None) -> float:
+    """SM cycles per step of the FP32 vector-cluster engine's exchange alone
+    (gfmc_measure_cluster_exchange)."""
+    lib = load()
+    out = np.zeros(1)
+    st = lib.gfmc_measure_cluster_exchange(int(steps), int(repeats), _dp(out), stream)
+    if st != GFMC_OK:
+        raise GfmcError(st, "gfmc_measure_cluster_exchange failed")
     return float(out[0])
 
 
