@@ -292,6 +292,45 @@ __device__ __forceinline__ void cp_async_wait_all()
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
+// Bulk copies through the tensor memory accelerator (1-D form): `bytes` (a
+// multiple of 16; both addresses 16-byte aligned) from global to this CTA's
+// shared memory, completing as transactions on the CTA's mbarrier `mb`.
+__device__ __forceinline__ void bulk_g2s(void* smem, const void* gmem, unsigned bytes, unsigned mb)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(s),
+                 "l"(gmem), "r"(bytes), "r"(mb)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_init1(unsigned mb)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// the one arrival of the phase, with the bytes the phase's copies bring
+__device__ __forceinline__ void mbar_expect(unsigned mb, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(bytes) : "memory");
+}
+// bounded wait for the completion of the phase of the given parity (acquire,
+// CTA scope); false when `budget` cycles ran out
+__device__ __forceinline__ bool mbar_wait_parity(unsigned mb, unsigned parity, long long budget)
+{
+    const long long t0 = clock64();
+    while (true) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(mb), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > budget) return false;
+    }
+}
+
 // wait_neighbours for one warp: the lanes poll the neighbour CTAs' flags
 // (acquire) in parallel; true in every lane when all reached `target`, false
 // when an error was recorded or this warp's wait ran out of its budget.
@@ -1780,27 +1819,38 @@ __device__ __forceinline__ int bip_site_map(int s0, int s1, int L, int (&n)[2])
     return tid < 256 ? s_map[tid] : -1;
 }
 
-constexpr int kBipUnits = 28;
-constexpr int kBipGroups = 8;
+constexpr int kBipUnits = 25;
+constexpr int kBipGroups = 10;
 
-// The 28 Gram units that are not zero by parity, each over 8 site groups of
-// its staging range: [a0, a1) holds the sites with r_m of vector 0, [b0, b1)
-// those with r_m of vectors 1..6.  Rows of the staging area: v = r_m^v,
-// 7+v = r_{m+1}^v, 14+v = -i r_m^v, 21+v = -i r_{m+1}^v.  Units 0-5:
-// <r_m^0|r_{m+1}^k> (block 2, over a); 6-20: <r_m^j|r_m^k>, 1 <= j < k (over
-// b); 21: |r_m^0|^2 (over a); 22-27: |r_m^j|^2, j >= 1 (over b).
+// The Gram entries that are not zero by parity, as 25 units of one shape:
+// re = sum_s Re(conj(A_s) B_s), im = sum_s Re(conj(C_s) D_s) over kBipGroups
+// site groups of the unit's staging range (a: the sites with r_m of vector 0;
+// b: those with r_m of vectors 1..6), so that every thread of a warp runs the
+// same instruction stream (no divergent unit kinds).  Rows of the staging
+// area: v = r_m^v, 7+v = r_{m+1}^v, 14+v = -i r_m^v, 21+v = -i r_{m+1}^v, and
+// Re(conj(x)(-i y)) = Im(conj(x) y).
+//   units 0-5   <r_m^0|r_{m+1}^k>, k = u+1 (block 2, over a): A = C = r_m^0,
+//               B = r_{m+1}^k, D = -i r_{m+1}^k
+//   units 6-20  <r_m^j|r_m^k>, 1 <= j < k (over b): A = C = r_m^j, B = r_m^k,
+//               D = -i r_m^k
+//   units 21-23 |r_m^j|^2 and |r_m^{j+1}|^2 for j = 1, 3, 5 (over b): A = B =
+//               r_m^j, C = D = r_m^{j+1}; im is the next diagonal's real part
+//   unit 24     |r_m^0|^2 (over a): A = B = C = D = r_m^0; im lands in the
+//               imaginary slot of the (0, 0) entry, which is never read
+// gsum[g][kEntries] receives the group sums (at most kBipGroups rows).
 __device__ __forceinline__ void gram_units_bip(const double2* sr, int a0, int a1, int b0, int b1, double* gsum)
 {
     const int tid = threadIdx.x;
     if (tid >= kBipUnits * kBipGroups) return;
     const int u = tid % kBipUnits, g = tid / kBipUnits;
-    int rx = 0, ry = 0, rz = 0, ere, lo, hi;
-    bool offd = true;
+    int ra, rb, rc, rd, e1, e2, lo, hi;
     if (u < 6) {
         const int k = u + 1;
-        ry = kVec + k;
-        rz = 3 * kVec + k;
-        ere = 56 + 2 * pair_of(0, k);
+        ra = rc = 0;
+        rb = kVec + k;
+        rd = 3 * kVec + k;
+        e1 = 56 + 2 * pair_of(0, k);
+        e2 = e1 + 1;
         lo = a0;
         hi = a1;
     } else if (u < 21) {
@@ -1810,45 +1860,43 @@ __device__ __forceinline__ void gram_units_bip(const double2* sr, int a0, int a1
             ++j;
         }
         const int k = j + 1 + q;
-        rx = j;
-        ry = k;
-        rz = 2 * kVec + k;
-        ere = 2 * pair_of(j, k);
+        ra = rc = j;
+        rb = k;
+        rd = 2 * kVec + k;
+        e1 = 2 * pair_of(j, k);
+        e2 = e1 + 1;
+        lo = b0;
+        hi = b1;
+    } else if (u < 24) {
+        const int j = 2 * (u - 21) + 1;
+        ra = rb = j;
+        rc = rd = j + 1;
+        e1 = 2 * pair_of(j, j);
+        e2 = 2 * pair_of(j + 1, j + 1);
         lo = b0;
         hi = b1;
     } else {
-        const int j = u - 21;
-        rx = j;
-        offd = false;
-        ere = 2 * pair_of(j, j);
-        lo = j == 0 ? a0 : b0;
-        hi = j == 0 ? a1 : b1;
+        ra = rb = rc = rd = 0;
+        e1 = 2 * pair_of(0, 0);
+        e2 = e1 + 1;
+        lo = a0;
+        hi = a1;
     }
-    const double2* xs = sr + rx * kStage;
+    const double2 *as = sr + ra * kStage, *bs = sr + rb * kStage, *cs = sr + rc * kStage, *ds = sr + rd * kStage;
     double re = 0.0, im = 0.0;
-    if (offd) {
-        const double2* ys = sr + ry * kStage;
-        const double2* zs = sr + rz * kStage;
-        for (int s = lo + g; s < hi; s += kBipGroups) {
-            const double2 x = xs[s], y = ys[s], z = zs[s];
-            re = fma(x.x, y.x, re);
-            re = fma(x.y, y.y, re);
-            im = fma(x.x, z.x, im);
-            im = fma(x.y, z.y, im);
-        }
-    } else {
-        for (int s = lo + g; s < hi; s += kBipGroups) {
-            const double2 x = xs[s];
-            re = fma(x.x, x.x, re);
-            re = fma(x.y, x.y, re);
-        }
+    for (int s = lo + g; s < hi; s += kBipGroups) {
+        const double2 A = as[s], B = bs[s], C = cs[s], D = ds[s];
+        re = fma(A.x, B.x, re);
+        re = fma(A.y, B.y, re);
+        im = fma(C.x, D.x, im);
+        im = fma(C.y, D.y, im);
     }
     double* gs = gsum + g * kEntries;
-    gs[ere] = re;
-    gs[ere + 1] = im;
+    gs[e1] = re;
+    gs[e2] = im;
 }
 
-// Entry e of the CTA's Gram sums of step m = the 8 groups of gram_units_bip
+// Entry e of the CTA's Gram sums of step m = the kBipGroups groups of gram_units_bip
 // added in order, into the chain's sums; the entries that vanish by parity
 // add nothing (threads e < kEntries).
 __device__ __forceinline__ void gram_groups_bip(const double* gsum, const Params& p, int m)
@@ -1908,10 +1956,12 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                   "other block sizes: the cluster variant, and the FP64 single-chain engine's helper warp");
     static_assert(NT % 32 == 0 && NT >= kThreads, "whole warps, at least the default block");
     constexpr int NW = NT / 32;
-    // per warp: room for 112 Gram entries; the cluster variant only reduces 8 here
+    // per warp: room for 112 Gram entries; the cluster variant only reduces 8 here;
+    // the FP64 engine's bipartite Gram units use kBipGroups rows
     constexpr int kRed = VARIANT == 2 ? 8 : kEntries;
+    constexpr int kRedRows = (VARIANT == 0 && sizeof(R) == 8 && NT > kThreads && NW < kBipGroups) ? kBipGroups : NW;
     using R2 = typename Cx<R>::T;
-    __shared__ double red[NW][kRed];
+    __shared__ double red[kRedRows][kRed];
     __shared__ double2 s_mu2[NW][2][kPairs];
     __shared__ double2 s_mu1[kPairs];
     __shared__ double2 s_c[kVec];
@@ -1964,6 +2014,10 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
     R2* buf1 = buf0 + (size_t)NV * N;
     const long long nupd = (p.mode == MODE_SWEEP) ? p.n_updates : 1;
     unsigned phase = 0;
+    // FP64 engine with prefetch: the mbarrier its bulk copies complete on, and the
+    // parity of the phase each thread waits for next
+    __shared__ __align__(8) unsigned long long s_pfbar;
+    [[maybe_unused]] unsigned pf_par = 0;
     long long nmag = 0;
     unsigned long long nacc = 0;
 
@@ -2194,8 +2248,11 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 // the Gram sums of step m, so neither the release nor the poll is on the
                 // FP64 pipe's critical path.
                 __shared__ int s_go;
+                const unsigned pfb = (unsigned)__cvta_generic_to_shared(&s_pfbar);
                 if (warp == kWarps) {
                     bool ok = true;
+                    if (q == 0 && lane == 0 && p.prefetch) mbar_init1(pfb);
+                    __syncwarp();
                     for (int m = 1; m <= p.nsteps + 1 && ok; ++m) {
                         if (m > 1) {
                             nbar_sync(2, NT);
@@ -2205,23 +2262,37 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                         if (m <= p.nsteps) {
                             ok = warp_wait_neighbours(p, cta, phase + (unsigned)m, 100 + m, lane);
                             if (ok && p.prefetch) {
-                                // r_m of every site the stencil of step m reads, into shared memory
+                                // r_m of every site the stencil of step m reads, into shared memory:
+                                // one bulk copy per run of sites and vector, all completing on one
+                                // mbarrier.  The proxy fence orders the neighbours' stores of r_m
+                                // (acquired above) and this CTA's reads of the last copy (before
+                                // barrier 2) with the copies.
                                 __syncwarp();
-                                const R2* src = (m & 1) ? buf1 : buf0;
-                                double2* wsm = dyn + 4 * kVec * kStage;
-                                const int wb = p.win_ptr[cta], we = p.win_ptr[cta + 1], W = p.win_max;
-                                int off = 0;
-                                for (int w = wb; w < we; ++w) {
-                                    const int2 r = p.win[w];
-                                    for (int v = 0; v < kVec; ++v) {
-                                        const R2* sv = src + (size_t)v * N + r.x;
-                                        double2* dv = wsm + v * W + off;
-                                        for (int c = lane; c < r.y; c += 32) cp_async16(dv + c, sv + c);
+                                if (lane == 0) {
+                                    const R2* src = (m & 1) ? buf1 : buf0;
+                                    double2* wsm = dyn + 4 * kVec * kStage;
+                                    const int wb = p.win_ptr[cta], we = p.win_ptr[cta + 1], W = p.win_max;
+                                    unsigned bytes = 0;
+                                    for (int w = wb; w < we; ++w) bytes += (unsigned)p.win[w].y * (unsigned)(kVec * sizeof(R2));
+                                    asm volatile("fence.proxy.async;" ::: "memory");
+                                    mbar_expect(pfb, bytes);
+                                    int off = 0;
+                                    for (int w = wb; w < we; ++w) {
+                                        const int2 r = p.win[w];
+                                        if (r.y > 0)
+                                            for (int v = 0; v < kVec; ++v)
+                                                bulk_g2s(wsm + v * W + off, src + (size_t)v * N + r.x,
+                                                         (unsigned)r.y * (unsigned)sizeof(R2), pfb);
+                                        off += r.y;
                                     }
-                                    off += r.y;
                                 }
-                                cp_async_wait_all();
                                 __syncwarp();
+                                ok = mbar_wait_parity(pfb, pf_par, p.budget);
+                                pf_par ^= 1u;
+                                if (__any_sync(0xffffffffu, !ok)) {
+                                    ok = false;
+                                    if (lane == 0) set_error(p, ERR_TIMEOUT, 95, m);
+                                }
                             }
                             if (lane == 0) s_go = ok ? 1 : 0;
                             nbar_arrive(3, NT);
@@ -2242,6 +2313,12 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                         // barrier 3 also ends every compute warp's Gram units of step m-1
                         nbar_sync(3, NT);
                         if (!s_go) return;
+                        if (p.prefetch) {
+                            // the helper saw the copies complete; each thread observes the
+                            // completed phase itself (acquire) before reading the copies
+                            if (!mbar_wait_parity(pfb, pf_par, p.budget)) return;
+                            pf_par ^= 1u;
+                        }
                         if (m >= 2)
                             gram_groups_bip(&red[0][0], p, m - 1);
                         const R2* rd = (m & 1) ? buf1 : buf0;  // r_m of every site
@@ -2305,6 +2382,12 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                         // barrier 3 also ends every compute warp's Gram units of step m-1
                         nbar_sync(3, NT);
                         if (!s_go) return;
+                        if (p.prefetch) {
+                            // the helper saw the copies complete; each thread observes the
+                            // completed phase itself (acquire) before reading the copies
+                            if (!mbar_wait_parity(pfb, pf_par, p.budget)) return;
+                            pf_par ^= 1u;
+                        }
                         if (m >= 2)
                             gram_groups_f64(&red[0][0], p, m - 1);
                         const R2* rd = (m & 1) ? buf1 : buf0;  // r_m of every site
