@@ -1883,9 +1883,11 @@ __device__ __forceinline__ void gram_units_bip(const double2* sr, int a0, int a1
         hi = a1;
     }
     const double2 *as = sr + ra * kStage, *bs = sr + rb * kStage, *cs = sr + rc * kStage, *ds = sr + rd * kStage;
+    const bool c_is_a = rc == ra;  // units 0-20 and 24: C is row A, loaded once
     double re = 0.0, im = 0.0;
     for (int s = lo + g; s < hi; s += kBipGroups) {
-        const double2 A = as[s], B = bs[s], C = cs[s], D = ds[s];
+        const double2 A = as[s], B = bs[s], D = ds[s];
+        const double2 C = c_is_a ? A : cs[s];
         re = fma(A.x, B.x, re);
         re = fma(A.y, B.y, re);
         im = fma(C.x, D.x, im);
@@ -2319,8 +2321,6 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                             if (!mbar_wait_parity(pfb, pf_par, p.budget)) return;
                             pf_par ^= 1u;
                         }
-                        if (m >= 2)
-                            gram_groups_bip(&red[0][0], p, m - 1);
                         const R2* rd = (m & 1) ? buf1 : buf0;  // r_m of every site
                         R2* wr = (m & 1) ? buf0 : buf1;        // receives r_{m+1}; held r_{m-1}
                         const int pa = (par_o + m) & 1;        // parity of the sites holding r_m^0
@@ -2366,6 +2366,11 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                             }
                         }
                         nbar_arrive(2, NT);
+                        // the group sums of step m-1 (their units ended at barrier 3), after the
+                        // stencil so that their dependent additions do not delay its FMAs; the
+                        // units of step m overwrite red only after barrier 1
+                        if (m >= 2)
+                            gram_groups_bip(&red[0][0], p, m - 1);
                         nbar_sync(1, kThreads);
                         const int a0 = pa * 128, b0 = (1 - pa) * 128;
                         gram_units_bip(dyn, a0, a0 + bip_n[pa], b0, b0 + bip_n[1 - pa], &red[0][0]);
