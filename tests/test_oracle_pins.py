@@ -520,6 +520,31 @@ def test_magnetization_limits():
     assert O.magnetization(8, inputs.uniform_sphere(8, 0)) < 0.1
 
 
+def test_grand_potential_limits_and_particle_number():
+    """Pins of Omega(beta, mu) = -(1/beta) sum ln(1 + e^{-beta(e - mu)}) that do
+    not restate it: the zero-temperature limit sum_{e < mu} (e - mu) (error at
+    most n ln2 / beta), the high-temperature expansion of ln(1 + e^x) =
+    ln 2 + x/2 + x^2/8 + O(x^4), and -dOmega/dmu = N = sum of Fermi factors."""
+    rng = np.random.default_rng(3)
+    e = np.sort(rng.uniform(-6.0, 6.0, 40))
+    mu = -0.7
+    # T -> 0: the occupied levels' e - mu
+    for beta in (1e3, 1e5):
+        om = O.grand_potential(e, beta, mu)
+        assert abs(om - np.sum(np.minimum(e - mu, 0.0))) <= len(e) * np.log(2.0) / beta
+    # T -> infinity: -(1/beta) (n ln2 + sum x/2 + sum x^2/8), x = -beta (e - mu)
+    beta = 1e-3
+    x = -beta * (e - mu)
+    hot = -(len(e) * np.log(2.0) + x.sum() / 2 + (x ** 2).sum() / 8) / beta
+    assert O.grand_potential(e, beta, mu) == pytest.approx(hot, abs=len(e) * np.max(np.abs(x)) ** 4 / beta)
+    # particle number: centred difference in mu against the Fermi sum
+    for beta in (0.5, 5.0, 20.0):
+        h = 1e-5
+        n_fd = -(O.grand_potential(e, beta, mu + h) - O.grand_potential(e, beta, mu - h)) / (2 * h)
+        fermi = np.sum(1.0 / (1.0 + np.exp(beta * (e - mu))))
+        assert n_fd == pytest.approx(fermi, rel=1e-7, abs=1e-7)
+
+
 def test_grand_potential_matches_definition():
     e = np.linspace(-5, 5, 11)
     for beta in (0.5, 20.0, 200.0):
