@@ -531,6 +531,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-variant", action="store_true")
+    ap.add_argument("--no-l16", action="store_true", help="skip the single-chain L=16 leg")
     ap.add_argument("--no-graph", action="store_true",
                     help="skip the CUDA-graph replays of the batch steps")
     ap.add_argument("--batch-updates", type=int, default=4)
@@ -644,6 +645,23 @@ def main():
                         "arithmetic; the engine takes M - 1 steps per update (moments read off the "
                         "recursion), engine cycles per step include the update's tail"}
         chm.close()
+
+    if not args.no_l16:
+        # the single-chain workload's smaller lattice: L=16 (N=4096), same M, both precisions
+        L16, spins16 = 16, inputs.uniform_sphere(16, 0)
+        l16 = {"L": L16, "M": M, "note": "single chain, uniform spins (seed 0), M=1024; the FP32-mixed chain "
+                                          "runs the grid engine (the vector-cluster engine is for L=32)"}
+        for prec, u16 in (("fp64", 64), ("fp32_mixed", 64)):
+            c16 = gfmc.Chain(L16, spins16, M=M, beta=20.0, mu=-2.0, seed=1, chain_id=rank, precision=prec,
+                             stream=stream.cuda_stream)
+            per16, _ = time_device(c16, stream, u16, max(3, args.steps // 2), args.warmup, flush, dist)
+            c16.close()
+            tot16 = max_over_ranks(dist, sum(per16))
+            _, b16 = update_work(L16, M, 8 if prec == "fp64" else 4)
+            l16[prec] = {"value": aggregate(world, max(3, args.steps // 2), u16, tot16), "unit": UNIT,
+                         "updates_per_step": u16, "ms_per_update": statistics.mean(per16) / u16,
+                         "stencil_gbs": u16 * b16 / (statistics.mean(per16) / 1000.0) / 1e9}
+        line["single_chain_L16"] = l16
 
     if not args.no_variant:
         # the paper's recursion on the proposal's vectors (o, v; o+v and o+iv by linearity)
