@@ -1786,7 +1786,9 @@ __device__ __forceinline__ void magnetisation_partial(const Params& p, int s0, i
 // of the tile, tid in [128, 256) the (tid - 128)-th odd one; -1 if none (and
 // for the threads beyond 256).  n[c] receives the count of parity c.  Every
 // thread of the block calls it.
-__device__ __forceinline__ int bip_site_map(int s0, int s1, int L, int (&n)[2])
+// small: every class of the tile has at most 32 sites; the class's four warps
+// then all take its sites (lane l: the class's l-th site) and split the vectors.
+__device__ __forceinline__ int bip_site_map(int s0, int s1, int L, int (&n)[2], bool small)
 {
     __shared__ int s_map[256];
     __shared__ int s_cnt[2][8];
@@ -1816,7 +1818,7 @@ __device__ __forceinline__ int bip_site_map(int s0, int s1, int L, int (&n)[2])
         n[1] += s_cnt[1][w];
     }
     __syncthreads();
-    return tid < 256 ? s_map[tid] : -1;
+    return tid < 256 ? s_map[small ? (tid & 128) + lane : tid] : -1;
 }
 
 constexpr int kBipUnits = 25;
@@ -1948,7 +1950,8 @@ template <int VARIANT> __device__ __forceinline__ bool chain_barrier(const Param
 // WIDE: the team variant's FP32 paths take two sites per thread per pass (more
 // registers); the server kernel, which holds every instantiation in one kernel,
 // takes one.
-template <class R, int VARIANT, int NV = kVec, int NT = kThreads, bool WIDE = true, bool COMP = false>
+template <class R, int VARIANT, int NV = kVec, int NT = kThreads, bool WIDE = true, bool COMP = false,
+          bool SMALL = false>
 __device__ __forceinline__ void run_chain(const Params& p, const int cta, double2* dyn,
                                           typename Cx<R>::T* vec_smem)
 {
@@ -1983,7 +1986,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
     [[maybe_unused]] int bip_n[2] = {0, 0};
     if constexpr (VARIANT == 0 && sizeof(R) == 8 && NT > kThreads) {
         if (p.bip) {
-            i = bip_site_map(s0, s1, p.L, bip_n);
+            i = bip_site_map(s0, s1, p.L, bip_n, SMALL);
             active = i >= 0;
         }
     }
@@ -2309,6 +2312,8 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                     const int o0 = s_loc[0];
                     const int par_o = (o0 % L + (o0 / L) % L + o0 / (L * L)) & 1;
                     const int cls = tid >= 128 ? 1 : 0;
+                    const int wq = warp & 3;                               // the warp within its class
+                    const int ps = SMALL ? (tid & 128) + lane : tid;  // staging position
                     const double2* wsm = dyn + 4 * kVec * kStage;
                     const int W = p.win_max;
                     for (int m = 1; m <= p.nsteps; ++m) {
@@ -2317,8 +2322,11 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                         if (!s_go) return;
                         if (p.prefetch) {
                             // the helper saw the copies complete; each thread observes the
-                            // completed phase itself (acquire) before reading the copies
-                            if (!mbar_wait_parity(pfb, pf_par, p.budget)) return;
+                            // completed phase itself (acquire) before reading the copies.  The
+                            // phase is complete, so this returns at once; were it ever to run out,
+                            // the thread records it and stays in step with the others (leaving
+                            // alone would strand the helper at its next named barrier)
+                            if (!mbar_wait_parity(pfb, pf_par, p.budget)) set_error(p, ERR_TIMEOUT, 96, m);
                             pf_par ^= 1u;
                         }
                         const R2* rd = (m & 1) ? buf1 : buf0;  // r_m of every site
@@ -2343,26 +2351,77 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                                 nxt[v] = acc;
                                 if (m < p.nsteps) stcg2(wr + (size_t)v * N + i, acc);
                             };
-                            if (holds0) {
-    #pragma unroll
-                                for (int v = 1; v < kVec; ++v) adv(v);
+                            if constexpr (SMALL) {
+                                // small tiles: the class's four warps share its sites and split
+                                // the vectors, heavy {1,2} {3,4} {5} {6}, light 0 on the fourth,
+                                // so the stencil runs on all four sub-partitions' FP64 pipes
+                                if (holds0) {
+                                    if (wq == 0) {
+                                        adv(1);
+                                        adv(2);
+                                    } else if (wq == 1) {
+                                        adv(3);
+                                        adv(4);
+                                    } else if (wq == 2) {
+                                        adv(5);
+                                    } else {
+                                        adv(6);
+                                    }
+                                } else if (wq == 3) {
+                                    adv(0);
+                                }
                             } else {
-                                adv(0);
+                                if (holds0) {
+    #pragma unroll
+                                    for (int v = 1; v < kVec; ++v) adv(v);
+                                } else {
+                                    adv(0);
+                                }
                             }
                         }
-                        // stage the rows the units of this thread's class read
-                        if (holds0) {
-                            dyn[tid] = cur[0];
-    #pragma unroll
-                            for (int v = 1; v < kVec; ++v) {
-                                dyn[(kVec + v) * kStage + tid] = nxt[v];
-                                dyn[(3 * kVec + v) * kStage + tid] = minus_i(nxt[v]);
+                        // stage the rows the units of this thread's class read (small tiles:
+                        // each warp the rows of its own vectors, at its lane's position)
+                        auto stage_next = [&](int v) {
+                            dyn[(kVec + v) * kStage + ps] = nxt[v];
+                            dyn[(3 * kVec + v) * kStage + ps] = minus_i(nxt[v]);
+                        };
+                        auto stage_cur = [&](int v) {
+                            dyn[v * kStage + ps] = cur[v];
+                            dyn[(2 * kVec + v) * kStage + ps] = minus_i(cur[v]);
+                        };
+                        if constexpr (SMALL) {
+                            if (holds0 && wq == 3) dyn[ps] = cur[0];
+                            if (wq == 0) {
+                                if (holds0) {
+                                    stage_next(1);
+                                    stage_next(2);
+                                } else {
+                                    stage_cur(1);
+                                    stage_cur(2);
+                                }
+                            } else if (wq == 1) {
+                                if (holds0) {
+                                    stage_next(3);
+                                    stage_next(4);
+                                } else {
+                                    stage_cur(3);
+                                    stage_cur(4);
+                                }
+                            } else if (wq == 2) {
+                                if (holds0) stage_next(5);
+                                else stage_cur(5);
+                            } else {
+                                if (holds0) stage_next(6);
+                                else stage_cur(6);
                             }
                         } else {
+                            if (holds0) {
+                                dyn[ps] = cur[0];
     #pragma unroll
-                            for (int v = 1; v < kVec; ++v) {
-                                dyn[v * kStage + tid] = cur[v];
-                                dyn[(2 * kVec + v) * kStage + tid] = minus_i(cur[v]);
+                                for (int v = 1; v < kVec; ++v) stage_next(v);
+                            } else {
+    #pragma unroll
+                                for (int v = 1; v < kVec; ++v) stage_cur(v);
                             }
                         }
                         nbar_arrive(2, NT);
@@ -2389,8 +2448,11 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                         if (!s_go) return;
                         if (p.prefetch) {
                             // the helper saw the copies complete; each thread observes the
-                            // completed phase itself (acquire) before reading the copies
-                            if (!mbar_wait_parity(pfb, pf_par, p.budget)) return;
+                            // completed phase itself (acquire) before reading the copies.  The
+                            // phase is complete, so this returns at once; were it ever to run out,
+                            // the thread records it and stays in step with the others (leaving
+                            // alone would strand the helper at its next named barrier)
+                            if (!mbar_wait_parity(pfb, pf_par, p.budget)) set_error(p, ERR_TIMEOUT, 96, m);
                             pf_par ^= 1u;
                         }
                         if (m >= 2)
@@ -2716,11 +2778,13 @@ template <class R, int NV> constexpr int engine_threads()
 
 // A single chain spread over the whole GPU.  COMP (FP32 only): compensated
 // Gram dot products.
-template <class R, int NV = kVec, bool COMP = false>
+// SMALL (FP64, 7 vectors, bipartite tiles whose parity classes have at most 32
+// sites): the instantiation whose class warps split the vectors.
+template <class R, int NV = kVec, bool COMP = false, bool SMALL = false>
 __global__ void __launch_bounds__(engine_threads<R, NV>(), 1) gfmc_engine(const Params p)
 {
     extern __shared__ double2 dyn[];
-    run_chain<R, 0, NV, engine_threads<R, NV>(), true, COMP>(p, blockIdx.x, dyn, nullptr);
+    run_chain<R, 0, NV, engine_threads<R, NV>(), true, COMP, SMALL>(p, blockIdx.x, dyn, nullptr);
 }
 
 // A batch of chains, each on its own team of CTAs (jobs sorted by cta0).

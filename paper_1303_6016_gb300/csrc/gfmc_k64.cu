@@ -3,30 +3,36 @@
 
 namespace gfmc {
 
-template <int NV>
+template <int NV, bool SMALL = false>
 static cudaError_t launch_nv_f64(const Params& p, cudaStream_t s)
 {
     const int smem = single_smem_bytes(p.K, 0, p.prefetch ? p.win_max : 0);
-    cudaError_t e = allow_dynamic_smem((const void*)gfmc_engine<double, NV>);
+    cudaError_t e = allow_dynamic_smem((const void*)gfmc_engine<double, NV, false, SMALL>);
     if (e != cudaSuccess) return e;
     Params q = p;
     void* args[] = {(void*)&q};
-    return cudaLaunchCooperativeKernel((void*)gfmc_engine<double, NV>, dim3(p.ncta),
+    return cudaLaunchCooperativeKernel((void*)gfmc_engine<double, NV, false, SMALL>, dim3(p.ncta),
                                        dim3(engine_threads<double, NV>()), args, (size_t)smem, s);
 }
 
-cudaError_t launch_engine_f64(const Params& p, cudaStream_t s) { return launch_nv_f64<kVec>(p, s); }
+// p.bip == 2: the small-tile instantiation (the class warps split the vectors)
+cudaError_t launch_engine_f64(const Params& p, cudaStream_t s)
+{
+    return p.bip == 2 ? launch_nv_f64<kVec, true>(p, s) : launch_nv_f64<kVec>(p, s);
+}
 
 cudaError_t launch_engine_f64(const Params& p, int nv, cudaStream_t s)
 {
-    return nv == 2 ? launch_nv_f64<2>(p, s) : launch_nv_f64<kVec>(p, s);
+    return nv == 2 ? launch_nv_f64<2>(p, s) : launch_engine_f64(p, s);
 }
 
 cudaError_t engine_static_smem_f64(int* out)
 {
-    cudaFuncAttributes a;
-    const cudaError_t e = cudaFuncGetAttributes(&a, gfmc_engine<double, kVec>);
-    if (e == cudaSuccess) *out = (int)a.sharedSizeBytes;
+    // the larger of the two 7-vector instantiations, so one fit check covers both
+    cudaFuncAttributes a, b;
+    cudaError_t e = cudaFuncGetAttributes(&a, gfmc_engine<double, kVec>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&b, gfmc_engine<double, kVec, false, true>);
+    if (e == cudaSuccess) *out = (int)(a.sharedSizeBytes > b.sharedSizeBytes ? a.sharedSizeBytes : b.sharedSizeBytes);
     return e;
 }
 
