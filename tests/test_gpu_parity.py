@@ -353,8 +353,13 @@ def test_lorentz_sweep_matches_oracle(G):
 # sites or more)
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("L,ncta", [(20, 0), (10, 7), (24, 152), (9, 5), (16, 17)])
+@pytest.mark.parametrize("L,ncta", [(20, 0), (10, 7), (24, 152), (9, 5), (16, 17), (16, 0), (20, 152), (14, 0)])
 def test_fp64_tile_layouts_match_oracle(G, L, ncta):
+    """Tile layouts of the FP64 engine: odd L (no bipartite step), bipartite
+    tiles, and the small-tile instantiation where every parity class fits one
+    warp and the class's four warps split the vectors -- (20, 0), (16, 0):
+    64-site tiles; (20, 152): ragged 52/53-site tiles; (14, 0): 65-site tiles,
+    one site past the small-tile bound."""
     M = 64
     sp = inputs.uniform_sphere(L, 40 + L)
     with chain(G, L, sp, M, num_ctas=ncta, seed=3) as ch:
