@@ -1984,7 +1984,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
     int i = s0 + tid;
     bool active = VARIANT == 0 && i < s1;
     [[maybe_unused]] int bip_n[2] = {0, 0};
-    if constexpr (VARIANT == 0 && sizeof(R) == 8 && NT > kThreads) {
+    if constexpr (VARIANT == 0 && sizeof(R) == 8 && (NT > kThreads || NV == 2)) {
         if (p.bip) {
             i = bip_site_map(s0, s1, p.L, bip_n, SMALL);
             active = i >= 0;
@@ -2122,7 +2122,17 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
             // With every tile within 7 warps (p.helper7), warp 7 has no site: it publishes
             // the CTA's flag after the stencil (named barrier 2) and polls the neighbours'
             // flags of the next step (named barrier 3) while warps 0-6 form the sums.
-            const bool helper = p.helper7 != 0;
+            // FP64 on a bipartite lattice (p.bip): r_m^o and r_m^v live on opposite site
+            // parities, so a site advances one of them per step -- o where r_{m+1}^o
+            // lives, v on the other parity -- and of the 8 products only |r_m^o|^2 and
+            // <r_m^o|r_{m+1}^v> (at the sites of r_m^o) and |r_m^v|^2 are not zero by
+            // parity; warps 0-3 hold the even sites, 4-7 the odd ones, so each warp runs
+            // one branch (all 8 warps hold sites, so warp 7 is no flag helper then)
+            bool bipm = false;
+            if constexpr (sizeof(R) == 8 && !COMP) bipm = p.bip != 0;
+            const int cls = tid >= 128 ? 1 : 0;
+            const int par_o = (s_loc[0] % L + (s_loc[0] / L) % L + s_loc[0] / (L * L)) & 1;
+            const bool helper = p.helper7 != 0 && !bipm;
             __shared__ int s_go2;
             if (helper && warp == kWarps - 1) {
                 for (int e = lane; e < 16; e += 32) w8[e >> 3][kWarps - 1][e & 7] = W8T{};
@@ -2151,15 +2161,46 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 const R2* rd = (m & 1) ? buf1 : buf0;
                 R2* wr = (m & 1) ? buf0 : buf1;
                 R2 nv[2][6];
+                // bipartite: this site receives r_{m+1}^o (adv_v = 0) or r_{m+1}^v (adv_v = 1)
+                const int adv_v = (cls == ((par_o + m + 1) & 1)) ? 0 : 1;
                 if (active) {
+                    if (bipm) {
+                        if (adv_v == 0) {
 #pragma unroll
-                    for (int v = 0; v < 2; ++v)
+                            for (int d = 0; d < 6; ++d) nv[0][d] = ldcg2(rd + nb[d]);
+                        } else {
 #pragma unroll
-                        for (int d = 0; d < 6; ++d) nv[v][d] = ldcg2(rd + (size_t)v * N + nb[d]);
+                            for (int d = 0; d < 6; ++d) nv[1][d] = ldcg2(rd + (size_t)N + nb[d]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < 2; ++v)
+#pragma unroll
+                            for (int d = 0; d < 6; ++d) nv[v][d] = ldcg2(rd + (size_t)v * N + nb[d]);
+                    }
                 }
                 if (m >= 2) flush8(m - 1);
                 R2 nxt[2];
-                if (active) {
+                if (active && bipm) {
+                    if constexpr (sizeof(R) == 8) {
+                        // one recursion per site; the other vector is zero here at m - 1, m + 1
+                        // and is neither formed nor stored (nothing reads it)
+                        auto adv1 = [&](int v) {
+                            R2 acc = c_make<R2>(-prv[v].x, -prv[v].y);
+#pragma unroll
+                            for (int d = 0; d < 6; ++d) c_fma(acc, h[d], nv[v][d]);
+                            if (m < p.nsteps) stcg2(wr + (size_t)v * N + i, acc);
+                            return acc;
+                        };
+                        if (adv_v == 0) {
+                            nxt[0] = adv1(0);
+                            nxt[1] = c_make<R2>(0, 0);
+                        } else {
+                            nxt[0] = c_make<R2>(0, 0);
+                            nxt[1] = adv1(1);
+                        }
+                    }
+                } else if (active) {
 #pragma unroll
                     for (int v = 0; v < 2; ++v) {
                         if constexpr (sizeof(R) == 8) {
@@ -2189,6 +2230,17 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                     if ((lane & 3) == 0) w8[m & 1][warp][lane >> 2] = make_float2(s8.hi, s8.lo);
                 } else {
                 R v8[8];
+                if (bipm) {
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) v8[e] = (R)0;
+                    if (adv_v == 1) {  // the sites of r_m^o, which receive r_{m+1}^v
+                        v8[0] = fma(a.x, a.x, a.y * a.y);
+                        v8[6] = fma(a.x, nbv.x, a.y * nbv.y);
+                        v8[7] = fma(a.x, nbv.y, -(a.y * nbv.x));
+                    } else {
+                        v8[1] = fma(b.x, b.x, b.y * b.y);
+                    }
+                } else {
                 v8[0] = fma(a.x, a.x, a.y * a.y);
                 v8[1] = fma(b.x, b.x, b.y * b.y);
                 v8[2] = fma(a.x, b.x, a.y * b.y);
@@ -2197,6 +2249,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                 v8[5] = fma(b.x, nbv.x, b.y * nbv.y);
                 v8[6] = fma(a.x, nbv.x, a.y * nbv.y);
                 v8[7] = fma(a.x, nbv.y, -(a.y * nbv.x));
+                }
                 const R s8 = warp_reduce_scatter8(v8, lane);
                 if ((lane & 3) == 0) w8[m & 1][warp][lane >> 2] = s8;
                 }
