@@ -1154,6 +1154,29 @@ __device__ bool team_steps2(const Params& p, int cta, unsigned phase, typename C
     }
     publish(p, cta, phase + 1);
 
+    // Bipartite lattice (L even; plain sums): r_m^o and r_m^v live on opposite site
+    // parities.  The tile's sites are enumerated class by class in closed form --
+    // in row r (y = r mod L, z = r / L) the class-c sites are x = 2j + ((c + y + z) & 1),
+    // L/2 of them -- so that a warp holds one class (except the one at the boundary).
+    const bool bipm = (L % 2 == 0) && !COMP && sizeof(R) == 8;
+    const int half = L / 2;
+    const int par_o = (lo % L + (lo / L) % L + lo / (L * L)) & 1;
+    auto row_par = [&](int r, int c) {  // x offset of class c in row r
+        const int z = (int)__umulhi((unsigned)r, p.divL), y = r - z * L;
+        return (c + y + z) & 1;
+    };
+    auto rank_c = [&](int si, int c) {  // class-c sites in [0, si)
+        const int r = (int)__umulhi((unsigned)si, p.divL), x = si - r * L;
+        return r * half + ((x + 1 - row_par(r, c)) >> 1);
+    };
+    auto site_of = [&](int c, int g) {  // the g-th class-c site of the lattice
+        const int r = (int)__umulhi((unsigned)(2 * g), p.divL), j = g - r * half;
+        return r * L + 2 * j + row_par(r, c);
+    };
+    const int F0 = bipm ? rank_c(s0, 0) : 0, F1 = bipm ? rank_c(s0, 1) : 0;
+    const int C0 = bipm ? rank_c(s1, 0) - F0 : 0;
+    const int T = s1 - s0;
+
     for (int m = 1; m <= p.nsteps; ++m) {
         if (!wait_neighbours(p, cta, phase + (unsigned)m, 100 + m)) return false;
         const R2* rd = (m & 1) ? buf1 : buf0;
@@ -1205,7 +1228,60 @@ __device__ bool team_steps2(const Params& p, int cta, unsigned phase, typename C
             acc[6] = fma(a.x, nbv.x, fma(a.y, nbv.y, acc[6]));
             acc[7] = fma(a.x, nbv.y, fma(-a.y, nbv.x, acc[7]));
         };
-        if constexpr (WIDE && sizeof(R) == 4 && !COMP) {
+        if (bipm) {
+            // bipartite lattice: the tile's sites parity by parity; a site advances one
+            // vector and forms the products parity leaves (o where r_{m+1}^o lives,
+            // with |r_m^v|^2; v on the other parity, with |r_m^o|^2 and <r_m^o|r_{m+1}^v>)
+            const int par_o1 = (par_o + m + 1) & 1;  // the class receiving r_{m+1}^o
+            struct OpsB {
+                R2 h[6], nv[6], held, pv;
+                int i, av;
+            };
+            auto loadb = [&](int k, OpsB& q) {
+                const int c = k < C0 ? 0 : 1;
+                q.i = site_of(c, c == 0 ? F0 + k : F1 + (k - C0));
+                q.av = c == par_o1 ? 0 : 1;  // the vector this site advances
+                int nb[6];
+                site_nbrs(q.i, L, p.divL, p.divLL, nb);
+#pragma unroll
+                for (int d = 0; d < 6; ++d) q.h[d] = hop_of(hop, N, q.i, d, nb[d]);
+                const R2* rv = rd + (size_t)q.av * N;
+#pragma unroll
+                for (int d = 0; d < 6; ++d) q.nv[d] = vm.ld(rv + nb[d]);
+                q.held = vm.ld(rd + (size_t)(1 - q.av) * N + q.i);  // r_m of the other vector
+                q.pv = vm.ld(wr + (size_t)q.av * N + q.i);
+            };
+            auto stepb = [&](const OpsB& q) {
+                const R2 a = bond_sum6(q.h, q.nv);
+                const R2 nx = c_make<R2>(fma((R)2, a.x, -q.pv.x), fma((R)2, a.y, -q.pv.y));
+                if (m < p.nsteps) vm.st(wr + (size_t)q.av * N + q.i, nx);
+                const R2 held = q.held;
+                if (q.av == 0) {
+                    acc[1] = fma(held.x, held.x, fma(held.y, held.y, acc[1]));
+                } else {
+                    acc[0] = fma(held.x, held.x, fma(held.y, held.y, acc[0]));
+                    acc[6] = fma(held.x, nx.x, fma(held.y, nx.y, acc[6]));
+                    acc[7] = fma(held.x, nx.y, fma(-held.y, nx.x, acc[7]));
+                }
+            };
+            if constexpr (WIDE && sizeof(R) == 4) {
+                // FP32: two sites per pass, both sites' loads issued before the first use
+                for (int k = tid; k < T; k += 2 * kThreads) {
+                    const int k2 = k + kThreads;
+                    OpsB qa, qb;
+                    loadb(k, qa);
+                    if (k2 < T) loadb(k2, qb);
+                    stepb(qa);
+                    if (k2 < T) stepb(qb);
+                }
+            } else {
+                for (int k = tid; k < T; k += kThreads) {
+                    OpsB q;
+                    loadb(k, q);
+                    stepb(q);
+                }
+            }
+        } else if constexpr (WIDE && sizeof(R) == 4 && !COMP) {
             // two sites per pass, both sites' loads issued before the first use
             // (the sites are still summed in the order i, i + kThreads, ...)
             for (int i = s0 + tid; i < s1; i += 2 * kThreads) {
