@@ -977,6 +977,28 @@ __device__ bool team_steps(const Params& p, int cta, unsigned phase, typename Cx
     }
     publish(p, cta, phase + 1);
 
+    // Bipartite lattice, FP64 (L even, plain sums): the tile's sites enumerated
+    // class by class in closed form (as in team_steps2) -- in row r (y = r mod L,
+    // z = r / L) the class-c sites are x = 2j + ((c + y + z) & 1).
+    const bool bipm = (L % 2 == 0) && !COMP && sizeof(R) == 8;
+    const int half = L / 2;
+    const int par_o = (s_loc[0] % L + (s_loc[0] / L) % L + s_loc[0] / (L * L)) & 1;
+    auto row_par = [&](int r, int c) {
+        const int z = (int)__umulhi((unsigned)r, p.divL), y = r - z * L;
+        return (c + y + z) & 1;
+    };
+    auto rank_c = [&](int si, int c) {
+        const int r = (int)__umulhi((unsigned)si, p.divL), x = si - r * L;
+        return r * half + ((x + 1 - row_par(r, c)) >> 1);
+    };
+    auto site_of = [&](int c, int g) {
+        const int r = (int)__umulhi((unsigned)(2 * g), p.divL), j = g - r * half;
+        return r * L + 2 * j + row_par(r, c);
+    };
+    const int F0 = bipm ? rank_c(s0, 0) : 0, F1 = bipm ? rank_c(s0, 1) : 0;
+    const int C0 = bipm ? rank_c(s1, 0) - F0 : 0;
+    const int T = s1 - s0;
+
     for (int m = 1; m <= p.nsteps; ++m) {
         if (!wait_neighbours(p, cta, phase + (unsigned)m, 100 + m)) return false;
         const R2* rd = (m & 1) ? buf1 : buf0;  // r_m of every site
@@ -1053,6 +1075,142 @@ __device__ bool team_steps(const Params& p, int cta, unsigned phase, typename Cx
                 for (int w = 0; w < kWarps; ++w) sum += red[w][tid];
                 gram_add(p, m, tid, sum);
             }
+        } else if (bipm) {
+            // FP64 on a bipartite lattice: the tile's sites parity by parity, chunks of
+            // kThreads.  Class A (parity pa) holds r_m^0 and receives r_{m+1}^{1..6}; class B
+            // holds r_m^{1..6} and receives r_{m+1}^0.  The Gram entries not zero by parity
+            // are 7 over A -- |r_m^0|^2 and <r_m^0|r_{m+1}^k> -- and the 21 <r_m^j|r_m^k>,
+            // 1 <= j <= k, over B: 7 x 32 and 21 x 12 uniform units over the chunk's
+            // A and B positions, their group sums added in order at the end of the step.
+            const int pa = (par_o + m) & 1;
+            double reA = 0.0, imA = 0.0, reB = 0.0, imB = 0.0;
+            // units: A entry uA = warp (tid < 224) over groups lane; B entry uB = tid / 12 (tid < 252)
+            const int uA = warp, uB = tid / 12, gB = tid % 12;
+            int ax = 0, ay = 0, bx = 0, by = 0;
+            if (uA == 0) {
+                ax = ay = 0;
+            } else {
+                ax = 0;
+                ay = kVec + uA;
+            }
+            {
+                int q = uB < 21 ? uB : 0, j = 1;
+                while (q >= 7 - j) {
+                    q -= 7 - j;
+                    ++j;
+                }
+                bx = j;
+                by = j + q;
+            }
+            const int nch = (T + kThreads - 1) / kThreads;
+            for (int c = 0; c < nch; ++c) {
+                const int k = c * kThreads + tid;
+                if (k < T) {
+                    const int cls = k < C0 ? 0 : 1;
+                    const int i = site_of(cls, cls == 0 ? F0 + k : F1 + (k - C0));
+                    int nb[6];
+                    site_nbrs(i, L, p.divL, p.divLL, nb);
+                    R2 h[6];
+#pragma unroll
+                    for (int d = 0; d < 6; ++d) h[d] = hop_of(hop, N, i, d, nb[d]);
+                    auto adv = [&](int v) {
+                        const R2* cv = rd + (size_t)v * N;
+                        R2 a = c_make<R2>(0, 0);
+#pragma unroll
+                        for (int d = 0; d < 6; ++d) c_fma(a, h[d], vm.ld(cv + nb[d]));
+                        const R2 pv = vm.ld(wr + (size_t)v * N + i);
+                        const R2 nx = c_make<R2>(fma((R)2, a.x, -pv.x), fma((R)2, a.y, -pv.y));
+                        if (m < p.nsteps) vm.st(wr + (size_t)v * N + i, nx);
+                        return nx;
+                    };
+                    if (cls == pa) {
+                        const R2 c0 = vm.ld(rd + i);
+                        dyn[tid] = make_double2(c0.x, c0.y);
+#pragma unroll
+                        for (int v = 1; v < kVec; ++v) {
+                            const R2 nx = adv(v);
+                            dyn[(kVec + v) * kStage + tid] = make_double2(nx.x, nx.y);
+                        }
+                    } else {
+                        adv(0);
+#pragma unroll
+                        for (int v = 1; v < kVec; ++v) {
+                            const R2 cv = vm.ld(rd + (size_t)v * N + i);
+                            dyn[v * kStage + tid] = make_double2(cv.x, cv.y);
+                        }
+                    }
+                }
+                __syncthreads();
+                // the chunk's class-0 positions come first, then class 1
+                const int n = min(kThreads, T - c * kThreads);
+                const int n0 = max(0, min(C0 - c * kThreads, n));
+                const int a_lo = pa == 0 ? 0 : n0, a_hi = pa == 0 ? n0 : n;
+                const int b_lo = pa == 0 ? n0 : 0, b_hi = pa == 0 ? n : n0;
+                if (tid < 7 * 32) {
+                    const double2 *xs = dyn + ax * kStage, *ys = dyn + ay * kStage;
+                    for (int q = a_lo + lane; q < a_hi; q += 32) {
+                        const double2 x = xs[q], y = ys[q];
+                        reA = fma(x.x, y.x, reA);
+                        reA = fma(x.y, y.y, reA);
+                        imA = fma(x.x, y.y, imA);
+                        imA = fma(-x.y, y.x, imA);
+                    }
+                }
+                if (tid < 21 * 12) {
+                    const double2 *xs = dyn + bx * kStage, *ys = dyn + by * kStage;
+                    for (int q = b_lo + gB; q < b_hi; q += 12) {
+                        const double2 x = xs[q], y = ys[q];
+                        reB = fma(x.x, y.x, reB);
+                        reB = fma(x.y, y.y, reB);
+                        imB = fma(x.x, y.y, imB);
+                        imB = fma(-x.y, y.x, imB);
+                    }
+                }
+                __syncthreads();
+            }
+            publish(p, cta, phase + (unsigned)m + 1u);
+            // the group sums of each entry, added in order
+            double* part = (double*)dyn;  // [224][2] A, then [252][2] B
+            if (tid < 7 * 32) {
+                part[2 * tid] = reA;
+                part[2 * tid + 1] = imA;
+            }
+            if (tid < 21 * 12) {
+                part[448 + 2 * tid] = reB;
+                part[448 + 2 * tid + 1] = imB;
+            }
+            __syncthreads();
+            if (tid < 7) {
+                double sr = 0.0, si = 0.0;
+                for (int g = 0; g < 32; ++g) {
+                    sr += part[2 * (tid * 32 + g)];
+                    si += part[2 * (tid * 32 + g) + 1];
+                }
+                if (tid == 0) {
+                    gram_add(p, m, 2 * pair_of(0, 0), sr);
+                } else {
+                    const int e = 56 + 2 * pair_of(0, tid);
+                    gram_add(p, m, e, sr);
+                    gram_add(p, m, e + 1, si);
+                }
+            } else if (tid >= 32 && tid < 32 + 21) {
+                const int u = tid - 32;
+                int q = u, j = 1;
+                while (q >= 7 - j) {
+                    q -= 7 - j;
+                    ++j;
+                }
+                const int kk = j + q;
+                double sr = 0.0, si = 0.0;
+                for (int g = 0; g < 12; ++g) {
+                    sr += part[448 + 2 * (u * 12 + g)];
+                    si += part[448 + 2 * (u * 12 + g) + 1];
+                }
+                const int e = 2 * pair_of(j, kk);
+                gram_add(p, m, e, sr);
+                if (j != kk) gram_add(p, m, e + 1, si);
+            }
+            __syncthreads();
         } else {
             double re = 0.0, im = 0.0;
             const int T = s1 - s0;
