@@ -136,6 +136,14 @@ def _dp(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+def _host_spins(spins) -> np.ndarray:
+    """Spins (theta, phi) as a contiguous host float64 [N][2] array, from a numpy
+    array or a torch tensor on any device (the library copies host spins)."""
+    if hasattr(spins, "detach") and hasattr(spins, "cpu"):
+        spins = spins.detach().cpu().numpy()
+    return np.ascontiguousarray(spins, dtype=np.float64).reshape(-1, 2)
+
+
 def current_stream_handle():
     """The raw cudaStream_t of torch's current stream, or None (default stream)."""
     try:
@@ -178,7 +186,7 @@ class Chain:
         opt.compensated = 1 if compensated else 0
         self.engine = engine
         self.compensated = bool(compensated)
-        sp = np.ascontiguousarray(spins, dtype=np.float64).reshape(-1, 2)
+        sp = _host_spins(spins)
         if sp.shape[0] != self.N:
             raise ValueError(f"spins has {sp.shape[0]} rows, expected N = {self.N}")
         h = ctypes.c_void_p()
@@ -259,7 +267,7 @@ class Chain:
         return out
 
     def set_state(self, spins, counter: int):
-        sp = np.ascontiguousarray(spins, dtype=np.float64).reshape(-1, 2)
+        sp = _host_spins(spins)
         self._check(self._lib.gfmc_set_state(self._h, _dp(sp), int(counter)))
 
     def set_wait_budget(self, cycles: int):

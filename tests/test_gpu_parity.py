@@ -380,3 +380,19 @@ def test_fp32_with_and_without_the_helper_warp(G, L, ncta):
         out = ch.updates(5)
     res = O.updates(L, sp, 5, M, beta=20.0, chem=-2.0, seed=4, forced=out["decisions"].astype(np.int8))
     assert np.abs(out["d_omega"] - res["d_omega"]).max() <= 1e-4
+
+
+def test_torch_tensor_spins_give_the_same_chain(G):
+    """Spins as a torch tensor on the GPU or the host, or as numpy: the same chain."""
+    torch = pytest.importorskip("torch")
+    L, M = 6, 64
+    sp = inputs.uniform_sphere(L, 21)
+    outs = []
+    for arg in (sp, torch.tensor(sp), torch.tensor(sp, device="cuda")):
+        with chain(G, L, arg, M, seed=5) as ch:
+            out = ch.updates(8)
+            ch.set_state(arg, 0)
+            outs.append((out["d_omega"], ch.moments(9)))
+    for d, mu in outs[1:]:
+        np.testing.assert_array_equal(d, outs[0][0])
+        np.testing.assert_array_equal(mu, outs[0][1])
