@@ -981,6 +981,7 @@ __device__ bool team_steps(const Params& p, int cta, unsigned phase, typename Cx
     // class by class in closed form (as in team_steps2) -- in row r (y = r mod L,
     // z = r / L) the class-c sites are x = 2j + ((c + y + z) & 1).
     const bool bipm = (L % 2 == 0) && !COMP && sizeof(R) == 8;
+    const bool bip32 = (L % 2 == 0) && !COMP && sizeof(R) == 4;
     const int half = L / 2;
     const int par_o = (s_loc[0] % L + (s_loc[0] / L) % L + s_loc[0] / (L * L)) & 1;
     auto row_par = [&](int r, int c) {
@@ -995,8 +996,8 @@ __device__ bool team_steps(const Params& p, int cta, unsigned phase, typename Cx
         const int r = (int)__umulhi((unsigned)(2 * g), p.divL), j = g - r * half;
         return r * L + 2 * j + row_par(r, c);
     };
-    const int F0 = bipm ? rank_c(s0, 0) : 0, F1 = bipm ? rank_c(s0, 1) : 0;
-    const int C0 = bipm ? rank_c(s1, 0) - F0 : 0;
+    const int F0 = (bipm || bip32) ? rank_c(s0, 0) : 0, F1 = (bipm || bip32) ? rank_c(s0, 1) : 0;
+    const int C0 = (bipm || bip32) ? rank_c(s1, 0) - F0 : 0;
     const int T = s1 - s0;
 
     for (int m = 1; m <= p.nsteps; ++m) {
@@ -1004,6 +1005,121 @@ __device__ bool team_steps(const Params& p, int cta, unsigned phase, typename Cx
         const R2* rd = (m & 1) ? buf1 : buf0;  // r_m of every site
         R2* wr = (m & 1) ? buf0 : buf1;        // r_{m-1}, overwritten by r_{m+1}
         if constexpr (sizeof(R) == 4) {
+          if (bip32) {
+            // FP32 on a bipartite lattice: the tile's sites parity by parity (as the FP64
+            // path below); a site of class A (parity pa, holding r_m^0) advances vectors
+            // 1..6 and adds |r_m^0|^2 and <r_m^0|r_{m+1}^k>, a site of class B advances
+            // vector 0 and adds the 21 <r_m^j|r_m^k>, 1 <= j <= k.  The thread's 13 + 36
+            // sums of two chunks go by warp butterfly into this warp's FP64 row of red.
+            for (int e = lane; e < kEntries; e += 32) red[warp][e] = 0.0;
+            const int pa = (par_o + m) & 1;
+            float sa[13], sb[36];
+#pragma unroll
+            for (int e = 0; e < 13; ++e) sa[e] = 0.f;
+#pragma unroll
+            for (int e = 0; e < 36; ++e) sb[e] = 0.f;
+            auto flush = [&]() {
+                float v0[32], v1[32];
+#pragma unroll
+                for (int e = 0; e < 13; ++e) v0[e] = sa[e];
+#pragma unroll
+                for (int e = 0; e < 19; ++e) v0[13 + e] = sb[e];
+#pragma unroll
+                for (int e = 0; e < 17; ++e) v1[e] = sb[19 + e];
+#pragma unroll
+                for (int e = 17; e < 32; ++e) v1[e] = 0.f;
+                const float w0 = warp_reduce_scatter32(v0, lane);
+                const float w1 = warp_reduce_scatter32(v1, lane);
+                red[warp][lane] += (double)w0;
+                red[warp][32 + lane] += (double)w1;
+#pragma unroll
+                for (int e = 0; e < 13; ++e) sa[e] = 0.f;
+#pragma unroll
+                for (int e = 0; e < 36; ++e) sb[e] = 0.f;
+            };
+            const int nch = (T + kThreads - 1) / kThreads;
+            for (int c = 0; c < nch; ++c) {
+                const int k = c * kThreads + tid;
+                if (k < T) {
+                    const int cls = k < C0 ? 0 : 1;
+                    const int i = site_of(cls, cls == 0 ? F0 + k : F1 + (k - C0));
+                    int nb[6];
+                    site_nbrs(i, L, p.divL, p.divLL, nb);
+                    R2 h[6];
+#pragma unroll
+                    for (int d = 0; d < 6; ++d) h[d] = hop_of(hop, N, i, d, nb[d]);
+                    if (cls == pa) {
+                        R2 nv[6][6], pv[6];
+                        const R2 c0 = vm.ld(rd + i);
+#pragma unroll
+                        for (int v = 1; v < kVec; ++v) {
+#pragma unroll
+                            for (int d = 0; d < 6; ++d) nv[v - 1][d] = vm.ld(rd + (size_t)v * N + nb[d]);
+                            pv[v - 1] = vm.ld(wr + (size_t)v * N + i);
+                        }
+                        sa[0] = fmaf(c0.x, c0.x, fmaf(c0.y, c0.y, sa[0]));
+#pragma unroll
+                        for (int v = 1; v < kVec; ++v) {
+                            const R2 a = bond_sum6(h, nv[v - 1]);
+                            const R2 nx = c_make<R2>(fmaf(2.f, a.x, -pv[v - 1].x), fmaf(2.f, a.y, -pv[v - 1].y));
+                            if (m < p.nsteps) vm.st(wr + (size_t)v * N + i, nx);
+                            sa[2 * v - 1] = fmaf(c0.x, nx.x, fmaf(c0.y, nx.y, sa[2 * v - 1]));
+                            sa[2 * v] = fmaf(c0.x, nx.y, fmaf(-c0.y, nx.x, sa[2 * v]));
+                        }
+                    } else {
+                        R2 n0[6], cv[6];
+#pragma unroll
+                        for (int d = 0; d < 6; ++d) n0[d] = vm.ld(rd + nb[d]);
+                        const R2 p0 = vm.ld(wr + i);
+#pragma unroll
+                        for (int v = 1; v < kVec; ++v) cv[v - 1] = vm.ld(rd + (size_t)v * N + i);
+                        const R2 a = bond_sum6(h, n0);
+                        const R2 nx = c_make<R2>(fmaf(2.f, a.x, -p0.x), fmaf(2.f, a.y, -p0.y));
+                        if (m < p.nsteps) vm.st(wr + i, nx);
+                        int b = 0;
+#pragma unroll
+                        for (int j = 0; j < 6; ++j) {
+#pragma unroll
+                            for (int kk = j; kk < 6; ++kk) {
+                                const R2 x = cv[j], y = cv[kk];
+                                sb[b] = fmaf(x.x, y.x, fmaf(x.y, y.y, sb[b]));
+                                ++b;
+                                if (kk != j) {
+                                    sb[b] = fmaf(x.x, y.y, fmaf(-x.y, y.x, sb[b]));
+                                    ++b;
+                                }
+                            }
+                        }
+                    }
+                }
+                if ((c & 1) || c == nch - 1) flush();
+            }
+            publish(p, cta, phase + (unsigned)m + 1u);
+            // value e < 49 of the rows: 0 |r_m^0|^2; 1..12 <r_m^0|r_{m+1}^k> (re, im);
+            // 13.. the pairs j <= k of vectors 1..6 in order (re, and im off the diagonal)
+            if (tid < 49) {
+                double sum = 0.0;
+#pragma unroll
+                for (int w = 0; w < kWarps; ++w) sum += red[w][tid];
+                int e;
+                if (tid == 0) {
+                    e = 2 * pair_of(0, 0);
+                } else if (tid < 13) {
+                    const int kk = (tid - 1) / 2 + 1;
+                    e = 56 + 2 * pair_of(0, kk) + ((tid - 1) & 1);
+                } else {
+                    int b = tid - 13, j = 1, kk = 1;
+                    for (j = 1; j <= 6; ++j) {
+                        const int len = 2 * (6 - j) + 1;  // this row's values: the diagonal and 2 per pair
+                        if (b < len) break;
+                        b -= len;
+                    }
+                    kk = j + (b + 1) / 2;
+                    e = 2 * pair_of(j, kk) + ((b > 0 && (b & 1) == 0) ? 1 : 0);
+                }
+                gram_add(p, m, e, sum);
+            }
+          } else {
             // chunks of kThreads sites, one per thread: all loads issued before the first use;
             // the Gram products of two chunks summed in the thread, then by warp butterfly
             // into this warp's FP64 row of red
@@ -1075,6 +1191,7 @@ __device__ bool team_steps(const Params& p, int cta, unsigned phase, typename Cx
                 for (int w = 0; w < kWarps; ++w) sum += red[w][tid];
                 gram_add(p, m, tid, sum);
             }
+          }
         } else if (bipm) {
             // FP64 on a bipartite lattice: the tile's sites parity by parity, chunks of
             // kThreads.  Class A (parity pa) holds r_m^0 and receives r_{m+1}^{1..6}; class B
