@@ -90,8 +90,8 @@ def update_flop_nonzero(L: int, M: int) -> float:
 # otherwise.
 TRAFFIC_SOURCES = ("gfmc_engine.cuh", "gfmc_k64.cu", "gfmc_k32.cu", "gfmc_internal.h", "gfmc_vcluster.cuh",
                    "gfmc_kvc.cu")
-TRAFFIC_HASH = "c647f26799a44ad0"
-TRAFFIC_PER_LAUNCH = {"fp64": (16, 7258880 + 3816704), "fp32_mixed": (64, 1478144 + 53504)}
+TRAFFIC_HASH = "8e9790f3f11249d3"
+TRAFFIC_PER_LAUNCH = {"fp64": (16, 7347456 + 3860992), "fp32_mixed": (64, 1034752 + 48128)}
 
 
 def engine_sources_hash() -> str:
