@@ -524,18 +524,16 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
         return bail(cuda_fail(h, e, "allocating chain state"));
     P.helper7 = (!h->multi_site && (N + ncta - 1) / ncta <= gfmc::kThreads - 32) ? 1 : 0;
     // FP64 single chain on an even lattice: the bipartite step when every tile's
-    // sites of each parity fit the 128 threads of their half of the CTA
-    // (2: every class has at most 32 sites, and the class's four warps split its vectors)
+    // sites of each parity fit the 128 staging positions of their class
     P.bip = 0;
     if (h->precision == GFMC_PREC_FP64 && !h->multi_site && L % 2 == 0) {
-        bool fits = true, small = true;
+        bool fits = true;
         for (int c = 0; c < ncta && fits; ++c) {
             int n[2] = {0, 0};
             for (int s = tstart[c]; s < tstart[c + 1]; ++s) ++n[(s % L + (s / L) % L + s / (L * L)) & 1];
             fits = n[0] <= 128 && n[1] <= 128;
-            small = small && n[0] <= 32 && n[1] <= 32;
         }
-        P.bip = fits ? (small ? 2 : 1) : 0;
+        P.bip = fits ? 1 : 0;
     }
     if (prefetch) {
         int* d_wp = nullptr;

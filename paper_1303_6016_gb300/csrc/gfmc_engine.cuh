@@ -178,13 +178,41 @@ __device__ __forceinline__ void set_error(const Params& p, int code, int where, 
 // that ended early the host clears it.
 constexpr int kGramFrac = 58;
 
+// round(x 2^58), ties to even, from the bits of x with integer operations only
+// (the FP64 pipe, the bound of the FP64 engines, is left to the FMAs).  |x| =
+// mant 2^(ex' - 1075), ex' = max(ex, 1), so x 2^58 = mant 2^(ex' - 1017); for
+// |x| <= 16 the shift is at most 10 and the result below 2^63.  Subnormals and
+// values below 2^-59 round to 0.  ok: |x| <= 16 (false for NaN and infinities).
+__device__ __forceinline__ long long fixed58(double x, bool& ok)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long mag_bits = b & 0x7fffffffffffffffull;
+    ok = mag_bits <= 0x4030000000000000ull;  // the bits of 16.0
+    const int ex = (int)(mag_bits >> 52);
+    const unsigned long long mant = (mag_bits & 0xfffffffffffffull) | (ex ? (1ull << 52) : 0ull);
+    const int sh = (ex ? ex : 1) - 1017;
+    unsigned long long q;
+    if (sh >= 0) {
+        q = mant << sh;
+    } else if (sh <= -54) {
+        q = 0;  // mant < 2^53: below half of one unit
+    } else {
+        const int k = -sh;
+        const unsigned long long rem = mant & ((1ull << k) - 1ull), half = 1ull << (k - 1);
+        q = mant >> k;
+        if (rem > half || (rem == half && (q & 1ull))) ++q;
+    }
+    return (b >> 63) ? -(long long)q : (long long)q;
+}
+
 __device__ __forceinline__ void gram_add(const Params& p, int m, int e, double x)
 {
-    if (!(fabs(x) <= 16.0)) {
+    bool ok;
+    long long q = fixed58(x, ok);
+    if (!ok) {
         set_error(p, ERR_NUMERIC, 90, m);
-        x = 0.0;
+        q = 0;
     }
-    const long long q = __double2ll_rn(x * 0x1p58);
     atomicAdd(p.gram + (size_t)(m - 1) * kEntries + e, (unsigned long long)q);
 }
 
@@ -807,6 +835,12 @@ __device__ __forceinline__ double2 minus_i(double2 z)
 {
     // -i z = (Im z, -Re z); the sign flip is a bit operation
     return make_double2(z.y, __hiloint2double(__double2hiint(z.x) ^ 0x80000000, __double2loint(z.x)));
+}
+
+// -x by a sign-bit flip (no FP64 instruction)
+__device__ __forceinline__ double dneg(double x)
+{
+    return __hiloint2double(__double2hiint(x) ^ 0x80000000, __double2loint(x));
 }
 
 // The units' partial sums go to gsum[g][kEntries]; gram_groups_f64 adds the
@@ -2137,9 +2171,7 @@ __device__ __forceinline__ void magnetisation_partial(const Params& p, int s0, i
 // of the tile, tid in [128, 256) the (tid - 128)-th odd one; -1 if none (and
 // for the threads beyond 256).  n[c] receives the count of parity c.  Every
 // thread of the block calls it.
-// small: every class of the tile has at most 32 sites; the class's four warps
-// then all take its sites (lane l: the class's l-th site) and split the vectors.
-__device__ __forceinline__ int bip_site_map(int s0, int s1, int L, int (&n)[2], bool small)
+__device__ __forceinline__ int bip_site_map(int s0, int s1, int L, int (&n)[2])
 {
     __shared__ int s_map[256];
     __shared__ int s_cnt[2][8];
@@ -2169,19 +2201,22 @@ __device__ __forceinline__ int bip_site_map(int s0, int s1, int L, int (&n)[2], 
         n[1] += s_cnt[1][w];
     }
     __syncthreads();
-    return tid < 256 ? s_map[small ? (tid & 128) + lane : tid] : -1;
+    return tid < 256 ? s_map[tid] : -1;
 }
 
 constexpr int kBipUnits = 25;
-constexpr int kBipGroups = 10;
+// 5 site groups: 125 unit threads in 4 warps, as full as 250 in 8, and half
+// the group additions (the FP64 pipe is shared by the SM's warps, so the unit
+// FMAs take the same time on 4 warps as on 8)
+constexpr int kBipGroups = 5;
 
 // The Gram entries that are not zero by parity, as 25 units of one shape:
 // re = sum_s Re(conj(A_s) B_s), im = sum_s Re(conj(C_s) D_s) over kBipGroups
 // site groups of the unit's staging range (a: the sites with r_m of vector 0;
 // b: those with r_m of vectors 1..6), so that every thread of a warp runs the
-// same instruction stream (no divergent unit kinds).  Rows of the staging
-// area: v = r_m^v, 7+v = r_{m+1}^v, 14+v = -i r_m^v, 21+v = -i r_{m+1}^v, and
-// Re(conj(x)(-i y)) = Im(conj(x) y).
+// same instruction stream (no divergent unit kinds).  Row kVec + v of the
+// staging area holds r_m^v on b and r_{m+1}^v on a for v >= 1, and r_m^0 on a;
+// row 3 kVec + v holds -i times row kVec + v, and Re(conj(x)(-i y)) = Im(conj(x) y).
 //   units 0-5   <r_m^0|r_{m+1}^k>, k = u+1 (block 2, over a): A = C = r_m^0,
 //               B = r_{m+1}^k, D = -i r_{m+1}^k
 //   units 6-20  <r_m^j|r_m^k>, 1 <= j < k (over b): A = C = r_m^j, B = r_m^k,
@@ -2199,7 +2234,7 @@ __device__ __forceinline__ void gram_units_bip(const double2* sr, int a0, int a1
     int ra, rb, rc, rd, e1, e2, lo, hi;
     if (u < 6) {
         const int k = u + 1;
-        ra = rc = 0;
+        ra = rc = kVec;
         rb = kVec + k;
         rd = 3 * kVec + k;
         e1 = 56 + 2 * pair_of(0, k);
@@ -2213,23 +2248,23 @@ __device__ __forceinline__ void gram_units_bip(const double2* sr, int a0, int a1
             ++j;
         }
         const int k = j + 1 + q;
-        ra = rc = j;
-        rb = k;
-        rd = 2 * kVec + k;
+        ra = rc = kVec + j;
+        rb = kVec + k;
+        rd = 3 * kVec + k;
         e1 = 2 * pair_of(j, k);
         e2 = e1 + 1;
         lo = b0;
         hi = b1;
     } else if (u < 24) {
         const int j = 2 * (u - 21) + 1;
-        ra = rb = j;
-        rc = rd = j + 1;
+        ra = rb = kVec + j;
+        rc = rd = kVec + j + 1;
         e1 = 2 * pair_of(j, j);
         e2 = 2 * pair_of(j + 1, j + 1);
         lo = b0;
         hi = b1;
     } else {
-        ra = rb = rc = rd = 0;
+        ra = rb = rc = rd = kVec;
         e1 = 2 * pair_of(0, 0);
         e2 = e1 + 1;
         lo = a0;
@@ -2301,8 +2336,7 @@ template <int VARIANT> __device__ __forceinline__ bool chain_barrier(const Param
 // WIDE: the team variant's FP32 paths take two sites per thread per pass (more
 // registers); the server kernel, which holds every instantiation in one kernel,
 // takes one.
-template <class R, int VARIANT, int NV = kVec, int NT = kThreads, bool WIDE = true, bool COMP = false,
-          bool SMALL = false>
+template <class R, int VARIANT, int NV = kVec, int NT = kThreads, bool WIDE = true, bool COMP = false>
 __device__ __forceinline__ void run_chain(const Params& p, const int cta, double2* dyn,
                                           typename Cx<R>::T* vec_smem)
 {
@@ -2337,7 +2371,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
     [[maybe_unused]] int bip_n[2] = {0, 0};
     if constexpr (VARIANT == 0 && sizeof(R) == 8 && (NT > kThreads || NV == 2)) {
         if (p.bip) {
-            i = bip_site_map(s0, s1, p.L, bip_n, SMALL);
+            i = bip_site_map(s0, s1, p.L, bip_n);
             active = i >= 0;
         }
     }
@@ -2709,19 +2743,48 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                     }
                     if (!ok) return;
                 } else if (p.bip) {
-                    // bipartite lattice: this thread's site holds r_m of vector 0 when its
-                    // parity is parity(o) + m (then it advances vectors 1..6), else r_m of
-                    // vectors 1..6 (then it advances vector 0); warps 0-3 hold the even
-                    // sites and warps 4-7 the odd ones, so the choice is warp-uniform
+                    // Bipartite lattice.  At step m the sites of parity pa = parity(o) + m
+                    // (class a) hold r_m^0 and receive r_{m+1}^1..6; the other class (b) holds
+                    // r_m^1..6 and receives r_{m+1}^0.  The step is a list of items (vector,
+                    // staging position): 6 n_a heavy ones on class a, n_b light ones on
+                    // class b, dealt to the 256 compute threads in passes of 256, so every
+                    // warp of a pass but the last is full (the FP64 pipe costs a whole warp
+                    // per instruction whatever the active lanes).  No vector lives in
+                    // registers: row kVec + v of the staging area holds the latest value of
+                    // vector v at each position of its class -- r_m^v where it is read as
+                    // r_m, r_{m-1}^v where the item overwrites it with r_{m+1}^v -- and row
+                    // 3 kVec + v holds -i times it; the rows of classes a and b together are
+                    // the Gram units' operands.  Rows 0..5 hold 2 Htilde of each position's
+                    // bonds and rows 2 kVec.. (read as ints) its neighbours and site.
                     const int o0 = s_loc[0];
                     const int par_o = (o0 % L + (o0 / L) % L + o0 / (L * L)) & 1;
                     const int cls = tid >= 128 ? 1 : 0;
-                    const int wq = warp & 3;                               // the warp within its class
-                    const int ps = SMALL ? (tid & 128) + lane : tid;  // staging position
                     const double2* wsm = dyn + 4 * kVec * kStage;
                     const int W = p.win_max;
+                    double2* hs = dyn;                                // [6][kStage]
+                    int* ns = (int*)(dyn + 2 * kVec * kStage);        // [6][kStage], then the sites
+                    int* ss = ns + 6 * kStage;
+                    if (tid < kThreads) {
+                        // this thread's position is its own site: the tables, r_0 and r_1
+                        const bool a1 = cls == ((par_o + 1) & 1);  // class a of step 1
+    #pragma unroll
+                        for (int d = 0; d < 6; ++d) {
+                            hs[d * kStage + tid] = h[d];
+                            ns[d * kStage + tid] = p.prefetch ? nbo[d] : nb[d];
+                        }
+                        ss[tid] = active ? i : 0;
+                        // class a of step 1: r_1^0 and r_0^1..6; class b: r_0^0 and r_1^1..6
+                        dyn[kVec * kStage + tid] = a1 ? cur[0] : prv[0];
+    #pragma unroll
+                        for (int v = 1; v < kVec; ++v) {
+                            const R2 x = a1 ? prv[v] : cur[v];
+                            dyn[(kVec + v) * kStage + tid] = x;
+                            dyn[(3 * kVec + v) * kStage + tid] = minus_i(x);
+                        }
+                    }
                     for (int m = 1; m <= p.nsteps; ++m) {
-                        // barrier 3 also ends every compute warp's Gram units of step m-1
+                        // barrier 3 also ends every compute warp's Gram units of step m-1 (and
+                        // orders the tables and rows above)
                         nbar_sync(3, NT);
                         if (!s_go) return;
                         if (p.prefetch) {
@@ -2734,99 +2797,37 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                             pf_par ^= 1u;
                         }
                         const R2* rd = (m & 1) ? buf1 : buf0;  // r_m of every site
-                        R2* wr = (m & 1) ? buf0 : buf1;        // receives r_{m+1}; held r_{m-1}
-                        const int pa = (par_o + m) & 1;        // parity of the sites holding r_m^0
-                        const bool holds0 = cls == pa;
-                        R2 nxt[kVec];
-    #pragma unroll
-                        for (int v = 0; v < kVec; ++v) nxt[v] = c_make<R2>(0, 0);
-                        if (active) {
+                        R2* wr = (m & 1) ? buf0 : buf1;        // receives r_{m+1}
+                        const int pa = (par_o + m) & 1;
+                        const int na = bip_n[pa], nbc = bip_n[1 - pa];
+                        const int a0 = pa * 128, b0 = (1 - pa) * 128;
+                        const int heavy = 6 * na, items = heavy + nbc;
+    #pragma unroll 1
+                        for (int it = tid; it < items; it += kThreads) {
+                            int v, ps;
+                            if (it < heavy) {
+                                v = 1 + it / na;
+                                ps = a0 + it - (v - 1) * na;
+                            } else {
+                                v = 0;
+                                ps = b0 + it - heavy;
+                            }
                             // h holds 2 Htilde: r_{m+1} = -r_{m-1} + sum_d (2 h_d) r_m(nb_d), FMAs only
-                            auto adv = [&](int v) {
-                                R2 acc = c_make<R2>(-prv[v].x, -prv[v].y);
-                                if (p.prefetch) {
+                            double2* row = dyn + (kVec + v) * kStage;
+                            const double2 pr = row[ps];
+                            R2 acc = c_make<R2>(dneg(pr.x), dneg(pr.y));
+                            if (p.prefetch) {
+                                const double2* src = wsm + v * W;
     #pragma unroll
-                                    for (int d = 0; d < 6; ++d) c_fma(acc, h[d], wsm[v * W + nbo[d]]);
-                                } else {
-                                    const R2* cv = rd + (size_t)v * N;
-    #pragma unroll
-                                    for (int d = 0; d < 6; ++d) c_fma(acc, h[d], ldcg2(cv + nb[d]));
-                                }
-                                nxt[v] = acc;
-                                if (m < p.nsteps) stcg2(wr + (size_t)v * N + i, acc);
-                            };
-                            if constexpr (SMALL) {
-                                // small tiles: the class's four warps share its sites and split
-                                // the vectors, heavy {1,2} {3,4} {5} {6}, light 0 on the fourth,
-                                // so the stencil runs on all four sub-partitions' FP64 pipes
-                                if (holds0) {
-                                    if (wq == 0) {
-                                        adv(1);
-                                        adv(2);
-                                    } else if (wq == 1) {
-                                        adv(3);
-                                        adv(4);
-                                    } else if (wq == 2) {
-                                        adv(5);
-                                    } else {
-                                        adv(6);
-                                    }
-                                } else if (wq == 3) {
-                                    adv(0);
-                                }
+                                for (int d = 0; d < 6; ++d) c_fma(acc, hs[d * kStage + ps], src[ns[d * kStage + ps]]);
                             } else {
-                                if (holds0) {
+                                const R2* src = rd + (size_t)v * N;
     #pragma unroll
-                                    for (int v = 1; v < kVec; ++v) adv(v);
-                                } else {
-                                    adv(0);
-                                }
+                                for (int d = 0; d < 6; ++d) c_fma(acc, hs[d * kStage + ps], ldcg2(src + ns[d * kStage + ps]));
                             }
-                        }
-                        // stage the rows the units of this thread's class read (small tiles:
-                        // each warp the rows of its own vectors, at its lane's position)
-                        auto stage_next = [&](int v) {
-                            dyn[(kVec + v) * kStage + ps] = nxt[v];
-                            dyn[(3 * kVec + v) * kStage + ps] = minus_i(nxt[v]);
-                        };
-                        auto stage_cur = [&](int v) {
-                            dyn[v * kStage + ps] = cur[v];
-                            dyn[(2 * kVec + v) * kStage + ps] = minus_i(cur[v]);
-                        };
-                        if constexpr (SMALL) {
-                            if (holds0 && wq == 3) dyn[ps] = cur[0];
-                            if (wq == 0) {
-                                if (holds0) {
-                                    stage_next(1);
-                                    stage_next(2);
-                                } else {
-                                    stage_cur(1);
-                                    stage_cur(2);
-                                }
-                            } else if (wq == 1) {
-                                if (holds0) {
-                                    stage_next(3);
-                                    stage_next(4);
-                                } else {
-                                    stage_cur(3);
-                                    stage_cur(4);
-                                }
-                            } else if (wq == 2) {
-                                if (holds0) stage_next(5);
-                                else stage_cur(5);
-                            } else {
-                                if (holds0) stage_next(6);
-                                else stage_cur(6);
-                            }
-                        } else {
-                            if (holds0) {
-                                dyn[ps] = cur[0];
-    #pragma unroll
-                                for (int v = 1; v < kVec; ++v) stage_next(v);
-                            } else {
-    #pragma unroll
-                                for (int v = 1; v < kVec; ++v) stage_cur(v);
-                            }
+                            row[ps] = acc;
+                            if (v > 0) dyn[(3 * kVec + v) * kStage + ps] = minus_i(acc);  // -i r^0 is never read
+                            if (m < p.nsteps) stcg2(wr + (size_t)v * N + ss[ps], acc);
                         }
                         nbar_arrive(2, NT);
                         // the group sums of step m-1 (their units ended at barrier 3), after the
@@ -2835,13 +2836,7 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                         if (m >= 2)
                             gram_groups_bip(&red[0][0], p, m - 1);
                         nbar_sync(1, kThreads);
-                        const int a0 = pa * 128, b0 = (1 - pa) * 128;
-                        gram_units_bip(dyn, a0, a0 + bip_n[pa], b0, b0 + bip_n[1 - pa], &red[0][0]);
-    #pragma unroll
-                        for (int v = 0; v < kVec; ++v) {
-                            prv[v] = cur[v];
-                            cur[v] = nxt[v];
-                        }
+                        gram_units_bip(dyn, a0, a0 + na, b0, b0 + nbc, &red[0][0]);
                     }
                     nbar_sync(1, kThreads);
                     gram_groups_bip(&red[0][0], p, p.nsteps);
@@ -3182,13 +3177,11 @@ template <class R, int NV> constexpr int engine_threads()
 
 // A single chain spread over the whole GPU.  COMP (FP32 only): compensated
 // Gram dot products.
-// SMALL (FP64, 7 vectors, bipartite tiles whose parity classes have at most 32
-// sites): the instantiation whose class warps split the vectors.
-template <class R, int NV = kVec, bool COMP = false, bool SMALL = false>
+template <class R, int NV = kVec, bool COMP = false>
 __global__ void __launch_bounds__(engine_threads<R, NV>(), 1) gfmc_engine(const Params p)
 {
     extern __shared__ double2 dyn[];
-    run_chain<R, 0, NV, engine_threads<R, NV>(), true, COMP, SMALL>(p, blockIdx.x, dyn, nullptr);
+    run_chain<R, 0, NV, engine_threads<R, NV>(), true, COMP>(p, blockIdx.x, dyn, nullptr);
 }
 
 // A batch of chains, each on its own team of CTAs (jobs sorted by cta0).

@@ -89,11 +89,10 @@ struct Params {
     int win_max;
     int prefetch;
     // FP64 single-chain engine, L even (the periodic cubic lattice is then
-    // bipartite): warps 0-3 take the tile's even-parity sites, warps 4-7 the
-    // odd ones, and each step advances only the vectors that are nonzero at a
-    // site (vector o on one parity, its 6 neighbours' on the other) and forms
-    // only the Gram sums that are not zero by parity; 2: every class has at most
-    // 32 sites, all four warps of a class take its sites and split the vectors
+    // bipartite): each step advances only the vectors that are nonzero at a
+    // site (vector o on one parity, its 6 neighbours' on the other), dealt to
+    // the compute threads as (vector, site) items, and forms only the Gram sums
+    // that are not zero by parity
     int bip;
     // FP32-mixed: the Gram dot products of the doubling (Eq. mu2) with
     // compensated FP32 products and warp sums (Dot2) before FP64
