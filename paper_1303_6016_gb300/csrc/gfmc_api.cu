@@ -158,10 +158,11 @@ gfmc_status plan_tiles(gfmc_ctx* h, int ncta, std::vector<int>& start, std::vect
 
 // The sites the stencil of CTA c reads -- its tile and every neighbour of a
 // tile site -- as runs of consecutive site indices (first, length) in
-// increasing order: wins[ptr[c] .. ptr[c+1]).  max_len receives the largest
-// number of sites of one CTA.
+// increasing order: wins[ptr[c] .. ptr[c+1]).  halo_only: without the tile's
+// own sites (the bipartite step reads those from its staging rows).  max_len
+// receives the largest number of sites of one CTA.
 void plan_windows(int L, int ncta, const std::vector<int>& start, std::vector<int>& ptr, std::vector<int2>& wins,
-                  int& max_len)
+                  int& max_len, bool halo_only)
 {
     ptr.assign(1, 0);
     wins.clear();
@@ -181,6 +182,10 @@ void plan_windows(int L, int ncta, const std::vector<int>& start, std::vector<in
         }
         std::sort(sites.begin(), sites.end());
         sites.erase(std::unique(sites.begin(), sites.end()), sites.end());
+        if (halo_only)
+            sites.erase(std::remove_if(sites.begin(), sites.end(),
+                                       [&](int i) { return i >= start[c] && i < start[c + 1]; }),
+                        sites.end());
         for (size_t q = 0; q < sites.size(); ++q) {
             if (q > 0 && sites[q] == sites[q - 1] + 1) ++wins.back().y;
             else wins.push_back(make_int2(sites[q], 1));
@@ -473,8 +478,24 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
     std::vector<int2> wins;
     int win_max = 0;
     bool prefetch = false;
+    // FP64 single chain on an even lattice: the bipartite step when every tile's
+    // sites of each parity fit the 128 staging positions of their class; split
+    // when every tile also has at least 128 sites -- then the step's units are
+    // long enough to hide the group sums and the neighbours' flags, and the
+    // prefetch copies only the sites outside the tile
+    bool bip = false, split = false;
+    if (h->precision == GFMC_PREC_FP64 && !h->multi_site && L % 2 == 0) {
+        bip = split = true;
+        for (int c = 0; c < ncta && bip; ++c) {
+            int n[2] = {0, 0};
+            for (int s = tstart[c]; s < tstart[c + 1]; ++s) ++n[(s % L + (s / L) % L + s / (L * L)) & 1];
+            bip = n[0] <= 128 && n[1] <= 128;
+            split = split && tstart[c + 1] - tstart[c] >= 128;
+        }
+        split = split && bip;
+    }
     if (h->precision == GFMC_PREC_FP64 && !h->multi_site) {
-        plan_windows(L, ncta, tstart, wptr, wins, win_max);
+        plan_windows(L, ncta, tstart, wptr, wins, win_max, split);
         int dev_smem = 0, static_smem = 0;
         if ((e = cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device)) != cudaSuccess ||
             (e = gfmc::engine_static_smem_f64(&static_smem)) != cudaSuccess)
@@ -523,18 +544,7 @@ gfmc_status gfmc_create(int L, const double* spins, double t, double mu, double 
         (e = dalloc(h, &h->d_nmag, 1)) != cudaSuccess)
         return bail(cuda_fail(h, e, "allocating chain state"));
     P.helper7 = (!h->multi_site && (N + ncta - 1) / ncta <= gfmc::kThreads - 32) ? 1 : 0;
-    // FP64 single chain on an even lattice: the bipartite step when every tile's
-    // sites of each parity fit the 128 staging positions of their class
-    P.bip = 0;
-    if (h->precision == GFMC_PREC_FP64 && !h->multi_site && L % 2 == 0) {
-        bool fits = true;
-        for (int c = 0; c < ncta && fits; ++c) {
-            int n[2] = {0, 0};
-            for (int s = tstart[c]; s < tstart[c + 1]; ++s) ++n[(s % L + (s / L) % L + s / (L * L)) & 1];
-            fits = n[0] <= 128 && n[1] <= 128;
-        }
-        P.bip = fits ? 1 : 0;
-    }
+    P.bip = bip ? (split ? 2 : 1) : 0;
     if (prefetch) {
         int* d_wp = nullptr;
         int2* d_w = nullptr;

@@ -2169,9 +2169,9 @@ __device__ __forceinline__ void magnetisation_partial(const Params& p, int s0, i
 
 // Site of thread tid of a tile [s0, s1): tid < 128 the tid-th even-parity site
 // of the tile, tid in [128, 256) the (tid - 128)-th odd one; -1 if none (and
-// for the threads beyond 256).  n[c] receives the count of parity c.  Every
-// thread of the block calls it.
-__device__ __forceinline__ int bip_site_map(int s0, int s1, int L, int (&n)[2])
+// for the threads beyond 256).  n[c] receives the count of parity c, pos[t]
+// the position (thread) of tile site s0 + t.  Every thread of the block calls it.
+__device__ __forceinline__ int bip_site_map(int s0, int s1, int L, int (&n)[2], int* pos)
 {
     __shared__ int s_map[256];
     __shared__ int s_cnt[2][8];
@@ -2194,6 +2194,7 @@ __device__ __forceinline__ int bip_site_map(int s0, int s1, int L, int (&n)[2])
         int r = __popc((par ? mo : me) & ((1u << lane) - 1u));
         for (int w = 0; w < warp; ++w) r += s_cnt[par][w];
         s_map[par * 128 + r] = s;  // r < 128: the host admits tiles whose classes have at most 128 sites
+        pos[tid] = par * 128 + r;
     }
     n[0] = n[1] = 0;
     for (int w = 0; w < 8; ++w) {
@@ -2205,6 +2206,8 @@ __device__ __forceinline__ int bip_site_map(int s0, int s1, int L, int (&n)[2])
 }
 
 constexpr int kBipUnits = 25;
+// flag of a neighbour offset that is a staging position in the CTA's own tile
+constexpr int kOwnSite = 1 << 20;
 // 5 site groups: 125 unit threads in 4 warps, as full as 250 in 8, and half
 // the group additions (the FP64 pipe is shared by the SM's warps, so the unit
 // FMAs take the same time on 4 warps as on 8)
@@ -2288,10 +2291,9 @@ __device__ __forceinline__ void gram_units_bip(const double2* sr, int a0, int a1
 
 // Entry e of the CTA's Gram sums of step m = the kBipGroups groups of gram_units_bip
 // added in order, into the chain's sums; the entries that vanish by parity
-// add nothing (threads e < kEntries).
-__device__ __forceinline__ void gram_groups_bip(const double* gsum, const Params& p, int m)
+// add nothing (callers e < kEntries).
+__device__ __forceinline__ void gram_groups_bip(const double* gsum, const Params& p, int m, int e)
 {
-    const int e = threadIdx.x;
     if (e < kEntries) {
         const int pp = (e % 56) >> 1;
         const int j = pair_j(pp), k = pair_k(pp);
@@ -2336,7 +2338,8 @@ template <int VARIANT> __device__ __forceinline__ bool chain_barrier(const Param
 // WIDE: the team variant's FP32 paths take two sites per thread per pass (more
 // registers); the server kernel, which holds every instantiation in one kernel,
 // takes one.
-template <class R, int VARIANT, int NV = kVec, int NT = kThreads, bool WIDE = true, bool COMP = false>
+template <class R, int VARIANT, int NV = kVec, int NT = kThreads, bool WIDE = true, bool COMP = false,
+          bool SPLIT = false>
 __device__ __forceinline__ void run_chain(const Params& p, const int cta, double2* dyn,
                                           typename Cx<R>::T* vec_smem)
 {
@@ -2347,9 +2350,9 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
     static_assert(NT % 32 == 0 && NT >= kThreads, "whole warps, at least the default block");
     constexpr int NW = NT / 32;
     // per warp: room for 112 Gram entries; the cluster variant only reduces 8 here;
-    // the FP64 engine's bipartite Gram units use kBipGroups rows
+    // the FP64 engine's bipartite Gram units use kBipGroups rows per step parity
     constexpr int kRed = VARIANT == 2 ? 8 : kEntries;
-    constexpr int kRedRows = (VARIANT == 0 && sizeof(R) == 8 && NT > kThreads && NW < kBipGroups) ? kBipGroups : NW;
+    constexpr int kRedRows = (VARIANT == 0 && sizeof(R) == 8 && NT > kThreads && NW < 2 * kBipGroups) ? 2 * kBipGroups : NW;
     using R2 = typename Cx<R>::T;
     __shared__ double red[kRedRows][kRed];
     __shared__ double2 s_mu2[NW][2][kPairs];
@@ -2369,9 +2372,12 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
     int i = s0 + tid;
     bool active = VARIANT == 0 && i < s1;
     [[maybe_unused]] int bip_n[2] = {0, 0};
+    [[maybe_unused]] int* bip_pos = nullptr;
     if constexpr (VARIANT == 0 && sizeof(R) == 8 && (NT > kThreads || NV == 2)) {
+        __shared__ int s_bip_pos[kThreads];
+        bip_pos = s_bip_pos;
         if (p.bip) {
-            i = bip_site_map(s0, s1, p.L, bip_n);
+            i = bip_site_map(s0, s1, p.L, bip_n, s_bip_pos);
             active = i >= 0;
         }
     }
@@ -2382,7 +2388,9 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
 #pragma unroll
     for (int d = 0; d < 6; ++d) nb[d] = active ? nbr_site(i, d, L) : 0;
     // FP64 engine with prefetch: where each neighbour sits in the CTA's runs
-    // of prefetched sites (the host plans the runs to hold every neighbour)
+    // of prefetched sites (the host plans the runs to hold every neighbour; on
+    // the bipartite step only those outside the tile, and a neighbour inside it
+    // is kOwnSite | its staging position)
     [[maybe_unused]] int nbo[6] = {0, 0, 0, 0, 0, 0};
     if constexpr (VARIANT == 0 && sizeof(R) == 8 && NT > kThreads) {
         if (p.prefetch && active) {
@@ -2390,10 +2398,14 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
 #pragma unroll
             for (int d = 0; d < 6; ++d) {
                 int off = 0, at = 0;
-                for (int w = wb; w < we; ++w) {
-                    const int2 r = p.win[w];
-                    if (nb[d] >= r.x && nb[d] < r.x + r.y) at = off + nb[d] - r.x;
-                    off += r.y;
+                if (SPLIT && nb[d] >= s0 && nb[d] < s1) {
+                    at = kOwnSite | bip_pos[nb[d] - s0];
+                } else {
+                    for (int w = wb; w < we; ++w) {
+                        const int2 r = p.win[w];
+                        if (nb[d] >= r.x && nb[d] < r.x + r.y) at = off + nb[d] - r.x;
+                        off += r.y;
+                    }
                 }
                 nbo[d] = at;
             }
@@ -2817,9 +2829,17 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                             const double2 pr = row[ps];
                             R2 acc = c_make<R2>(dneg(pr.x), dneg(pr.y));
                             if (p.prefetch) {
+                                // a neighbour in the tile: its r_m^v is in this vector's row (at
+                                // the other class's positions, which no item writes this step)
                                 const double2* src = wsm + v * W;
     #pragma unroll
-                                for (int d = 0; d < 6; ++d) c_fma(acc, hs[d * kStage + ps], src[ns[d * kStage + ps]]);
+                                for (int d = 0; d < 6; ++d) {
+                                    const int o = ns[d * kStage + ps];
+                                    if constexpr (SPLIT)
+                                        c_fma(acc, hs[d * kStage + ps], (o & kOwnSite) ? row[o & (kOwnSite - 1)] : src[o]);
+                                    else
+                                        c_fma(acc, hs[d * kStage + ps], src[o]);
+                                }
                             } else {
                                 const R2* src = rd + (size_t)v * N;
     #pragma unroll
@@ -2830,16 +2850,38 @@ __device__ __forceinline__ void run_chain(const Params& p, const int cta, double
                             if (m < p.nsteps) stcg2(wr + (size_t)v * N + ss[ps], acc);
                         }
                         nbar_arrive(2, NT);
-                        // the group sums of step m-1 (their units ended at barrier 3), after the
-                        // stencil so that their dependent additions do not delay its FMAs; the
-                        // units of step m overwrite red only after barrier 1
-                        if (m >= 2)
-                            gram_groups_bip(&red[0][0], p, m - 1);
-                        nbar_sync(1, kThreads);
-                        gram_units_bip(dyn, a0, a0 + na, b0, b0 + nbc, &red[0][0]);
+                        double* red_m = &red[0][0] + (m & 1) * kBipGroups * kEntries;
+                        if constexpr (SPLIT) {
+                            if (tid < 128) {
+                                // warps 0-3: the units of step m once every item is staged
+                                nbar_sync(1, kThreads);
+                                gram_units_bip(dyn, a0, a0 + na, b0, b0 + nbc, red_m);
+                            } else {
+                                // warps 4-7: meanwhile the group sums of step m-1 (their units
+                                // ended at barrier 3; the units of step m fill the other rows),
+                                // so that their dependent additions and conversions stay off
+                                // the FP64 pipe's critical path
+                                nbar_arrive(1, kThreads);
+                                if (m >= 2)
+                                    gram_groups_bip(&red[0][0] + ((m - 1) & 1) * kBipGroups * kEntries, p, m - 1, tid - 128);
+                            }
+                        } else {
+                            // the group sums of step m-1 (their units ended at barrier 3), after
+                            // the stencil so that their dependent additions do not delay its
+                            // FMAs; the units of step m fill the other rows
+                            if (m >= 2) gram_groups_bip(&red[0][0] + ((m - 1) & 1) * kBipGroups * kEntries, p, m - 1, tid);
+                            nbar_sync(1, kThreads);
+                            gram_units_bip(dyn, a0, a0 + na, b0, b0 + nbc, red_m);
+                        }
                     }
-                    nbar_sync(1, kThreads);
-                    gram_groups_bip(&red[0][0], p, p.nsteps);
+                    // the units of the last step are complete.  A barrier of its own: no barrier 3
+                    // follows the last step, so (SPLIT) warps 4-7 may get here before warps 0-3
+                    // have met that step's barrier 1, and a second arrival of theirs on barrier 1
+                    // would complete it without warps 0-3
+                    nbar_sync(4, kThreads);
+                    if (SPLIT ? tid >= 128 : tid < kEntries)
+                        gram_groups_bip(&red[0][0] + (p.nsteps & 1) * kBipGroups * kEntries, p, p.nsteps,
+                                        SPLIT ? tid - 128 : tid);
                 } else {
                     for (int m = 1; m <= p.nsteps; ++m) {
                         // barrier 3 also ends every compute warp's Gram units of step m-1
@@ -3176,12 +3218,15 @@ template <class R, int NV> constexpr int engine_threads()
 }
 
 // A single chain spread over the whole GPU.  COMP (FP32 only): compensated
-// Gram dot products.
-template <class R, int NV = kVec, bool COMP = false>
+// Gram dot products.  SPLIT (FP64, 7 vectors, bipartite step, tiles of at
+// least 128 sites): the prefetch copies only the sites outside the tile (the
+// stencil reads the tile's own from the staging rows), and warps 4-7 add the
+// Gram group sums of the step before while warps 0-3 form the units.
+template <class R, int NV = kVec, bool COMP = false, bool SPLIT = false>
 __global__ void __launch_bounds__(engine_threads<R, NV>(), 1) gfmc_engine(const Params p)
 {
     extern __shared__ double2 dyn[];
-    run_chain<R, 0, NV, engine_threads<R, NV>(), true, COMP>(p, blockIdx.x, dyn, nullptr);
+    run_chain<R, 0, NV, engine_threads<R, NV>(), true, COMP, SPLIT>(p, blockIdx.x, dyn, nullptr);
 }
 
 // A batch of chains, each on its own team of CTAs (jobs sorted by cta0).

@@ -92,7 +92,8 @@ struct Params {
     // bipartite): each step advances only the vectors that are nonzero at a
     // site (vector o on one parity, its 6 neighbours' on the other), dealt to
     // the compute threads as (vector, site) items, and forms only the Gram sums
-    // that are not zero by parity
+    // that are not zero by parity; 2: tiles of at least 128 sites, the split
+    // instantiation (halo-only prefetch, group sums beside the units)
     int bip;
     // FP32-mixed: the Gram dot products of the doubling (Eq. mu2) with
     // compensated FP32 products and warp sums (Dot2) before FP64

@@ -3,21 +3,23 @@
 
 namespace gfmc {
 
-template <int NV>
+template <int NV, bool SPLIT = false>
 static cudaError_t launch_nv_f64(const Params& p, cudaStream_t s)
 {
     const int smem = single_smem_bytes(p.K, 0, p.prefetch ? p.win_max : 0);
-    cudaError_t e = allow_dynamic_smem((const void*)gfmc_engine<double, NV>);
+    cudaError_t e = allow_dynamic_smem((const void*)gfmc_engine<double, NV, false, SPLIT>);
     if (e != cudaSuccess) return e;
     Params q = p;
     void* args[] = {(void*)&q};
-    return cudaLaunchCooperativeKernel((void*)gfmc_engine<double, NV>, dim3(p.ncta), dim3(engine_threads<double, NV>()),
-                                       args, (size_t)smem, s);
+    return cudaLaunchCooperativeKernel((void*)gfmc_engine<double, NV, false, SPLIT>, dim3(p.ncta),
+                                       dim3(engine_threads<double, NV>()), args, (size_t)smem, s);
 }
 
+// p.bip == 2: the instantiation for tiles of at least 128 sites (halo-only
+// prefetch, group sums beside the units)
 cudaError_t launch_engine_f64(const Params& p, cudaStream_t s)
 {
-    return launch_nv_f64<kVec>(p, s);
+    return p.bip == 2 ? launch_nv_f64<kVec, true>(p, s) : launch_nv_f64<kVec>(p, s);
 }
 
 cudaError_t launch_engine_f64(const Params& p, int nv, cudaStream_t s)
@@ -27,9 +29,11 @@ cudaError_t launch_engine_f64(const Params& p, int nv, cudaStream_t s)
 
 cudaError_t engine_static_smem_f64(int* out)
 {
-    cudaFuncAttributes a;
-    const cudaError_t e = cudaFuncGetAttributes(&a, gfmc_engine<double, kVec>);
-    if (e == cudaSuccess) *out = (int)a.sharedSizeBytes;
+    // the larger of the two 7-vector instantiations, so one fit check covers both
+    cudaFuncAttributes a, b;
+    cudaError_t e = cudaFuncGetAttributes(&a, gfmc_engine<double, kVec>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&b, gfmc_engine<double, kVec, false, true>);
+    if (e == cudaSuccess) *out = (int)(a.sharedSizeBytes > b.sharedSizeBytes ? a.sharedSizeBytes : b.sharedSizeBytes);
     return e;
 }
 

@@ -46,8 +46,11 @@ def chain(G, L, spins, M, **kw):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("L,M,ncta", [(3, 32, 0), (4, 256, 0), (5, 64, 2), (8, 128, 0), (8, 64, 5),
-                                      (12, 64, 0)])
+                                      (12, 64, 0), (8, 128, 2), (6, 64, 1)])
 def test_moments_fp64_match_oracle(G, L, M, ncta):
+    """(8, 128, 2): 256-site tiles whose parity classes fill all 128 staging
+    positions, on the split instantiation; (6, 64, 1): one 216-site tile, whose
+    halo-only prefetch window is empty."""
     sp = inputs.uniform_sphere(L, 0)
     with chain(G, L, sp, M, num_ctas=ncta) as ch:
         for o in sorted({0, 1, L ** 3 // 2 + 3, L ** 3 - 1}):
@@ -355,11 +358,12 @@ def test_lorentz_sweep_matches_oracle(G):
 
 @pytest.mark.parametrize("L,ncta", [(20, 0), (10, 7), (24, 152), (9, 5), (16, 17), (16, 0), (20, 152), (14, 0)])
 def test_fp64_tile_layouts_match_oracle(G, L, ncta):
-    """Tile layouts of the FP64 engine: odd L (no bipartite step), bipartite
-    tiles, and the small-tile instantiation where every parity class fits one
-    warp and the class's four warps split the vectors -- (20, 0), (16, 0):
-    64-site tiles; (20, 152): ragged 52/53-site tiles; (14, 0): 65-site tiles,
-    one site past the small-tile bound."""
+    """Tile layouts of the FP64 engine: odd L (no bipartite step) and
+    bipartite tiles, the (vector, site) items of a step filling part of one
+    pass or spilling into a second -- (20, 0), (16, 0): 64-site tiles; (20,
+    152): ragged 52/53-site tiles; (14, 0): 65-site tiles -- and tiles of at
+    least 128 sites on the split instantiation (halo-only prefetch, group sums
+    beside the units): (10, 7), 142/143 sites; (16, 17), 240/241 sites."""
     M = 64
     sp = inputs.uniform_sphere(L, 40 + L)
     with chain(G, L, sp, M, num_ctas=ncta, seed=3) as ch:
