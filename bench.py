@@ -90,8 +90,8 @@ def update_flop_nonzero(L: int, M: int) -> float:
 # otherwise.
 TRAFFIC_SOURCES = ("gfmc_engine.cuh", "gfmc_k64.cu", "gfmc_k32.cu", "gfmc_internal.h", "gfmc_vcluster.cuh",
                    "gfmc_kvc.cu")
-TRAFFIC_HASH = "8e9790f3f11249d3"
-TRAFFIC_PER_LAUNCH = {"fp64": (16, 7347456 + 3860992), "fp32_mixed": (64, 1034752 + 48128)}
+TRAFFIC_HASH = "f1314c5534c2c5a7"
+TRAFFIC_PER_LAUNCH = {"fp64": (16, 6818304 + 2359296), "fp32_mixed": (64, 1485312 + 26880)}
 
 
 def engine_sources_hash() -> str:
@@ -570,6 +570,14 @@ def main():
     achieved_tf = U * flop_nz / launch_s / 1e12
     derived_tf = alu_peak_tflops("fp64", clocks.get("sm_max_mhz") or 2070.0) if clocks else alu_peak_tflops("fp64")
     peak_tf = gfmc.fma_peak_tflops("fp64", repeats=3, stream=stream.cuda_stream)
+    # what the FP64 pipe needs at the engine's occupancy (one CTA of 256 per SM)
+    issue = {"chains16_warps8": gfmc.fp64_issue_rate(16, 8, stream=stream.cuda_stream),
+             "chains1_warps4": gfmc.fp64_issue_rate(1, 4, stream=stream.cuda_stream),
+             "chains4_warps8_lanes12": gfmc.fp64_issue_rate(4, 8, lanes=12, stream=stream.cuda_stream),
+             "unit": "FP64 fma warp-lane slots per SM clock (gfmc_measure_fp64_issue)",
+             "note": "one dependent chain on each of 4 warps keeps the pipe as busy as 16 chains on 8, and a "
+                     "warp of 12 active lanes costs 32 lanes' slots: the engine's rate is set by its count of "
+                     "warp-level FP64 instructions"}
     e2e_per, h2d, d2h = time_e2e(ch, stream, U, max(3, args.steps // 2), ch.get_spins())
     e2e_value = U / (statistics.mean(e2e_per) / 1000.0) * world
     vec_bytes = 2 * 7 * L ** 3 * 16
@@ -595,13 +603,15 @@ def main():
                                   "count with them, 791, gives flop_full_per_update)",
                      "flop_full_per_update": flop_u,
                      "peak_source": "measured in this run: gfmc_measure_fma_peak (own kernel, 16 independent "
-                                    "double fma chains per thread, 2 CTAs of 256 per SM, best of 3, CUDA events)",
+                                    "double fma chains per thread, one CTA of 256 on every SM, best of 3, CUDA "
+                                    "events)",
                      "peak_derived": derived_tf,
                      "peak_derived_source": "152 SMs x max SM clock x 2 FP64 FMA lanes per SM x 2 flop",
                      "flop_s8d_per_update": (M // 2) * L ** 3 * 830,
                      "frac_s8d": U * (M // 2) * L ** 3 * 830 / launch_s / 1e12 / peak_tf,
                      "s8d_note": "the survey's per-update count (M/2) N 830 counts the products that vanish by "
-                                 "parity, which this engine does not execute; against it the fraction exceeds 1"},
+                                 "parity, which this engine does not execute; against it the fraction exceeds 1",
+                     "fp64_issue": issue},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": args.steps,
         "clocks": clocks,

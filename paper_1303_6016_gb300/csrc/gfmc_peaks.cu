@@ -1,8 +1,11 @@
 // gfmc_peaks.cu -- fused multiply-add throughput of the device, the
-// denominator of the engines' arithmetic rooflines, and the cost of the FP32
+// denominator of the engines' arithmetic rooflines, the FP64 pipe's issue
+// rate at the FP64 engines' occupancy, and the cost of the FP32
 // vector-cluster engine's exchange alone (include/gfmc_peaks.h).
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
+
+#include <vector>
 
 #include "../../include/gfmc_peaks.h"
 
@@ -29,13 +32,20 @@ __global__ void __launch_bounds__(kThreads) fma_stream(int iters, T m, T c, T* s
     if (s == (T)-1) sink[0] = s;
 }
 
+// One CTA on every SM: the dynamic shared memory keeps a second one out, so no
+// SM holds more of the launch than another (left to the block scheduler, a
+// grid of 2 CTAs per SM without it measured 16 % below the FP64 pipe's rate).
+constexpr int kPeakSmem = 120 * 1024;
+
 template <class T>
 gfmc_status measure(int repeats, int iters, double* tflops, cudaStream_t s)
 {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return GFMC_ECUDA;
-    const int blocks = 2 * sms;
+    if (cudaFuncSetAttribute(fma_stream<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kPeakSmem) != cudaSuccess)
+        return GFMC_ECUDA;
+    const int blocks = sms;
     T* sink = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     gfmc_status st = GFMC_OK;
@@ -45,7 +55,7 @@ gfmc_status measure(int repeats, int iters, double* tflops, cudaStream_t s)
     // one untimed launch, then the timed ones
     for (int r = 0; r <= repeats && st == GFMC_OK; ++r) {
         if (cudaEventRecord(e0, s) != cudaSuccess) { st = GFMC_ECUDA; break; }
-        fma_stream<T><<<blocks, kThreads, 0, s>>>(iters, (T)0.999, (T)1e-3, sink);
+        fma_stream<T><<<blocks, kThreads, kPeakSmem, s>>>(iters, (T)0.999, (T)1e-3, sink);
         if (cudaGetLastError() != cudaSuccess || cudaEventRecord(e1, s) != cudaSuccess ||
             cudaEventSynchronize(e1) != cudaSuccess) {
             st = GFMC_ECUDA;
@@ -208,12 +218,99 @@ extern "C" gfmc_status gfmc_measure_cluster_exchange(int steps, int repeats, dou
     return st;
 }
 
+// ---- the FP64 pipe's issue rate at the FP64 engines' occupancy ----
+// One CTA of 256 threads per SM (the dynamic shared memory keeps a second one
+// out); warps [0, warps) run lanes [0, lanes) of CH independent chains.  Each
+// CTA records the SM cycles between two CTA barriers around the chains.
+constexpr int kIssueSmem = 120 * 1024;
+
+template <int CH>
+__global__ void __launch_bounds__(kThreads, 1)
+    fp64_issue(int iters, int warps, int lanes, double m, double c, double* sink, long long* cycles)
+{
+    extern __shared__ double issue_pad[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    const long long t0 = clock64();
+    if (warp < warps && lane < lanes) {
+        double a[CH];
+#pragma unroll
+        for (int k = 0; k < CH; ++k) a[k] = (double)(threadIdx.x + k) * 1e-3;
+        for (int i = 0; i < iters; ++i)
+#pragma unroll
+            for (int k = 0; k < CH; ++k) a[k] = fma(a[k], m, c);
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < CH; ++k) s += a[k];
+        // never true for the bounded sequence a -> a m + c; keeps the chains alive
+        if (s == -1.0) sink[0] = s + issue_pad[0];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) cycles[blockIdx.x] = clock64() - t0;
+}
+
+template <int CH>
+gfmc_status issue_rate(int warps, int lanes, int repeats, double* rate, cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return GFMC_ECUDA;
+    if (cudaFuncSetAttribute(fp64_issue<CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, kIssueSmem) != cudaSuccess)
+        return GFMC_ECUDA;
+    // about 2e7 cycles per launch at the device's rate
+    const int iters = (int)(32000000LL / ((long long)warps * 32 * CH));
+    double* sink = nullptr;
+    long long* cyc = nullptr;
+    if (cudaMalloc(&sink, sizeof(double)) != cudaSuccess) return GFMC_ENOMEM;
+    if (cudaMalloc(&cyc, sizeof(long long) * (size_t)sms) != cudaSuccess) {
+        cudaFree(sink);
+        return GFMC_ENOMEM;
+    }
+    std::vector<long long> h((size_t)sms);
+    gfmc_status st = GFMC_OK;
+    double best = 0.0;
+    for (int r = 0; r <= repeats && st == GFMC_OK; ++r) {
+        fp64_issue<CH><<<sms, kThreads, kIssueSmem, s>>>(iters, warps, lanes, 0.999, 1e-3, sink, cyc);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(h.data(), cyc, sizeof(long long) * (size_t)sms, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            st = GFMC_ECUDA;
+            break;
+        }
+        long long mx = 1;
+        for (long long v : h) mx = v > mx ? v : mx;
+        // warp-lane slots: a warp's instruction occupies the pipe for all 32 lanes
+        const double r_ = (double)warps * 32.0 * CH * (double)iters / (double)mx;
+        if (r > 0 && r_ > best) best = r_;
+    }
+    cudaFree(sink);
+    cudaFree(cyc);
+    if (st == GFMC_OK) *rate = best;
+    return st;
+}
+
+extern "C" gfmc_status gfmc_measure_fp64_issue(int chains, int warps, int lanes, int repeats, double* fma_per_clock,
+                                               void* stream)
+{
+    if (!fma_per_clock || repeats < 1 || warps < 1 || warps > kThreads / 32 || lanes < 1 || lanes > 32)
+        return GFMC_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (chains) {
+    case 1: return issue_rate<1>(warps, lanes, repeats, fma_per_clock, s);
+    case 2: return issue_rate<2>(warps, lanes, repeats, fma_per_clock, s);
+    case 4: return issue_rate<4>(warps, lanes, repeats, fma_per_clock, s);
+    case 8: return issue_rate<8>(warps, lanes, repeats, fma_per_clock, s);
+    case 16: return issue_rate<16>(warps, lanes, repeats, fma_per_clock, s);
+    default: return GFMC_EINVAL;
+    }
+}
+
 extern "C" gfmc_status gfmc_measure_fma_peak(int precision, int repeats, double* tflops, void* stream)
 {
     if (!tflops || repeats < 1 || (precision != GFMC_PREC_FP64 && precision != GFMC_PREC_FP32_MIXED))
         return GFMC_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     // about 20-40 ms per launch on a GB300: FP64 issues ~64x fewer fmas per clock
-    return precision == GFMC_PREC_FP64 ? measure<double>(repeats, 20000, tflops, s)
-                                       : measure<float>(repeats, 800000, tflops, s);
+    return precision == GFMC_PREC_FP64 ? measure<double>(repeats, 40000, tflops, s)
+                                       : measure<float>(repeats, 1600000, tflops, s);
 }

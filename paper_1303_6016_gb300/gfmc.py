@@ -36,7 +36,7 @@ EXPORTS = ("gfmc_default_options", "gfmc_create", "gfmc_moments", "gfmc_delta_om
            "gfmc_server_create",
            "gfmc_server_submit",
            "gfmc_server_poll", "gfmc_server_last_error", "gfmc_server_destroy",
-           "gfmc_measure_fma_peak", "gfmc_measure_cluster_exchange")
+           "gfmc_measure_fma_peak", "gfmc_measure_fp64_issue", "gfmc_measure_cluster_exchange")
 
 
 class GfmcError(RuntimeError):
@@ -122,6 +122,8 @@ def load(path: str = LIB_PATH):
     L.gfmc_server_destroy.restype = None
     L.gfmc_measure_fma_peak.argtypes = [ctypes.c_int, ctypes.c_int, d, vp]
     L.gfmc_measure_fma_peak.restype = ctypes.c_int
+    L.gfmc_measure_fp64_issue.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, d, vp]
+    L.gfmc_measure_fp64_issue.restype = ctypes.c_int
     L.gfmc_measure_cluster_exchange.argtypes = [ctypes.c_int, ctypes.c_int, d, vp]
     L.gfmc_measure_cluster_exchange.restype = ctypes.c_int
     for name in ("gfmc_create", "gfmc_moments", "gfmc_delta_omega", "gfmc_updates", "gfmc_sweep",
@@ -297,6 +299,17 @@ def fma_peak_tflops(precision: str = "fp64", repeats: int = 3, stream=None) -> f
     st = lib.gfmc_measure_fma_peak(PRECISIONS[precision], int(repeats), _dp(out), stream)
     if st != GFMC_OK:
         raise GfmcError(st, "gfmc_measure_fma_peak failed")
+    return float(out[0])
+
+
+def fp64_issue_rate(chains: int, warps: int, lanes: int = 32, repeats: int = 2, stream=None) -> float:
+    """FP64 fma warp-lane slots an SM retires per clock at one CTA of 256
+    threads per SM (gfmc_measure_fp64_issue)."""
+    lib = load()
+    out = np.zeros(1)
+    st = lib.gfmc_measure_fp64_issue(int(chains), int(warps), int(lanes), int(repeats), _dp(out), stream)
+    if st != GFMC_OK:
+        raise GfmcError(st, "gfmc_measure_fp64_issue failed")
     return float(out[0])
 
 
