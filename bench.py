@@ -604,7 +604,8 @@ def main():
                      "flop_full_per_update": flop_u,
                      "peak_source": "measured in this run: gfmc_measure_fma_peak (own kernel, 16 independent "
                                     "double fma chains per thread, one CTA of 256 on every SM, best of 3, CUDA "
-                                    "events)",
+                                    "events; it retires the pipe's 2 warp-lane slots per SM clock, see "
+                                    "fp64_issue)",
                      "peak_derived": derived_tf,
                      "peak_derived_source": "152 SMs x max SM clock x 2 FP64 FMA lanes per SM x 2 flop",
                      "flop_s8d_per_update": (M // 2) * L ** 3 * 830,

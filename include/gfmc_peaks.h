@@ -27,7 +27,9 @@ extern "C" {
  *   stream     cudaStream_t (NULL: the legacy default stream).
  * Each launch runs one CTA of 256 threads on every SM (its dynamic shared
  * memory keeps a second one out), every thread 16 independent chains of
- * a = a * m + c for a fixed count; it takes tens of milliseconds.  The call is synchronous.  GFMC_EINVAL for a bad precision or
+ * a = a * m + c for a fixed count; it takes tens of milliseconds.  FP64 runs
+ * the kernel of gfmc_measure_fp64_issue, which retires the FP64 pipe's full
+ * 2 warp-lane slots per SM clock.  The call is synchronous.  GFMC_EINVAL for a bad precision or
  * repeats < 1, GFMC_ECUDA if a CUDA call fails. */
 gfmc_status gfmc_measure_fma_peak(int precision, int repeats, double* tflops, void* stream);
 

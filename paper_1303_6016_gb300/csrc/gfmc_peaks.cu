@@ -32,9 +32,8 @@ __global__ void __launch_bounds__(kThreads) fma_stream(int iters, T m, T c, T* s
     if (s == (T)-1) sink[0] = s;
 }
 
-// One CTA on every SM: the dynamic shared memory keeps a second one out, so no
-// SM holds more of the launch than another (left to the block scheduler, a
-// grid of 2 CTAs per SM without it measured 16 % below the FP64 pipe's rate).
+// One CTA on every SM (the dynamic shared memory keeps a second one out), the
+// occupancy of the engines.
 constexpr int kPeakSmem = 120 * 1024;
 
 template <class T>
@@ -218,6 +217,8 @@ extern "C" gfmc_status gfmc_measure_cluster_exchange(int steps, int repeats, dou
     return st;
 }
 
+namespace {
+
 // ---- the FP64 pipe's issue rate at the FP64 engines' occupancy ----
 // One CTA of 256 threads per SM (the dynamic shared memory keeps a second one
 // out); warps [0, warps) run lanes [0, lanes) of CH independent chains.  Each
@@ -289,6 +290,8 @@ gfmc_status issue_rate(int warps, int lanes, int repeats, double* rate, cudaStre
     return st;
 }
 
+}  // namespace
+
 extern "C" gfmc_status gfmc_measure_fp64_issue(int chains, int warps, int lanes, int repeats, double* fma_per_clock,
                                                void* stream)
 {
@@ -305,12 +308,59 @@ extern "C" gfmc_status gfmc_measure_fp64_issue(int chains, int warps, int lanes,
     }
 }
 
+namespace {
+
+// FP64: the kernel of gfmc_measure_fp64_issue with 8 warps of 16 chains, timed
+// by CUDA events.  It retires the pipe's 2 warp-lane slots per SM clock; a
+// kernel of the same fma count without its CTA barriers and clock reads
+// (fma_stream) retired 1.68 at the same clock, so the peak is taken from it.
+gfmc_status fp64_peak(int repeats, double* tflops, cudaStream_t s)
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return GFMC_ECUDA;
+    if (cudaFuncSetAttribute(fp64_issue<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kIssueSmem) != cudaSuccess)
+        return GFMC_ECUDA;
+    const int iters = 40000;  // about 40 ms per launch
+    double* sink = nullptr;
+    long long* cyc = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaMalloc(&sink, sizeof(double)) != cudaSuccess) return GFMC_ENOMEM;
+    if (cudaMalloc(&cyc, sizeof(long long) * (size_t)sms) != cudaSuccess) {
+        cudaFree(sink);
+        return GFMC_ENOMEM;
+    }
+    gfmc_status st = GFMC_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = GFMC_ECUDA;
+    double best = 0.0;
+    for (int r = 0; r <= repeats && st == GFMC_OK; ++r) {
+        if (cudaEventRecord(e0, s) != cudaSuccess) { st = GFMC_ECUDA; break; }
+        fp64_issue<16><<<sms, kThreads, kIssueSmem, s>>>(iters, kThreads / 32, 32, 0.999, 1e-3, sink, cyc);
+        if (cudaGetLastError() != cudaSuccess || cudaEventRecord(e1, s) != cudaSuccess ||
+            cudaEventSynchronize(e1) != cudaSuccess) {
+            st = GFMC_ECUDA;
+            break;
+        }
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess || !(ms > 0.f)) { st = GFMC_ECUDA; break; }
+        const double flops = 2.0 * 16 * (double)iters * sms * kThreads;
+        if (r > 0 && flops / (ms * 1e-3) / 1e12 > best) best = flops / (ms * 1e-3) / 1e12;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(sink);
+    cudaFree(cyc);
+    if (st == GFMC_OK) *tflops = best;
+    return st;
+}
+
+}  // namespace
+
 extern "C" gfmc_status gfmc_measure_fma_peak(int precision, int repeats, double* tflops, void* stream)
 {
     if (!tflops || repeats < 1 || (precision != GFMC_PREC_FP64 && precision != GFMC_PREC_FP32_MIXED))
         return GFMC_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
-    // about 20-40 ms per launch on a GB300: FP64 issues ~64x fewer fmas per clock
-    return precision == GFMC_PREC_FP64 ? measure<double>(repeats, 40000, tflops, s)
-                                       : measure<float>(repeats, 1600000, tflops, s);
+    // about 40 ms per launch on a GB300: FP64 issues ~64x fewer fmas per clock
+    return precision == GFMC_PREC_FP64 ? fp64_peak(repeats, tflops, s) : measure<float>(repeats, 1600000, tflops, s);
 }
