@@ -466,7 +466,8 @@ def cpu_baseline(L, M, spins, n_updates, threads):
 
 
 def run_reference(args, rank, world, dist):
-    """The oracle (plain single-threaded C, FP64) on the same workload."""
+    """The oracle (plain C, FP64, OpenMP over all host threads) on the same
+    workload: the reference arm, on rank 0 only."""
     if rank != 0:
         return 0
     from paper_1303_6016_gb300 import inputs
